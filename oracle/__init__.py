@@ -115,7 +115,7 @@ def lib():
                                     _P(i32), ctypes.c_int, _P(i32), ctypes.c_int]
             L.orc_rho.argtypes = [ctypes.c_int, _P(d), _P(d), d, ctypes.c_int, _P(i32), _P(d)]
             L.orc_rbe_forces.argtypes = [ctypes.c_int, _P(d), _P(d), _P(i32), _P(i32), _P(Params), u64,
-                                         _P(d), _P(d), _P(d), _P(d), _P(d), _P(d), _P(i32), _P(d)]
+                                         _P(d), _P(d), _P(d), _P(d), _P(d), _P(d), _P(i32), _P(d), _P(d)]
             L.orc_ewald_exact.argtypes = [ctypes.c_int, _P(d), _P(d), _P(i32), _P(i32), _P(Params),
                                           d, ctypes.c_int, _P(d), _P(d), _P(d)]
             L.orc_direct_coulomb.argtypes = [ctypes.c_int, _P(d), _P(d), d, d, ctypes.c_int]
@@ -216,19 +216,23 @@ def rho(pos, q, L, m):
 
 
 def rbe_forces(pos, q, typ, mol, pr, step):
-    """The IRBE estimator: dict(F, F_real, F_long, E[6], W[6], corr, m, rho, status)."""
+    """The IRBE estimator: dict(F, F_real, F_long, F_abs, E[6], W[6], corr, m, rho, status).
+
+    F_abs holds, per force component, the sum of the absolute values of all
+    its summands (the componentwise condition scale of the sum)."""
     pos, q = _f64(pos), _f64(q)
     typ, mol = _i32(typ), _i32(mol)
     n = pos.shape[0]
-    F = np.zeros((n, 3)); Fr = np.zeros((n, 3)); Fl = np.zeros((n, 3))
+    F = np.zeros((n, 3)); Fr = np.zeros((n, 3)); Fl = np.zeros((n, 3)); Fa = np.zeros((n, 3))
     E = np.zeros(6); W = np.zeros(6); corr = np.zeros(3)
     m = np.zeros((pr.P, 3), dtype=np.int32)
     rh = np.zeros((pr.P, 2))
     c = ctypes.c_double
     st = lib().orc_rbe_forces(n, _ptr(pos, c), _ptr(q, c), _ptr(typ, ctypes.c_int32), _ptr(mol, ctypes.c_int32),
                               ctypes.byref(pr), step, _ptr(F, c), _ptr(Fr, c), _ptr(Fl, c), _ptr(E, c), _ptr(W, c),
-                              _ptr(corr, c), _ptr(m, ctypes.c_int32), _ptr(rh, c))
-    return dict(F=F, F_real=Fr, F_long=Fl, E=E, W=W, corr=corr, m=m, rho=rh[:, 0] + 1j * rh[:, 1], status=st)
+                              _ptr(corr, c), _ptr(m, ctypes.c_int32), _ptr(rh, c), _ptr(Fa, c))
+    return dict(F=F, F_real=Fr, F_long=Fl, F_abs=Fa, E=E, W=W, corr=corr, m=m, rho=rh[:, 0] + 1j * rh[:, 1],
+                status=st)
 
 
 def ewald_exact(pos, q, typ, mol, pr, r_cut, kmax):

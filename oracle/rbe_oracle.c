@@ -121,6 +121,19 @@ static uint64_t uniform_below(uint64_t u, uint64_t n)
     return hi;
 }
 
+/* Compensated (Neumaier) running sum: the sums over all atoms below are
+ * evaluated to within a few ulp of the exact sum whatever N is, where plain
+ * recursion's error bound grows as (N-1) u. */
+typedef struct { double s, c; } ksum;
+static void ksum_add(ksum* k, double x)
+{
+    double t = k->s + x;
+    if (fabs(k->s) >= fabs(x)) k->c += (k->s - t) + x;
+    else k->c += (x - t) + k->s;
+    k->s = t;
+}
+static double ksum_get(const ksum* k) { return k->s + k->c; }
+
 /* ------------------------------------------------------------------------ */
 /* Fixed-point coordinates and cells (readings R2, R3)                      */
 /* ------------------------------------------------------------------------ */
@@ -586,20 +599,20 @@ void orc_rho(int n, const double* pos, const double* q, double L, int P, const i
 #pragma omp parallel for schedule(static)
     for (int l = 0; l < P; ++l) {
         double kx = twopi_L * m[3 * l], ky = twopi_L * m[3 * l + 1], kz = twopi_L * m[3 * l + 2];
-        double re = 0.0, im = 0.0;
+        ksum re = {0, 0}, im = {0, 0};
         for (int j = 0; j < n; ++j) {
             double th = kx * pos[3 * j] + ky * pos[3 * j + 1] + kz * pos[3 * j + 2];
-            re += q[j] * cos(th);
-            im += q[j] * sin(th);
+            ksum_add(&re, q[j] * cos(th));
+            ksum_add(&im, q[j] * sin(th));
         }
-        rho[2 * l] = re; rho[2 * l + 1] = im;
+        rho[2 * l] = ksum_get(&re); rho[2 * l + 1] = ksum_get(&im);
     }
 }
 
 /* F_i^{long,*} = - sum_l (S/P) (4 pi k_e q_i k_l / (V k_l^2)) Im(e^{-i k_l.r_i} rho_l)
  * (Eq. (2.9)); energy and virial of the reweighted reciprocal sum. */
 static void rbe_fourier(int n, const double* pos, const double* q, const orc_params* pr,
-                        const int32_t* m, const double* rho, double* F, double* Ek, double* Wk)
+                        const int32_t* m, const double* rho, double* F, double* Fabs, double* Ek, double* Wk)
 {
     double L = pr->L, V = L * L * L;
     double S = orc_S(pr->alpha, L);
@@ -624,7 +637,7 @@ static void rbe_fourier(int n, const double* pos, const double* q, const orc_par
     }
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
-        double f[3] = {0, 0, 0};
+        double f[3] = {0, 0, 0}, fa[3] = {0, 0, 0};
         for (int l = 0; l < P; ++l) {
             double kx = twopi_L * m[3 * l], ky = twopi_L * m[3 * l + 1], kz = twopi_L * m[3 * l + 2];
             double th = kx * pos[3 * i] + ky * pos[3 * i + 1] + kz * pos[3 * i + 2];
@@ -632,8 +645,11 @@ static void rbe_fourier(int n, const double* pos, const double* q, const orc_par
             double im = cos(th) * rho[2 * l + 1] - sin(th) * rho[2 * l];
             double g = -coef[l] * q[i] * im;
             f[0] += g * kx; f[1] += g * ky; f[2] += g * kz;
+            double ga = coef[l] * fabs(q[i]) * (fabs(rho[2 * l]) + fabs(rho[2 * l + 1]));
+            fa[0] += ga * fabs(kx); fa[1] += ga * fabs(ky); fa[2] += ga * fabs(kz);
         }
         F[3 * i] = f[0]; F[3 * i + 1] = f[1]; F[3 * i + 2] = f[2];
+        Fabs[3 * i] = fa[0]; Fabs[3 * i + 1] = fa[1]; Fabs[3 * i + 2] = fa[2];
     }
     *Ek = E;
     for (int a = 0; a < 6; ++a) Wk[a] = W[a];
@@ -647,13 +663,14 @@ static void rbe_fourier(int n, const double* pos, const double* q, const orc_par
  * momentum correction, may be NULL), F_long[3n] (may be NULL),
  * E[6] = {E_real_coul, E_k, E_self, E_lj, E_excl, 0}, W[6] = {xx,yy,zz,xy,xz,yz},
  * corr[3] the net-force correction of Eq. (2.12), m_out[3P] the k samples,
- * rho_out[2P].  mol may be NULL (no exclusions).
- * atoms_sel / n_sel: if atoms_sel is non-NULL only those atoms' F_real are
- * computed (corr is then not available and F is left untouched). */
+ * rho_out[2P], F_abs[3n] the sum of the absolute values of every summand
+ * of each force component (pair terms, the correction, the k terms): the
+ * scale that bounds the rounding error of the component.  mol may be NULL
+ * (no exclusions); every output pointer may be NULL. */
 int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* type,
                    const int32_t* mol, const orc_params* pr, uint64_t step,
                    double* F, double* F_real_out, double* F_long_out, double* E, double* W,
-                   double* corr, int32_t* m_out, double* rho_out)
+                   double* corr, int32_t* m_out, double* rho_out, double* F_abs)
 {
     grid_storage gs;
     build_grid(n, pos, pr, &gs);
@@ -663,6 +680,7 @@ int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* typ
     double* Freal = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     double* Eat = (double*)malloc(sizeof(double) * 3 * (size_t)n);  /* coul, lj, excl per atom */
     double* Wat = (double*)malloc(sizeof(double) * 6 * (size_t)n);
+    double* Aat = (double*)malloc(sizeof(double) * 3 * (size_t)n);  /* sum of |summands| */
     int status = 0;
 #pragma omp parallel
     {
@@ -681,7 +699,7 @@ int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* typ
             classify_and_sample(&g, i, cand, c.count, pr->p, pr->seed, step, &al, words, ord);
             if (al.overlap) local_status |= 2;
             double w_shell = (al.n_shell <= pr->p) ? 1.0 : (double)al.n_shell / (double)pr->p;
-            double f[3] = {0, 0, 0}, u[3] = {0, 0, 0}, wv[6] = {0, 0, 0, 0, 0, 0};
+            double f[3] = {0, 0, 0}, u[3] = {0, 0, 0}, wv[6] = {0, 0, 0, 0, 0, 0}, fa[3] = {0, 0, 0};
             for (int part = 0; part < 2; ++part) {
                 int cnt = part == 0 ? al.n_core : al.n_batch;
                 const int32_t* ids = part == 0 ? al.core : al.batch;
@@ -693,6 +711,7 @@ int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* typ
                     int excl = mol ? (mol[i] == mol[j]) : 0;
                     pair_term(&pc, q[i], q[j], type[i], type[j], excl, d, fij, uij);
                     for (int a = 0; a < 3; ++a) f[a] += w * fij[a];
+                    for (int a = 0; a < 3; ++a) fa[a] += fabs(w * fij[a]);
                     for (int a = 0; a < 3; ++a) u[a] += w * uij[a];
                     wv[0] += w * d[0] * fij[0];
                     wv[1] += w * d[1] * fij[1];
@@ -703,6 +722,7 @@ int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* typ
                 }
             }
             for (int a = 0; a < 3; ++a) Freal[3 * i + a] = f[a];
+            for (int a = 0; a < 3; ++a) Aat[3 * i + a] = fa[a];
             for (int a = 0; a < 3; ++a) Eat[3 * i + a] = u[a];
             for (int a = 0; a < 6; ++a) Wat[6 * i + a] = wv[a];
         }
@@ -710,30 +730,42 @@ int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* typ
         status |= local_status;
         free(cand); free(al.core); free(al.shell); free(al.batch); free(words); free(ord);
     }
-    /* Eq. (2.12): net force of the real-space estimate, sequential sum */
-    double cr[3] = {0, 0, 0};
-    for (int i = 0; i < n; ++i)
-        for (int a = 0; a < 3; ++a) cr[a] += Freal[3 * i + a];
-    for (int a = 0; a < 3; ++a) cr[a] /= (double)n;
-    double Ec = 0, Elj = 0, Ex = 0, Wr[6] = {0, 0, 0, 0, 0, 0};
-    for (int i = 0; i < n; ++i) {
-        Ec += Eat[3 * i]; Elj += Eat[3 * i + 1]; Ex += Eat[3 * i + 2];
-        for (int a = 0; a < 6; ++a) Wr[a] += Wat[6 * i + a];
+    /* Eq. (2.12): net force of the real-space estimate (compensated sums) */
+    double cr[3];
+    for (int a = 0; a < 3; ++a) {
+        ksum k = {0, 0};
+        for (int i = 0; i < n; ++i) ksum_add(&k, Freal[3 * i + a]);
+        cr[a] = ksum_get(&k) / (double)n;
+    }
+    double Ec, Elj, Ex, Wr[6];
+    {
+        ksum kc = {0, 0}, kl = {0, 0}, kx = {0, 0}, kw[6] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        for (int i = 0; i < n; ++i) {
+            ksum_add(&kc, Eat[3 * i]); ksum_add(&kl, Eat[3 * i + 1]); ksum_add(&kx, Eat[3 * i + 2]);
+            for (int a = 0; a < 6; ++a) ksum_add(&kw[a], Wat[6 * i + a]);
+        }
+        Ec = ksum_get(&kc); Elj = ksum_get(&kl); Ex = ksum_get(&kx);
+        for (int a = 0; a < 6; ++a) Wr[a] = ksum_get(&kw[a]);
     }
     /* Fourier part */
     int32_t* m = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)pr->P);
     double* rho = (double*)malloc(sizeof(double) * 2 * (size_t)pr->P);
     double* Flong = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* Flabs = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     orc_sample_k(pr->seed, step, pr->P, pr->alpha, pr->L, m);
     orc_rho(n, pos, q, pr->L, pr->P, m, rho);
     double Ek, Wk[6];
-    rbe_fourier(n, pos, q, pr, m, rho, Flong, &Ek, Wk);
-    double q2 = 0.0;
-    for (int i = 0; i < n; ++i) q2 += q[i] * q[i];
+    rbe_fourier(n, pos, q, pr, m, rho, Flong, Flabs, &Ek, Wk);
+    ksum kq2 = {0, 0};
+    for (int i = 0; i < n; ++i) ksum_add(&kq2, q[i] * q[i]);
+    double q2 = ksum_get(&kq2);
     /* Eq. (2.13) plus Eq. (2.9) */
     if (F)
         for (int i = 0; i < n; ++i)
             for (int a = 0; a < 3; ++a) F[3 * i + a] = Freal[3 * i + a] - cr[a] + Flong[3 * i + a];
+    if (F_abs)
+        for (int i = 0; i < n; ++i)
+            for (int a = 0; a < 3; ++a) F_abs[3 * i + a] = Aat[3 * i + a] + fabs(cr[a]) + Flabs[3 * i + a];
     if (F_real_out) memcpy(F_real_out, Freal, sizeof(double) * 3 * (size_t)n);
     if (F_long_out) memcpy(F_long_out, Flong, sizeof(double) * 3 * (size_t)n);
     if (corr) for (int a = 0; a < 3; ++a) corr[a] = cr[a];
@@ -748,8 +780,8 @@ int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* typ
     if (W) for (int a = 0; a < 6; ++a) W[a] = -0.5 * Wr[a] + Wk[a];
     if (m_out) memcpy(m_out, m, sizeof(int32_t) * 3 * (size_t)pr->P);
     if (rho_out) memcpy(rho_out, rho, sizeof(double) * 2 * (size_t)pr->P);
-    free(m); free(rho); free(Flong);
-    free(Freal); free(Eat); free(Wat);
+    free(m); free(rho); free(Flong); free(Flabs);
+    free(Freal); free(Eat); free(Wat); free(Aat);
     free_grid(&gs);
     return status;
 }
@@ -980,7 +1012,7 @@ int orc_vv_run(int n, double* pos, double* vel, const double* mass, const double
         for (int i = 0; i < n; ++i)
             for (int a = 0; a < 3; ++a) pos[3 * i + a] += dt * vel[3 * i + a];
         status |= orc_rbe_forces(n, pos, q, type, mol, pr, step0 + (uint64_t)k + 1, F, NULL, NULL, E, W,
-                                 NULL, NULL, NULL);
+                                 NULL, NULL, NULL, NULL);
         if (nmol_w > 0) E[5] = orc_water_bonded(nmol_w, 0, pos, pr->L, kb, r0, kth, th0, F);
         for (int i = 0; i < n; ++i)
             for (int a = 0; a < 3; ++a) vel[3 * i + a] += 0.5 * dt * accel * F[3 * i + a] / mass[i];
