@@ -1,0 +1,314 @@
+#!/usr/bin/env python3
+"""Benchmark of the IRBE (RBL + RBE) force step on GB300.
+
+Workload: the 1.2M-atom water-like system (400,000 rigid-geometry 3-site
+molecules at 0.0334 / A^3, L = 228.79 A, r_c = 5 A, r_s = 10 A, p = 20,
+P = 200, alpha from erfc(sqrt(alpha) r_s) = 1e-4), seeded synthetic inputs.
+A step is one full force evaluation (rbe_forces: cell sort, lists and shell
+batches, pair forces, k sampling, rho(k), Fourier forces, momentum
+correction, energies and virial).  The headline is the mixed-precision path
+(FP32 pair/phase arithmetic, FP64 positions and sums), whose force RMS error
+against the FP64 path on identical draws is measured in the same run; the
+FP64 path is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the plain CPU oracle (the same estimator in FP64 C)
+on the host cores, one full force evaluation of the same system per step.
+Under torchrun every rank runs an independent replica (the path does not
+shard: replicas only); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RBE+RBL force evals/s at 1.2M atoms (mixed precision at <=1e-4 force RMS error vs FP64)"
+UNIT = "force_evals/s"
+N_MOL = 400000
+SEED = 3
+DT_FS = 1.0
+L2_FLUSH_BYTES = 512 << 20
+# algorithmic work of the RBL kernel per atom: 420 pair classifications x 9
+# ops + 72.5 pair evaluations x 45 ops (core 52.5 + p = 20), in lane ops
+RBL_OPS_PER_ATOM = 420 * 9 + 72.5 * 45
+SM_COUNT = 152
+LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _workload_config(s):
+    return {"workload": f"water-like {s.n} atoms ({s.n // 3} 3-site molecules), L={s.L:.3f} A, "
+                        f"r_c={s.r_c} A, r_s={s.r_s} A, p={s.p}, P={s.P}, alpha={s.alpha:.6f} A^-2",
+            "n_atoms": s.n, "r_c": s.r_c, "r_s": s.r_s, "p": s.p, "P": s.P,
+            "l2": "flushed between timed steps (512 MB write, outside the timed region)",
+            "step": "one rbe_forces call (one force evaluation)"}
+
+
+def _clock_sampler():
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return None
+
+
+def _clock_summary(proc, dev_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9 or f[0] != str(dev_index):
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path)), "measured"
+        except (OSError, ValueError):
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _traffic(kernel_src):
+    """DRAM bytes per launch of the RBL kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "rbl_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    if rec.get("source_sha256") != sha or rec.get("precision") != "mixed":
+        return None
+    return rec.get("dram_bytes_per_launch_full")
+
+
+def run_reference(args):
+    import numpy as np  # noqa: F401
+    import oracle
+    from paper_2204_13595_gb300 import systems
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    oracle.build()
+    s = systems.water(N_MOL, seed=SEED)
+    pr = oracle.make_params(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, SEED, k_e=s.k_e, eps=s.eps, sigma=s.sigma)
+    for w in range(args.warmup):
+        oracle.rbe_forces(s.pos, s.q, s.type, s.mol, pr, w)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.rbe_forces(s.pos, s.q, s.type, s.mol, pr, args.warmup + k)
+    dt = (time.perf_counter() - t0) / args.steps
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = 1.0 / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _workload_config(s),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one full FP64 oracle force evaluation of the 1.2M-atom system per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2204_13595_gb300 import build as b
+    from paper_2204_13595_gb300 import rbe, systems
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    b.build()
+    s = systems.water(N_MOL, seed=SEED + rank)
+    dev = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device="cuda")
+    pos, q, typ, mol = dev(s.pos), dev(s.q), dev(s.type, torch.int32), dev(s.mol, torch.int32)
+    F = torch.empty_like(pos)
+    E = torch.zeros(rbe.NE, dtype=torch.float64, device="cuda")
+    W = torch.zeros(rbe.NW, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def make(prec):
+        return rbe.Context(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, SEED, k_e=s.k_e, eps=s.eps, sigma=s.sigma,
+                           precision=prec)
+
+    def timed(ctx, steps, warmup, profile=False):
+        for w in range(warmup):
+            ctx.forces(w, pos, q, typ, mol, F, E, W)
+        if ctx.sync_status() != 0:
+            raise RuntimeError("device status error during warm-up")
+        if profile:
+            ctx.profile(reset=True)
+            ctx.set_profiling(True)
+        total = 0.0
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.forces(warmup + k, pos, q, typ, mol, F, E, W)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        prof = None
+        if profile:
+            prof = ctx.profile(reset=True)
+            ctx.set_profiling(False)
+        launches = int(ctx.info()["launches"])
+        if ctx.sync_status() != 0:
+            raise RuntimeError("device status error during the timed steps")
+        ms = total / steps
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof, launches
+
+    # fixed-error check: mixed vs FP64 on identical draws (outside timing)
+    mixed, f64 = make(rbe.MIXED), make(rbe.FP64)
+    mixed.forces(123, pos, q, typ, mol, F)
+    Fm = F.clone()
+    f64.forces(123, pos, q, typ, mol, F)
+    err = float(torch.sqrt(((Fm - F) ** 2).mean()) / torch.sqrt((F ** 2).mean()))
+
+    clocks_proc = _clock_sampler() if rank == 0 else None
+    ms_mixed, prof, launches = timed(mixed, args.steps, args.warmup, profile=True)
+    clocks = _clock_summary(clocks_proc, local) if rank == 0 else None
+    ms_f64, _, _ = timed(f64, max(3, min(args.steps, 10)), max(3, min(args.warmup, 3)))
+
+    # end to end through the same C ABI with pinned host buffers
+    hp = torch.tensor(s.pos, dtype=torch.float64).pin_memory()
+    hq = torch.tensor(s.q, dtype=torch.float64).pin_memory()
+    ht = torch.tensor(s.type, dtype=torch.int32).pin_memory()
+    hm = torch.tensor(s.mol, dtype=torch.int32).pin_memory()
+    hF = torch.empty((s.n, 3), dtype=torch.float64).pin_memory()
+    hE = torch.empty(rbe.NE, dtype=torch.float64).pin_memory()
+    hW = torch.empty(rbe.NW, dtype=torch.float64).pin_memory()
+    for w in range(args.warmup):
+        mixed.forces(w, hp, hq, ht, hm, hF, hE, hW)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        mixed.forces(args.warmup + k, hp, hq, ht, hm, hF, hE, hW)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = hp.numel() * 8 + hq.numel() * 8 + ht.numel() * 4 + hm.numel() * 4
+    d2h = hF.numel() * 8 + hE.numel() * 8 + hW.numel() * 8
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (the RBL list + pair kernel)
+    rbl_ms, rbl_n = prof["rbl"]
+    rbl_avg_s = rbl_ms / max(rbl_n, 1) * 1e-3
+    achieved = RBL_OPS_PER_ATOM * s.n / rbl_avg_s / 1e12
+    peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    kshare = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-30), 4) for k, v in prof.items() if v[1]}
+    traffic = _traffic(os.path.join(ROOT, "paper_2204_13595_gb300", "csrc", "k_rbl.cu"))
+
+    # CPU baseline: the oracle on the host cores, one full evaluation
+    import oracle
+    oracle.build()
+    pr = oracle.make_params(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, SEED, k_e=s.k_e, eps=s.eps, sigma=s.sigma)
+    t0 = time.perf_counter()
+    oracle.rbe_forces(s.pos, s.q, s.type, s.mol, pr, 0)
+    cpu_s = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+    value = ws * 1e3 / ms_mixed
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 pair/phase + f64 positions/sums (mixed)", "data": "synthetic",
+        "config": dict(_workload_config(s), precision="mixed", parallelism=f"replicas x{ws}"),
+        "ns_per_day": 0.0864 * value * DT_FS, "atom_steps_per_s": value * s.n,
+        "fp64": {"value": ws * 1e3 / ms_f64, "ms_per_step": ms_f64, "ns_per_day": 0.0864 * ws * 1e3 / ms_f64 * DT_FS},
+        "speedup_mixed_vs_fp64": ms_f64 / ms_mixed,
+        "mixed_force_rms_rel_err_vs_fp64": err,
+        "roofline": {"kernel": "k_rbl (lists + shell batch + pair forces, mixed)", "bound": "alu",
+                     "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_source": "derived: 152 SMs x 128 lanes x 2070 MHz, 1 op/lane/clk",
+                     "avg_launch_ms": rbl_avg_s * 1e3},
+        "kernel_share": kshare,
+        "cpu_baseline": {"value": 1.0 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "one full FP64 oracle force evaluation of the same 1.2M-atom system"},
+        "e2e": {"value": ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clocks, "gpu_launches": launches * args.steps,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

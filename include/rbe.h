@@ -1,0 +1,202 @@
+/*
+ * rbe.h -- C ABI of librbe.so: the improved random batch Ewald (IRBE) non-bonded
+ * force step of Liang, Xu & Zhao (arXiv 2204.13595) on one NVIDIA GB300
+ * (sm_103a).
+ *
+ * The step joins two stochastic estimators:
+ *   RBL (Sec. 2.3, Eqs. (2.10)-(2.13)): every pair inside the core radius r_c
+ *       is summed exactly; a batch of p atoms drawn from the shell
+ *       r_c < r <= r_s is summed with weight N_S/p; the mean net real-space
+ *       force is removed from every atom (momentum correction, Eq. (2.13)).
+ *   RBE (Sec. 2.2, Eqs. (2.6)-(2.9)): P wave vectors k != 0 are drawn from
+ *       P_k = exp(-k^2/(4 alpha))/S, the structure factors
+ *       rho(k) = sum_j q_j exp(i k.r_j) are formed over all atoms and each
+ *       atom's long-range force is summed over the batch.
+ *
+ * Notation: r_c here is the paper's core radius r_eta and r_s the paper's
+ * outer cutoff r_c; p is the paper's shell batch p~ and P its Fourier batch p.
+ *
+ * Every random draw is a pure function of (seed, step, atom, slot) through
+ * Philox4x64-10: key (seed, 0); shell slot k of atom i uses word k%4 of the
+ * block at counter (i, k/4, step, 1), where i is the caller's atom index;
+ * k sample l, attempt t uses words 0..2 of the block at counter (l, t, step, 2).
+ * List membership is decided on 32-bit fixed-point fractional coordinates
+ * s = floor(frac(x/L) 2^32) with exact integer squared distances, so lists and
+ * batches are reproducible bit for bit.  Shell ordinals index S(i) in the
+ * canonical order: ascending (cell, atom index) on the grid of floor(L/r_c)
+ * cells per axis (the cell grid of Sec. 2.3).
+ *
+ * Conventions for every entry point:
+ *   - return 0 (RBE_OK) or a negative RBE_E* code; no exception or abort
+ *     crosses the ABI; rbe_last_error() gives a message for the last failure;
+ *   - a context is not thread-safe: use one context per host thread/stream;
+ *   - array arguments are caller-owned; the library never frees them;
+ *   - pos is [n][3] row-major FP64 (Angstrom or sigma), q is [n] FP64,
+ *     type and mol are [n] int32; F and vel are [n][3] FP64;
+ *   - a cuda_stream argument is a cudaStream_t (NULL = legacy default stream);
+ *     work is enqueued on it and the call returns without waiting, unless a
+ *     host pointer is involved (see rbe_forces).
+ */
+#ifndef RBE_H
+#define RBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RBE_OK            0
+#define RBE_EINVAL       -1   /* bad parameter or argument                     */
+#define RBE_ENONNEUTRAL  -2   /* |sum q| > 1e-10 sum |q| (Sec. 2.1 assumes 0)  */
+#define RBE_EOVERLAP     -3   /* two atoms at the same fixed-point position     */
+#define RBE_ENONFINITE   -4   /* non-finite position or result                  */
+#define RBE_ECAPACITY    -5   /* a per-atom list exceeded its capacity          */
+#define RBE_ECUDA        -6   /* a CUDA runtime call failed                     */
+#define RBE_ENOMEM       -7   /* device allocation failed                       */
+
+/* precision modes (rbe_set_precision) */
+#define RBE_FP64   0   /* all arithmetic in FP64                                */
+#define RBE_MIXED  1   /* FP32 pair and phase arithmetic; FP64 positions,
+                          rho(k) accumulation, force and energy totals          */
+
+/* energy components written by rbe_forces (RBE_NE doubles) */
+#define RBE_NE 6
+#define RBE_E_REAL   0   /* erfc real-space Coulomb, RBL estimate (Eq. (2.3) U^short) */
+#define RBE_E_KSPACE 1   /* reciprocal space, RBE estimate (Eq. (2.3) U^long)         */
+#define RBE_E_SELF   2   /* -k_e sqrt(alpha/pi) sum q^2 (Eq. (2.3) U^corr)             */
+#define RBE_E_LJ     3   /* Lennard-Jones, RBL estimate (Eq. (2.3) U^lj)               */
+#define RBE_E_EXCL   4   /* -k_e q_i q_j erf(sqrt(alpha) r)/r over same-molecule pairs */
+#define RBE_E_BOND   5   /* harmonic water bonds and angles (rbe_set_water_bonds)      */
+/* virial components (RBE_NW doubles): xx yy zz xy xz yz of
+ * W = -1/2 sum_i sum_j w_ij r_ij (x) f_ij  (r_ij = r_j - r_i, w_ij the RBL
+ * weight) plus the reweighted reciprocal-space Ewald virial; non-bonded only. */
+#define RBE_NW 6
+
+typedef struct rbe_ctx rbe_ctx;
+
+/* Creates a context for a cubic periodic box of edge box_L (Sec. 2.1).
+ * alpha > 0 is the Ewald parameter of erfc(sqrt(alpha) r) and
+ * exp(-k^2/(4 alpha)) (Eqs. (2.2)-(2.3)); 0 < r_c < r_s <= box_L/2 are the
+ * core radius and outer cutoff (Sec. 2.3); p >= 1 the shell batch size
+ * (Eq. (2.11)); P >= 1 the Fourier batch size (Eq. (2.9)); seed the Philox
+ * key.  Coulomb prefactor defaults to 1, no LJ, precision RBE_FP64.
+ * Allocates device memory lazily on the first rbe_forces call, on the device
+ * current at that time.  *out receives the context (NULL on failure). */
+int rbe_create(rbe_ctx** out, double box_L, double alpha, double r_c, double r_s,
+               int p, int P, uint64_t seed);
+
+/* Coulomb prefactor k_e multiplying every q_i q_j term (the paper writes
+ * Gaussian units, Eq. (2.1)): 1.4 for the reduced electrolyte, 1389.35458
+ * kJ mol^-1 A e^-2 for water. */
+int rbe_set_coulomb(rbe_ctx* ctx, double k_e);
+
+/* Lennard-Jones per-type parameters (host arrays of ntypes <= 16 entries)
+ * mixed by Lorentz-Berthelot (sigma_ij = (sigma_i+sigma_j)/2,
+ * eps_ij = sqrt(eps_i eps_j)); the pair force is Eq. (2.10), truncated at
+ * r_s; shift_energy = 1 shifts the LJ energy to zero at r_s. */
+int rbe_set_lj(rbe_ctx* ctx, int ntypes, const double* eps, const double* sigma, int shift_energy);
+
+/* RBE_FP64 or RBE_MIXED. */
+int rbe_set_precision(rbe_ctx* ctx, int mode);
+
+/* Harmonic 3-site water bonded terms for molecules m = 0..n_mol-1 made of
+ * atoms (3m, 3m+1, 3m+2) = (O, H, H): U = 1/2 k_b (r - r0)^2 per O-H bond and
+ * 1/2 k_theta (theta - theta0)^2 per H-O-H angle (theta in radians).  Added by
+ * rbe_forces to F and to energy[RBE_E_BOND].  n_mol = 0 disables them.
+ * The paper integrates with a force field (Sec. 3.2); these constants are the
+ * caller's choice. */
+int rbe_set_water_bonds(rbe_ctx* ctx, int n_mol, double k_b, double r0, double k_theta, double theta0);
+
+/* Per-atom list capacities used by the pair kernel (0 = automatic, from the
+ * density: roughly twice the mean count plus a margin).  A list longer than its
+ * capacity sets RBE_ECAPACITY in the status word. */
+int rbe_set_capacity(rbe_ctx* ctx, int core_cap, int shell_cap);
+
+/* One IRBE force evaluation at MD step `step` (Algorithm 1, force steps):
+ * F = F^core + F^{shell,*} - F^corr + F^{long,*} (Eqs. (2.9), (2.11), (2.13))
+ * plus the water bonded terms when configured.  Excluded pairs are the pairs
+ * with equal mol id (mol may be NULL: no exclusions); they keep their set
+ * membership and contribute -k_e q_i q_j erf(sqrt(alpha) r)/r instead of
+ * erfc + LJ.  type may be NULL (all type 0).
+ * pos, q, type, mol, F are either all device pointers or all host pointers.
+ * With host pointers the library stages them through device memory and the
+ * call returns after F is written.  energy (RBE_NE) and virial (RBE_NW) may each
+ * be NULL, a host pointer (the call then waits for the stream) or a device
+ * pointer.  Positions need not be wrapped into the box.
+ * Errors found on the device (overlap, capacity, non-neutral charge,
+ * non-finite input) are latched in a status word read by rbe_sync_status(). */
+int rbe_forces(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const double* q,
+               const int32_t* type, const int32_t* mol, double* F, double* energy, double* virial,
+               void* cuda_stream);
+
+/* nsteps of velocity Verlet (Algorithm 1, integration step, NVE):
+ *   v += (dt/2) accel F/m;  x += dt v;  F = rbe_forces(step0+k+1);  v += (dt/2) accel F/m
+ * accel converts force/mass to acceleration (1 in reduced units, 1e-4 for
+ * kJ/mol/A, g/mol, fs).  On entry F must hold the forces at (pos, step0); on
+ * exit it holds those at the final positions.  All arrays are device pointers;
+ * energy_trace (device, may be NULL) receives per step the potential energy
+ * (sum of the RBE_NE components) and the kinetic energy / accel. */
+int rbe_step(rbe_ctx* ctx, uint64_t step0, int nsteps, double dt, double accel, int n,
+             double* pos, double* vel, const double* mass, const double* q, const int32_t* type,
+             const int32_t* mol, double* F, double* energy_trace, void* cuda_stream);
+
+/* Waits for cuda_stream, returns the first latched device error (or RBE_OK)
+ * and clears the status word. */
+int rbe_sync_status(rbe_ctx* ctx, void* cuda_stream);
+
+/* Debug recording: when on, rbe_forces also records per atom (indexed by the
+ * caller's atom index) |C(i)|, |S(i)|, the core ids in canonical order (up to
+ * cap_core) and the batch B(i) in slot order (p entries, -1 padded). */
+int rbe_set_debug(rbe_ctx* ctx, int on, int cap_core);
+
+/* Copies the lists recorded by the last rbe_forces with debug on into host
+ * arrays: n_core[n], n_shell[n], core[n][cap_core], batch[n][p] (any may be
+ * NULL).  Waits for cuda_stream. */
+int rbe_get_lists(rbe_ctx* ctx, int n, int32_t* n_core, int32_t* n_shell, int32_t* core,
+                  int32_t* batch, void* cuda_stream);
+
+/* Copies the last step's k samples m[P][3] (integers, k = 2 pi m / L) and
+ * structure factors rho[P][2] (re, im) into host arrays (either may be NULL).
+ * Waits for cuda_stream. */
+int rbe_get_kspace(rbe_ctx* ctx, int32_t* m, double* rho, void* cuda_stream);
+
+/* Derived parameters: out[0] cells per axis, out[1] stencil reach in cells,
+ * out[2] k truncation M, out[3] S = H^3 - 1 (Eq. (2.6)), out[4] core capacity,
+ * out[5] shell capacity (after the last rbe_forces), out[6] kernel launches
+ * of the last rbe_forces. */
+int rbe_get_info(rbe_ctx* ctx, double* out, int nout);
+
+/* Kernel timing: when on, every launch is bracketed by CUDA events on its
+ * stream.  rbe_get_profile waits for cuda_stream and returns, per kernel id
+ * (RBE_K_*), the summed milliseconds and the number of launches since the
+ * last reset (reset = 1 clears them afterwards). */
+#define RBE_K_QUANTIZE 0
+#define RBE_K_SCAN     1
+#define RBE_K_SCATTER  2
+#define RBE_K_SORT     3
+#define RBE_K_GATHER   4
+#define RBE_K_KSAMPLE  5
+#define RBE_K_RHO      6
+#define RBE_K_RHOSUM   7
+#define RBE_K_RBL      8
+#define RBE_K_BONDED   9
+#define RBE_K_FINAL    10
+#define RBE_K_KFORCE   11
+#define RBE_K_VV       12
+#define RBE_K_MISC     13
+#define RBE_NKERNELS   14
+int rbe_set_profiling(rbe_ctx* ctx, int on);
+int rbe_get_profile(rbe_ctx* ctx, double* ms, int64_t* launches, int reset, void* cuda_stream);
+
+const char* rbe_last_error(const rbe_ctx* ctx);
+
+/* Releases the context and its device memory (after the caller's streams are
+ * idle). */
+void rbe_destroy(rbe_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBE_H */

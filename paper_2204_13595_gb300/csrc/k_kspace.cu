@@ -1,0 +1,443 @@
+// k_kspace.cu -- random batch Ewald (RBE) Fourier part, Sec. 2.2, plus the
+// deterministic finalisation of the step, bonded water terms and the
+// velocity-Verlet kernels.
+//
+//   k_sample   : P wave vectors from P_k of Eq. (2.8): per axis an exact
+//                inverse-CDF draw of the discrete Gaussian
+//                exp(-pi^2 m^2/(alpha L^2)) on 64-bit thresholds, (0,0,0)
+//                redrawn; Philox counter (l, attempt, step, 2).
+//   k_rho      : rho(k_l) = sum_j q_j exp(i k_l.r_j) (Eq. (2.4)); a block owns
+//                a contiguous chunk of atoms staged tile by tile in shared
+//                memory, each thread owns one k_l and keeps its partial sum in
+//                registers; block partials are summed over blocks in a fixed
+//                order by k_rho_sum (the single-GPU form of the paper's one
+//                MPI_Allreduce of rho(k), Sec. 3).
+//   k_kforce   : F_i^{long,*} of Eq. (2.9) with the sampled k_l and rho_l
+//                staged in shared memory, combined with the real-space
+//                estimate and the momentum correction of Eq. (2.13), written
+//                back in the caller's atom order.
+// Mixed precision: the phase m.s of the fixed-point coordinates is reduced
+// exactly in 32-bit integer arithmetic (k.r = 2 pi (m.s)/2^32 mod 2 pi), then
+// evaluated with FP32 sincos; sums go to FP64 every tile.
+#include <math.h>
+
+#include "rbe_internal.cuh"
+
+namespace {
+
+constexpr int TILE = 256;
+constexpr int TPB = 256;
+
+__device__ __forceinline__ int inv_cdf(uint64_t u, const uint64_t* __restrict__ T, int M)
+{
+    int lo = 0, hi = 2 * M;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (u < T[mid]) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo - M;
+}
+
+__global__ void __launch_bounds__(TPB) k_sample(RbeConsts c, uint64_t step, const uint64_t* __restrict__ T,
+                                                int4* __restrict__ km, double4_32a* __restrict__ kv,
+                                                int* __restrict__ status)
+{
+    const double twopi_L = 2.0 * 3.14159265358979323846 / c.L;
+    for (int l = blockIdx.x * TPB + threadIdx.x; l < c.P; l += gridDim.x * TPB) {
+        int mx = 1, my = 0, mz = 0;
+        bool ok = false;
+        for (uint64_t t = 0; t < 1024 && !ok; ++t) {
+            uint64_t w[4];
+            philox4x64_10((uint64_t)l, t, step, 2ull, c.seed, 0ull, w);
+            int ax = inv_cdf(w[0], T, c.M), ay = inv_cdf(w[1], T, c.M), az = inv_cdf(w[2], T, c.M);
+            if (ax != 0 || ay != 0 || az != 0) { mx = ax; my = ay; mz = az; ok = true; }
+        }
+        if (!ok) latch_status(status, RBE_ST_KSAMPLE);
+        double kx = twopi_L * mx, ky = twopi_L * my, kz = twopi_L * mz;
+        double k2 = kx * kx + ky * ky + kz * kz;
+        km[l] = make_int4(mx, my, mz, 0);
+        kv[l] = make_double4_32a(kx, ky, kz, c.kcoef / k2);
+    }
+}
+
+// rho partial sums: block b owns atoms [b*chunk, min(n,(b+1)*chunk)).
+template <bool MIXED>
+__global__ void k_rho(int n, int chunk, RbeConsts c, const uint4* __restrict__ s4, const double4_32a* __restrict__ p4,
+                      const int4* __restrict__ km, double2* __restrict__ part)
+{
+    __shared__ double4_32a tile_d[MIXED ? 1 : TILE];
+    __shared__ uint4 tile_u[MIXED ? TILE : 1];
+    const int b0 = blockIdx.x * chunk;
+    const int b1 = min(n, b0 + chunk);
+    for (int l0 = 0; l0 < c.P; l0 += blockDim.x) {
+        const int l = l0 + threadIdx.x;
+        const bool act = l < c.P;
+        int4 m = act ? km[l] : make_int4(0, 0, 0, 0);
+        double re = 0.0, im = 0.0;
+        for (int t0 = b0; t0 < b1; t0 += TILE) {
+            const int cnt = min(TILE, b1 - t0);
+            __syncthreads();
+            for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+                if (MIXED) tile_u[k] = s4[t0 + k];
+                else tile_d[k] = p4[t0 + k];
+            }
+            __syncthreads();
+            if (act) {
+                if (MIXED) {
+                    float fre = 0.f, fim = 0.f;
+                    const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
+                    for (int k = 0; k < cnt; ++k) {
+                        uint4 s = tile_u[k];
+                        uint32_t ph = mx * s.x + my * s.y + mz * s.z;
+                        float ang = (float)(int)ph * 1.4629180792671596e-09f;   // 2 pi / 2^32
+                        float sn, cs;
+                        __sincosf(ang, &sn, &cs);
+                        float q = __uint_as_float(s.w);
+                        fre += q * cs;
+                        fim += q * sn;
+                    }
+                    re += (double)fre;
+                    im += (double)fim;
+                } else {
+                    const double mxd = m.x, myd = m.y, mzd = m.z;
+                    for (int k = 0; k < cnt; ++k) {
+                        double4_32a p = tile_d[k];
+                        double t = (mxd * p.x + myd * p.y + mzd * p.z) * c.invL;
+                        t -= rint(t);
+                        double sn, cs;
+                        sincospi(2.0 * t, &sn, &cs);
+                        re += p.w * cs;
+                        im += p.w * sn;
+                    }
+                }
+            }
+        }
+        if (act) part[(size_t)blockIdx.x * c.P + l] = make_double2(re, im);
+    }
+}
+
+// Fixed-order sum over blocks; per-k energy and virial terms of the
+// reweighted reciprocal sum (E_k = sum_l c_l/2 |rho_l|^2).
+__global__ void __launch_bounds__(TPB) k_rho_sum(int nblk, RbeConsts c, const double2* __restrict__ part,
+                                                 const double4_32a* __restrict__ kv, double2* __restrict__ rho,
+                                                 double* __restrict__ kterms)
+{
+    int l = blockIdx.x * TPB + threadIdx.x;
+    if (l >= c.P) return;
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        double2 v = part[(size_t)b * c.P + l];
+        re += v.x;
+        im += v.y;
+    }
+    rho[l] = make_double2(re, im);
+    double4_32a k = kv[l];
+    double k2 = k.x * k.x + k.y * k.y + k.z * k.z;
+    double e = 0.5 * k.w * (re * re + im * im);
+    double bb = 2.0 * (1.0 / k2 + 1.0 / (4.0 * c.alpha));
+    double* o = kterms + 7 * (size_t)l;
+    o[0] = e;
+    o[1] = e * (1.0 - bb * k.x * k.x);
+    o[2] = e * (1.0 - bb * k.y * k.y);
+    o[3] = e * (1.0 - bb * k.z * k.z);
+    o[4] = e * (-bb * k.x * k.y);
+    o[5] = e * (-bb * k.x * k.z);
+    o[6] = e * (-bb * k.y * k.z);
+}
+
+// Harmonic water: molecule m = atoms (3m, 3m+1, 3m+2) = (O, H, H).
+__global__ void __launch_bounds__(TPB) k_bonded(int nmol, const double* __restrict__ pos, RbeConsts c, double kb,
+                                                double r0, double kth, double th0, double* __restrict__ Fb,
+                                                double* __restrict__ part)
+{
+    double u = 0.0;
+    for (int mI = blockIdx.x * TPB + threadIdx.x; mI < nmol; mI += gridDim.x * TPB) {
+        int o = 3 * mI;
+        double d1[3], d2[3];
+        for (int a = 0; a < 3; ++a) {
+            double x1 = pos[3 * (o + 1) + a] - pos[3 * o + a];
+            double x2 = pos[3 * (o + 2) + a] - pos[3 * o + a];
+            d1[a] = x1 - c.L * rint(x1 * c.invL);
+            d2[a] = x2 - c.L * rint(x2 * c.invL);
+        }
+        double r1 = sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+        double r2 = sqrt(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+        double g1 = -kb * (r1 - r0) / r1, g2 = -kb * (r2 - r0) / r2;
+        u += 0.5 * kb * (r1 - r0) * (r1 - r0) + 0.5 * kb * (r2 - r0) * (r2 - r0);
+        double cth = (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]) / (r1 * r2);
+        cth = fmin(1.0, fmax(-1.0, cth));
+        double th = acos(cth);
+        double sn = fmax(sqrt(1.0 - cth * cth), 1e-12);
+        u += 0.5 * kth * (th - th0) * (th - th0);
+        double dUdth = kth * (th - th0);
+        double fo[3], fh1[3], fh2[3];
+        for (int a = 0; a < 3; ++a) {
+            double f1 = -dUdth * (-(d2[a] / (r1 * r2) - cth * d1[a] / (r1 * r1)) / sn);
+            double f2 = -dUdth * (-(d1[a] / (r1 * r2) - cth * d2[a] / (r2 * r2)) / sn);
+            fh1[a] = g1 * d1[a] + f1;
+            fh2[a] = g2 * d2[a] + f2;
+            fo[a] = -(g1 * d1[a] + g2 * d2[a]) - (f1 + f2);
+        }
+        for (int a = 0; a < 3; ++a) {
+            Fb[3 * o + a] = fo[a];
+            Fb[3 * (o + 1) + a] = fh1[a];
+            Fb[3 * (o + 2) + a] = fh2[a];
+        }
+    }
+    __shared__ double red[TPB / 32];
+    u = warp_sum(u);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < TPB / 32; ++w) s += red[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+// Fixed-order block reduction of a strided column.
+__device__ double block_sum_col(const double* __restrict__ src, int nrow, int stride, int col, double* sh)
+{
+    double s = 0.0;
+    for (int r = threadIdx.x; r < nrow; r += blockDim.x) s += src[(size_t)r * stride + col];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// totals: E[0..5], W[6..11], corr[12..14]
+__global__ void __launch_bounds__(TPB) k_finalize(int n, RbeConsts c, const double* __restrict__ part_rbl, int grid_rbl,
+                                                  const double* __restrict__ part_q, int grid_q,
+                                                  const double* __restrict__ kterms,
+                                                  const double* __restrict__ part_bond, int grid_bond,
+                                                  double* __restrict__ totals, int* __restrict__ status)
+{
+    __shared__ double sh[TPB];
+    double r[RBE_NPART_RBL];
+    for (int q = 0; q < RBE_NPART_RBL; ++q) r[q] = block_sum_col(part_rbl, grid_rbl, RBE_NPART_RBL, q, sh);
+    double qs[RBE_NPART_Q];
+    for (int q = 0; q < RBE_NPART_Q; ++q) qs[q] = block_sum_col(part_q, grid_q, RBE_NPART_Q, q, sh);
+    double kt[7];
+    for (int q = 0; q < 7; ++q) kt[q] = block_sum_col(kterms, c.P, 7, q, sh);
+    double eb = grid_bond > 0 ? block_sum_col(part_bond, grid_bond, 1, 0, sh) : 0.0;
+    if (threadIdx.x == 0) {
+        totals[0] = 0.5 * r[0];
+        totals[1] = kt[0];
+        totals[2] = -c.k_e * sqrt(c.alpha / 3.14159265358979323846) * qs[0];
+        totals[3] = 0.5 * r[1];
+        totals[4] = 0.5 * r[2];
+        totals[5] = eb;
+        for (int a = 0; a < 6; ++a) totals[6 + a] = -0.5 * r[3 + a] + kt[1 + a];
+        for (int a = 0; a < 3; ++a) totals[12 + a] = r[9 + a] / (double)n;
+        if (fabs(qs[1]) > 1e-10 * qs[2]) latch_status(status, RBE_ST_NONNEUTRAL);
+        bool fin = true;
+        for (int a = 0; a < 15; ++a) fin = fin && isfinite(totals[a]);
+        if (!fin) latch_status(status, RBE_ST_NONFINITE);
+    }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(TPB) k_kforce(int n, RbeConsts c, const uint4* __restrict__ s4,
+                                                const double4_32a* __restrict__ p4, const int* __restrict__ perm,
+                                                const int4* __restrict__ km, const double4_32a* __restrict__ kv,
+                                                const double2* __restrict__ rho, const double* __restrict__ F_real,
+                                                const double* __restrict__ totals, const double* __restrict__ F_bond,
+                                                int n_bonded_atoms, double* __restrict__ F)
+{
+    constexpr int KT = 256;
+    __shared__ double4_32a sk_d[MIXED ? 1 : KT];      // kx, ky, kz, unused
+    __shared__ double2 sab_d[MIXED ? 1 : KT];     // (c Im rho, c Re rho)
+    __shared__ int4 sm[KT];
+    __shared__ float4 sk_f[MIXED ? KT : 1];       // kx, ky, kz, c Im rho
+    __shared__ float sb_f[MIXED ? KT : 1];        // c Re rho
+    const int i = blockIdx.x * TPB + threadIdx.x;
+    const bool act = i < n;
+    uint4 si = make_uint4(0, 0, 0, 0);
+    double4_32a pi = make_double4_32a(0, 0, 0, 0);
+    if (act) {
+        if (MIXED) si = s4[i];
+        else pi = p4[i];
+    }
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int l0 = 0; l0 < c.P; l0 += KT) {
+        const int cnt = min(KT, c.P - l0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += TPB) {
+            double4_32a k4 = kv[l0 + k];
+            double2 r = rho[l0 + k];
+            if (MIXED) {
+                sm[k] = km[l0 + k];
+                sk_f[k] = make_float4((float)k4.x, (float)k4.y, (float)k4.z, (float)(k4.w * r.y));
+                sb_f[k] = (float)(k4.w * r.x);
+            } else {
+                sm[k] = km[l0 + k];
+                sk_d[k] = k4;
+                sab_d[k] = make_double2(k4.w * r.y, k4.w * r.x);
+            }
+        }
+        __syncthreads();
+        if (act) {
+            if (MIXED) {
+                float g[3] = {0.f, 0.f, 0.f};
+                for (int k = 0; k < cnt; ++k) {
+                    int4 m = sm[k];
+                    uint32_t ph = (uint32_t)m.x * si.x + (uint32_t)m.y * si.y + (uint32_t)m.z * si.z;
+                    float ang = (float)(int)ph * 1.4629180792671596e-09f;
+                    float sn, cs;
+                    __sincosf(ang, &sn, &cs);
+                    float4 kk = sk_f[k];
+                    // Im(e^{-i th} rho) c = cos(th) c Im rho - sin(th) c Re rho
+                    float h = cs * kk.w - sn * sb_f[k];
+                    g[0] += h * kk.x; g[1] += h * kk.y; g[2] += h * kk.z;
+                }
+                for (int a = 0; a < 3; ++a) f[a] += (double)g[a];
+            } else {
+                for (int k = 0; k < cnt; ++k) {
+                    int4 m = sm[k];
+                    double t = ((double)m.x * pi.x + (double)m.y * pi.y + (double)m.z * pi.z) * c.invL;
+                    t -= rint(t);
+                    double sn, cs;
+                    sincospi(2.0 * t, &sn, &cs);
+                    double2 ab = sab_d[k];
+                    double h = cs * ab.x - sn * ab.y;
+                    double4_32a kk = sk_d[k];
+                    f[0] += h * kk.x; f[1] += h * kk.y; f[2] += h * kk.z;
+                }
+            }
+        }
+    }
+    if (!act) return;
+    const double qi = MIXED ? (double)p4[i].w : pi.w;
+    const int gi = perm[i];
+    for (int a = 0; a < 3; ++a) {
+        double v = F_real[3 * (size_t)i + a] - totals[12 + a] - qi * f[a];
+        if (gi < n_bonded_atoms) v += F_bond[3 * (size_t)gi + a];
+        F[3 * (size_t)gi + a] = v;
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_vv(int n, double* __restrict__ pos, double* __restrict__ vel,
+                                            const double* __restrict__ mass, const double* __restrict__ F, double hdta,
+                                            double dt, int drift)
+{
+    int i = blockIdx.x * TPB + threadIdx.x;
+    if (i >= n) return;
+    double m = mass[i];
+    for (int a = 0; a < 3; ++a) {
+        double v = __dadd_rn(vel[3 * i + a], __ddiv_rn(__dmul_rn(hdta, F[3 * i + a]), m));
+        vel[3 * i + a] = v;
+        if (drift) pos[3 * i + a] = __dadd_rn(pos[3 * i + a], __dmul_rn(dt, v));
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_ke(int n, const double* __restrict__ vel, const double* __restrict__ mass,
+                                            double* __restrict__ part)
+{
+    double s = 0.0;
+    for (int i = blockIdx.x * TPB + threadIdx.x; i < n; i += gridDim.x * TPB)
+        for (int a = 0; a < 3; ++a) s += 0.5 * mass[i] * vel[3 * i + a] * vel[3 * i + a];
+    __shared__ double red[TPB / 32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < TPB / 32; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_trace(const double* __restrict__ part, int nblk, const double* __restrict__ totals,
+                                               double accel, double* __restrict__ out)
+{
+    __shared__ double sh[TPB];
+    double ke = block_sum_col(part, nblk, 1, 0, sh);
+    if (threadIdx.x == 0) {
+        out[0] = totals[0] + totals[1] + totals[2] + totals[3] + totals[4] + totals[5];
+        out[1] = ke / accel;
+    }
+}
+
+}  // namespace
+
+void launch_ksample(rbe_ctx* ctx, uint64_t step, cudaStream_t st)
+{
+    prof_begin(ctx, RBE_K_KSAMPLE, st);
+    int g = (ctx->c.P + TPB - 1) / TPB;
+    k_sample<<<g, TPB, 0, st>>>(ctx->c, step, ctx->kT, ctx->km, ctx->kv, ctx->status);
+    prof_end(ctx, RBE_K_KSAMPLE, st);
+}
+
+void launch_rho(rbe_ctx* ctx, int n, cudaStream_t st)
+{
+    int P = ctx->c.P;
+    int threads = ((P < 1024 ? P : 1024) + 31) / 32 * 32;
+    int chunk = (n + ctx->grid_rho - 1) / ctx->grid_rho;
+    prof_begin(ctx, RBE_K_RHO, st);
+    if (ctx->precision == RBE_MIXED)
+        k_rho<true><<<ctx->grid_rho, threads, 0, st>>>(n, chunk, ctx->c, ctx->s4, ctx->p4, ctx->km, ctx->rho_part);
+    else
+        k_rho<false><<<ctx->grid_rho, threads, 0, st>>>(n, chunk, ctx->c, ctx->s4, ctx->p4, ctx->km, ctx->rho_part);
+    prof_end(ctx, RBE_K_RHO, st);
+    prof_begin(ctx, RBE_K_RHOSUM, st);
+    double* kterms = ctx->totals + 32;
+    k_rho_sum<<<(P + TPB - 1) / TPB, TPB, 0, st>>>(ctx->grid_rho, ctx->c, ctx->rho_part, ctx->kv, ctx->rho, kterms);
+    prof_end(ctx, RBE_K_RHOSUM, st);
+}
+
+void launch_bonded(rbe_ctx* ctx, int n, const double* pos, cudaStream_t st)
+{
+    (void)n;
+    prof_begin(ctx, RBE_K_BONDED, st);
+    k_bonded<<<ctx->grid_bond, TPB, 0, st>>>(ctx->n_wmol, pos, ctx->c, ctx->kb, ctx->r0, ctx->kth, ctx->th0, ctx->F_bond,
+                                             ctx->part_bond);
+    prof_end(ctx, RBE_K_BONDED, st);
+}
+
+void launch_finalize(rbe_ctx* ctx, int n, cudaStream_t st)
+{
+    prof_begin(ctx, RBE_K_FINAL, st);
+    k_finalize<<<1, TPB, 0, st>>>(n, ctx->c, ctx->part_rbl, ctx->grid_rbl, ctx->part_q, ctx->grid_q, ctx->totals + 32,
+                                  ctx->part_bond, ctx->n_wmol > 0 ? ctx->grid_bond : 0, ctx->totals, ctx->status);
+    prof_end(ctx, RBE_K_FINAL, st);
+}
+
+void launch_kforce(rbe_ctx* ctx, int n, double* F, cudaStream_t st)
+{
+    int g = (n + TPB - 1) / TPB;
+    int nb = ctx->n_wmol > 0 ? 3 * ctx->n_wmol : 0;
+    prof_begin(ctx, RBE_K_KFORCE, st);
+    if (ctx->precision == RBE_MIXED)
+        k_kforce<true><<<g, TPB, 0, st>>>(n, ctx->c, ctx->s4, ctx->p4, ctx->perm, ctx->km, ctx->kv, ctx->rho, ctx->F_real,
+                                          ctx->totals, ctx->F_bond, nb, F);
+    else
+        k_kforce<false><<<g, TPB, 0, st>>>(n, ctx->c, ctx->s4, ctx->p4, ctx->perm, ctx->km, ctx->kv, ctx->rho, ctx->F_real,
+                                           ctx->totals, ctx->F_bond, nb, F);
+    prof_end(ctx, RBE_K_KFORCE, st);
+}
+
+void launch_vv_kick_drift(rbe_ctx* ctx, int n, double* pos, double* vel, const double* mass, const double* F, double dt,
+                          double accel, int drift, cudaStream_t st)
+{
+    prof_begin(ctx, RBE_K_VV, st);
+    k_vv<<<(n + TPB - 1) / TPB, TPB, 0, st>>>(n, pos, vel, mass, F, 0.5 * dt * accel, dt, drift);
+    prof_end(ctx, RBE_K_VV, st);
+}
+
+void launch_ke_trace(rbe_ctx* ctx, int n, const double* vel, const double* mass, double accel, double* trace_slot,
+                     cudaStream_t st)
+{
+    prof_begin(ctx, RBE_K_MISC, st);
+    k_ke<<<ctx->grid_q, TPB, 0, st>>>(n, vel, mass, ctx->ke_part);
+    prof_end(ctx, RBE_K_MISC, st);
+    prof_begin(ctx, RBE_K_MISC, st);
+    k_trace<<<1, TPB, 0, st>>>(ctx->ke_part, ctx->grid_q, ctx->totals, accel, trace_slot);
+    prof_end(ctx, RBE_K_MISC, st);
+}

@@ -1,0 +1,594 @@
+// rbe_api.cu -- host side of the C ABI declared in include/rbe.h: context,
+// parameter derivation, device memory, the launch sequence of one force step
+// and the velocity-Verlet driver.
+//
+// Launch sequence of rbe_forces on one stream (Algorithm 1, force steps):
+//   quantize+count -> scan -> scatter/sort/gather   (cell list, Sec. 2.3)
+//   k sample -> rho partials -> rho sum             (RBE, Eqs. (2.4), (2.8))
+//   RBL pair kernel                                 (Eqs. (2.10)-(2.11))
+//   [bonded water]                                  (integration force field)
+//   finalize: energies, virial, F^corr              (Eqs. (2.3), (2.12))
+//   k-space force + combination                     (Eqs. (2.9), (2.13))
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "rbe_internal.cuh"
+
+int rbl_blocks_per_sm(const rbe_ctx* ctx);
+
+namespace {
+
+const double PI = 3.14159265358979323846;
+
+struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+struct ProfState {
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t pending_a = nullptr;
+};
+
+int set_err(rbe_ctx* ctx, int code, const char* fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                         \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return set_err(ctx, RBE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));          \
+    } while (0)
+
+// Inverse-CDF thresholds of the per-axis discrete Gaussian
+// w_m = exp(-pi^2 m^2 / (alpha L^2)), |m| <= M (reading of Eqs. (2.7)-(2.8)):
+// T[m+M] = floor(2^64 * sum_{j<=m} w_j / H), saturating at 2^64-1.
+int k_truncation(double alpha, double L)
+{
+    double aL2 = alpha * L * L;
+    return (int)ceil(sqrt(aL2 * 64.0 * log(2.0)) / PI);
+}
+
+double k_thresholds(double alpha, double L, int M, uint64_t* T)
+{
+    double aL2 = alpha * L * L;
+    double c = PI * PI / aL2;
+    double H = 0.0;
+    for (int m = -M; m <= M; ++m) H += exp(-c * (double)m * (double)m);
+    double acc = 0.0;
+    for (int m = -M; m <= M; ++m) {
+        acc += exp(-c * (double)m * (double)m);
+        double v = (acc / H) * 18446744073709551616.0;
+        T[m + M] = (v >= 18446744073709551616.0) ? UINT64_MAX : (uint64_t)v;
+    }
+    return H;
+}
+
+uint64_t radius2_fixed(double r, double L)
+{
+    double invL = 1.0 / L;
+    double a = (r * invL) * 4294967296.0;
+    return (uint64_t)(a * a);
+}
+
+void refresh_consts(rbe_ctx* ctx)
+{
+    RbeConsts& c = ctx->c;
+    c.invL = 1.0 / c.L;
+    c.sqrt_alpha = sqrt(c.alpha);
+    c.two_sqrt_alpha_over_sqrt_pi = 2.0 * sqrt(c.alpha) / sqrt(PI);
+    double V = c.L * c.L * c.L;
+    c.kcoef = (c.S / (double)c.P) * 4.0 * PI * c.k_e / V;
+    c.Lfix = (float)(c.L * 2.3283064365386963e-10);
+}
+
+void free_dev(rbe_ctx* ctx)
+{
+    void* ptrs[] = {ctx->s4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
+                    ctx->F_real, ctx->F_bond, ctx->part_rbl, ctx->part_q, ctx->part_bond, ctx->kT, ctx->km, ctx->kv,
+                    ctx->rho_part, ctx->rho, ctx->totals, ctx->status, ctx->lj, ctx->dbg_ncore, ctx->dbg_nshell,
+                    ctx->dbg_core, ctx->dbg_batch, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
+                    ctx->ke_part};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    ctx->s4 = nullptr; ctx->p4 = nullptr; ctx->tm = nullptr; ctx->perm = nullptr; ctx->cell_of = nullptr;
+    ctx->slot = nullptr; ctx->cell_count = nullptr; ctx->cell_start = nullptr; ctx->F_real = nullptr;
+    ctx->F_bond = nullptr; ctx->part_rbl = nullptr; ctx->part_q = nullptr; ctx->part_bond = nullptr;
+    ctx->kT = nullptr; ctx->km = nullptr; ctx->kv = nullptr; ctx->rho_part = nullptr; ctx->rho = nullptr;
+    ctx->totals = nullptr; ctx->status = nullptr; ctx->lj = nullptr; ctx->dbg_ncore = nullptr;
+    ctx->dbg_nshell = nullptr; ctx->dbg_core = nullptr; ctx->dbg_batch = nullptr; ctx->h_pos = nullptr;
+    ctx->h_q = nullptr; ctx->h_type = nullptr; ctx->h_mol = nullptr; ctx->h_F = nullptr; ctx->ke_part = nullptr;
+    ctx->n_cap = 0; ctx->dbg_n_cap = 0; ctx->h_cap = 0;
+    for (int k = 0; k < 20; ++k) ctx->cap_atoms[k] = 0;
+}
+
+template <typename T>
+int dev_alloc(rbe_ctx* ctx, T** p, size_t count)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return set_err(ctx, RBE_ENOMEM, "cudaMalloc of %zu bytes failed: %s", sizeof(T) * count, cudaGetErrorString(e));
+    }
+    return RBE_OK;
+}
+
+int round32(double x) { return ((int)ceil(x) + 31) / 32 * 32; }
+
+// Capacities of the per-warp core and shell buffers from the density:
+// twice the mean count plus six standard deviations plus a margin.
+void auto_caps(rbe_ctx* ctx, int n)
+{
+    double rho = (double)n / (ctx->c.L * ctx->c.L * ctx->c.L);
+    double rc = ctx->c.r_c, rs = ctx->c.r_s;
+    double mc = 4.0 / 3.0 * PI * rc * rc * rc * rho;
+    double ms = 4.0 / 3.0 * PI * (rs * rs * rs - rc * rc * rc) * rho;
+    int cc = ctx->user_core_cap > 0 ? ctx->user_core_cap : round32(2.0 * mc + 6.0 * sqrt(mc) + 32.0);
+    int sc = ctx->user_shell_cap > 0 ? ctx->user_shell_cap : round32(2.0 * ms + 6.0 * sqrt(ms) + 32.0);
+    ctx->core_cap = (cc + 31) / 32 * 32;
+    ctx->shell_cap = (sc + 31) / 32 * 32;
+}
+
+// Reallocates *p only when `count` exceeds the recorded capacity *cap.
+template <typename T>
+int grow(rbe_ctx* ctx, T** p, size_t* cap, size_t count)
+{
+    if (*p && count <= *cap) return RBE_OK;
+    int rc = dev_alloc(ctx, p, count);
+    *cap = rc ? 0 : (count == 0 ? 1 : count);
+    return rc;
+}
+
+int ensure(rbe_ctx* ctx, int n)
+{
+    int dev = 0;
+    CUDA_TRY(ctx, cudaGetDevice(&dev));
+    if (ctx->device >= 0 && dev != ctx->device)
+        return set_err(ctx, RBE_EINVAL, "context was created on device %d, current device is %d", ctx->device, dev);
+    bool first = ctx->device < 0;
+    ctx->device = dev;
+    int rc;
+    if (first) {
+        CUDA_TRY(ctx, cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev));
+        // fixed-size buffers
+        int M = ctx->c.M;
+        std::vector<uint64_t> T(2 * M + 1);
+        k_thresholds(ctx->c.alpha, ctx->c.L, M, T.data());
+        if ((rc = dev_alloc(ctx, &ctx->kT, T.size()))) return rc;
+        CUDA_TRY(ctx, cudaMemcpy(ctx->kT, T.data(), sizeof(uint64_t) * T.size(), cudaMemcpyHostToDevice));
+        if ((rc = dev_alloc(ctx, &ctx->km, ctx->c.P))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->kv, ctx->c.P))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->rho, ctx->c.P))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->totals, 32 + 7 * (size_t)ctx->c.P))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->status, 1))) return rc;
+        CUDA_TRY(ctx, cudaMemset(ctx->status, 0, sizeof(int)));
+        CUDA_TRY(ctx, cudaMemset(ctx->totals, 0, sizeof(double) * (32 + 7 * (size_t)ctx->c.P)));
+        if ((rc = dev_alloc(ctx, &ctx->lj, 1))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->cell_count, ctx->ncells + 1))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->cell_start, ctx->ncells + 1))) return rc;
+        ctx->lj_dirty = 1;
+    }
+    if (ctx->lj_dirty) {
+        RbeLJ h;
+        memset(&h, 0, sizeof(h));
+        for (int a = 0; a < ctx->c.ntypes; ++a)
+            for (int b = 0; b < ctx->c.ntypes; ++b) {
+                double e = sqrt(ctx->eps[a] * ctx->eps[b]);          // Berthelot
+                double s = 0.5 * (ctx->sigma[a] + ctx->sigma[b]);    // Lorentz
+                double s6 = s * s * s * s * s * s;
+                h.c12[a * RBE_MAXT + b] = 4.0 * e * s6 * s6;
+                h.c6[a * RBE_MAXT + b] = 4.0 * e * s6;
+                double sr6 = pow(s / ctx->c.r_s, 6.0);
+                h.shift[a * RBE_MAXT + b] = ctx->c.shift_lj ? 4.0 * e * (sr6 * sr6 - sr6) : 0.0;
+            }
+        CUDA_TRY(ctx, cudaMemcpy(ctx->lj, &h, sizeof(h), cudaMemcpyHostToDevice));
+        ctx->lj_dirty = 0;
+    }
+    if (n != ctx->last_n || ctx->precision != ctx->last_precision) {
+        auto_caps(ctx, n);
+        if (rbl_smem_bytes(ctx) > 220 * 1024)
+            return set_err(ctx, RBE_ECAPACITY, "list capacities (%d core, %d shell) exceed shared memory",
+                           ctx->core_cap, ctx->shell_cap);
+        // grids (fixed for a given n and device, so every reduction order is fixed)
+        int nsm = ctx->n_sm;
+        ctx->grid_q = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+        int bps = rbl_blocks_per_sm(ctx);
+        int g = (n + RBE_WARPS_RBL - 1) / RBE_WARPS_RBL;
+        ctx->grid_rbl = g < bps * nsm ? g : bps * nsm;
+        int gr = (n + 255) / 256;
+        ctx->grid_rho = gr < 2 * nsm ? gr : 2 * nsm;
+        ctx->last_n = n;
+        ctx->last_precision = ctx->precision;
+    }
+    int gb = ctx->n_wmol > 0 ? (ctx->n_wmol + 255) / 256 : 0;
+    ctx->grid_bond = gb < 4 * ctx->n_sm ? gb : 4 * ctx->n_sm;
+    if ((rc = grow(ctx, &ctx->s4, &ctx->cap_atoms[0], n))) return rc;
+    if ((rc = grow(ctx, &ctx->p4, &ctx->cap_atoms[1], n))) return rc;
+    if ((rc = grow(ctx, &ctx->tm, &ctx->cap_atoms[2], n))) return rc;
+    if ((rc = grow(ctx, &ctx->perm, &ctx->cap_atoms[3], n))) return rc;
+    if ((rc = grow(ctx, &ctx->cell_of, &ctx->cap_atoms[4], n))) return rc;
+    if ((rc = grow(ctx, &ctx->slot, &ctx->cap_atoms[5], n))) return rc;
+    if ((rc = grow(ctx, &ctx->F_real, &ctx->cap_atoms[6], 3 * (size_t)n))) return rc;
+    if ((rc = grow(ctx, &ctx->part_rbl, &ctx->cap_atoms[7], (size_t)ctx->grid_rbl * RBE_NPART_RBL))) return rc;
+    if ((rc = grow(ctx, &ctx->part_q, &ctx->cap_atoms[8], (size_t)ctx->grid_q * RBE_NPART_Q))) return rc;
+    if ((rc = grow(ctx, &ctx->ke_part, &ctx->cap_atoms[9], (size_t)ctx->grid_q))) return rc;
+    if ((rc = grow(ctx, &ctx->part_bond, &ctx->cap_atoms[10], (size_t)(ctx->grid_bond > 0 ? ctx->grid_bond : 1)))) return rc;
+    if ((rc = grow(ctx, &ctx->rho_part, &ctx->cap_atoms[11], (size_t)ctx->grid_rho * ctx->c.P))) return rc;
+    if (ctx->n_wmol > 0 && (rc = grow(ctx, &ctx->F_bond, &ctx->cap_atoms[12], 9 * (size_t)ctx->n_wmol))) return rc;
+    ctx->n_cap = (int)ctx->cap_atoms[0];
+    if (ctx->debug) {
+        size_t cc = (size_t)(ctx->dbg_cap_core > 0 ? ctx->dbg_cap_core : 1);
+        if ((rc = grow(ctx, &ctx->dbg_ncore, &ctx->cap_atoms[13], n))) return rc;
+        if ((rc = grow(ctx, &ctx->dbg_nshell, &ctx->cap_atoms[14], n))) return rc;
+        if ((rc = grow(ctx, &ctx->dbg_core, &ctx->cap_atoms[15], (size_t)n * cc))) return rc;
+        if ((rc = grow(ctx, &ctx->dbg_batch, &ctx->cap_atoms[16], (size_t)n * ctx->c.p))) return rc;
+        ctx->dbg_n_cap = n;
+    }
+    return RBE_OK;
+}
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int forces_device(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const double* q, const int32_t* type,
+                  const int32_t* mol, double* F, cudaStream_t st)
+{
+    ctx->last_launches = 0;
+    launch_quantize_count(ctx, n, pos, q, st);
+    launch_scan(ctx, st);
+    launch_scatter_sort_gather(ctx, n, pos, q, type, mol, st);
+    launch_ksample(ctx, step, st);
+    launch_rho(ctx, n, st);
+    launch_rbl(ctx, n, step, st);
+    if (ctx->n_wmol > 0) launch_bonded(ctx, n, pos, st);
+    launch_finalize(ctx, n, st);
+    launch_kforce(ctx, n, F, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(ctx, RBE_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return RBE_OK;
+}
+
+int copy_out(rbe_ctx* ctx, double* dst, const double* src, int count, cudaStream_t st, bool* need_sync)
+{
+    if (!dst) return RBE_OK;
+    if (is_device_ptr(dst)) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDeviceToDevice, st));
+    } else {
+        CUDA_TRY(ctx, cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
+        *need_sync = true;
+    }
+    return RBE_OK;
+}
+
+int status_code(int bits)
+{
+    if (bits & RBE_ST_OVERLAP) return RBE_EOVERLAP;
+    if (bits & RBE_ST_CAPACITY) return RBE_ECAPACITY;
+    if (bits & RBE_ST_NONFINITE) return RBE_ENONFINITE;
+    if (bits & RBE_ST_NONNEUTRAL) return RBE_ENONNEUTRAL;
+    if (bits & RBE_ST_BADTYPE) return RBE_EINVAL;
+    if (bits & RBE_ST_KSAMPLE) return RBE_ECUDA;
+    return RBE_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// profiling helpers
+// ---------------------------------------------------------------------------
+void prof_begin(rbe_ctx* ctx, int kid, cudaStream_t st)
+{
+    (void)kid;
+    ctx->last_launches++;
+    if (!ctx->profiling) return;
+    ProfState* ps = (ProfState*)ctx->prof;
+    cudaEvent_t a;
+    if (!ps->pool.empty()) { a = ps->pool.back(); ps->pool.pop_back(); }
+    else cudaEventCreate(&a);
+    cudaEventRecord(a, st);
+    ps->pending_a = a;
+}
+
+void prof_end(rbe_ctx* ctx, int kid, cudaStream_t st)
+{
+    if (!ctx->profiling) return;
+    ProfState* ps = (ProfState*)ctx->prof;
+    cudaEvent_t b;
+    if (!ps->pool.empty()) { b = ps->pool.back(); ps->pool.pop_back(); }
+    else cudaEventCreate(&b);
+    cudaEventRecord(b, st);
+    ps->recs.push_back({kid, ps->pending_a, b});
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int rbe_create(rbe_ctx** out, double box_L, double alpha, double r_c, double r_s, int p, int P, uint64_t seed)
+{
+    if (!out) return RBE_EINVAL;
+    *out = nullptr;
+    if (!(box_L > 0) || !(alpha > 0) || !(r_c > 0) || !(r_s > r_c) || !(r_s <= 0.5 * box_L) || p < 1 || P < 1 ||
+        !isfinite(box_L) || !isfinite(alpha))
+        return RBE_EINVAL;
+    int n_cell = (int)floor(box_L / r_c);
+    long ncells = (long)n_cell * n_cell * n_cell;
+    if (n_cell < 1 || ncells > (1L << 26) || p > 4096 || P > (1 << 20)) return RBE_EINVAL;
+    rbe_ctx* ctx = (rbe_ctx*)calloc(1, sizeof(rbe_ctx));
+    if (!ctx) return RBE_ENOMEM;
+    ctx->prof = new ProfState();
+    RbeConsts& c = ctx->c;
+    c.L = box_L; c.alpha = alpha; c.r_c = r_c; c.r_s = r_s; c.k_e = 1.0; c.p = p; c.P = P; c.seed = seed;
+    c.n_cell = n_cell;
+    c.reach = (int)floor(r_s * (double)n_cell / box_L) + 1;
+    c.Rc2 = radius2_fixed(r_c, box_L);
+    c.Rs2 = radius2_fixed(r_s, box_L);
+    c.rs_frac2 = (float)((r_s / box_L) * (r_s / box_L) * (1.0 + 1e-4));
+    c.M = k_truncation(alpha, box_L);
+    {
+        std::vector<uint64_t> T(2 * c.M + 1);
+        double H = k_thresholds(alpha, box_L, c.M, T.data());
+        c.S = H * H * H - 1.0;
+    }
+    c.ntypes = 1;
+    c.shift_lj = 0;
+    ctx->eps[0] = 0.0;
+    ctx->sigma[0] = 1.0;
+    ctx->ncells = ncells;
+    ctx->device = -1;
+    ctx->last_n = -1;
+    ctx->last_precision = -1;
+    ctx->precision = RBE_FP64;
+    refresh_consts(ctx);
+    *out = ctx;
+    return RBE_OK;
+}
+
+int rbe_set_coulomb(rbe_ctx* ctx, double k_e)
+{
+    if (!ctx || !isfinite(k_e)) return RBE_EINVAL;
+    ctx->c.k_e = k_e;
+    refresh_consts(ctx);
+    return RBE_OK;
+}
+
+int rbe_set_lj(rbe_ctx* ctx, int ntypes, const double* eps, const double* sigma, int shift_energy)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (ntypes < 1 || ntypes > RBE_MAXT || !eps || !sigma)
+        return set_err(ctx, RBE_EINVAL, "ntypes must be in [1, %d] with eps and sigma given", RBE_MAXT);
+    for (int t = 0; t < ntypes; ++t) {
+        if (!(eps[t] >= 0) || !(sigma[t] > 0)) return set_err(ctx, RBE_EINVAL, "bad LJ parameters for type %d", t);
+        ctx->eps[t] = eps[t];
+        ctx->sigma[t] = sigma[t];
+    }
+    ctx->c.ntypes = ntypes;
+    ctx->c.shift_lj = shift_energy ? 1 : 0;
+    ctx->lj_dirty = 1;
+    return RBE_OK;
+}
+
+int rbe_set_precision(rbe_ctx* ctx, int mode)
+{
+    if (!ctx || (mode != RBE_FP64 && mode != RBE_MIXED)) return RBE_EINVAL;
+    ctx->precision = mode;
+    return RBE_OK;
+}
+
+int rbe_set_water_bonds(rbe_ctx* ctx, int n_mol, double k_b, double r0, double k_theta, double theta0)
+{
+    if (!ctx || n_mol < 0) return RBE_EINVAL;
+    ctx->n_wmol = n_mol;
+    ctx->kb = k_b; ctx->r0 = r0; ctx->kth = k_theta; ctx->th0 = theta0;
+    return RBE_OK;
+}
+
+int rbe_set_capacity(rbe_ctx* ctx, int core_cap, int shell_cap)
+{
+    if (!ctx || core_cap < 0 || shell_cap < 0) return RBE_EINVAL;
+    ctx->user_core_cap = core_cap;
+    ctx->user_shell_cap = shell_cap;
+    ctx->last_n = -1;
+    return RBE_OK;
+}
+
+int rbe_set_debug(rbe_ctx* ctx, int on, int cap_core)
+{
+    if (!ctx || cap_core < 0) return RBE_EINVAL;
+    ctx->debug = on ? 1 : 0;
+    ctx->dbg_cap_core = cap_core;
+    ctx->dbg_n_cap = 0;
+    return RBE_OK;
+}
+
+int rbe_set_profiling(rbe_ctx* ctx, int on)
+{
+    if (!ctx) return RBE_EINVAL;
+    ctx->profiling = on ? 1 : 0;
+    return RBE_OK;
+}
+
+int rbe_forces(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const double* q, const int32_t* type,
+               const int32_t* mol, double* F, double* energy, double* virial, void* cuda_stream)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (n < 1 || !pos || !q || !F) return set_err(ctx, RBE_EINVAL, "n >= 1 and pos, q, F are required");
+    if (ctx->n_wmol > 0 && 3 * ctx->n_wmol > n)
+        return set_err(ctx, RBE_EINVAL, "water bonds cover %d atoms but n = %d", 3 * ctx->n_wmol, n);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc = ensure(ctx, n);
+    if (rc) return rc;
+    bool dev_in = is_device_ptr(pos);
+    if (dev_in != is_device_ptr(q) || dev_in != is_device_ptr(F) || (type && dev_in != is_device_ptr(type)) ||
+        (mol && dev_in != is_device_ptr(mol)))
+        return set_err(ctx, RBE_EINVAL, "pos, q, type, mol and F must all be device or all host pointers");
+    bool need_sync = false;
+    if (dev_in) {
+        rc = forces_device(ctx, step, n, pos, q, type, mol, F, st);
+    } else {
+        if (n > ctx->h_cap) {
+            if ((rc = dev_alloc(ctx, &ctx->h_pos, 3 * (size_t)n))) return rc;
+            if ((rc = dev_alloc(ctx, &ctx->h_q, n))) return rc;
+            if ((rc = dev_alloc(ctx, &ctx->h_type, n))) return rc;
+            if ((rc = dev_alloc(ctx, &ctx->h_mol, n))) return rc;
+            if ((rc = dev_alloc(ctx, &ctx->h_F, 3 * (size_t)n))) return rc;
+            ctx->h_cap = n;
+        }
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_q, q, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        if (type) CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_type, type, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        if (mol) CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_mol, mol, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        rc = forces_device(ctx, step, n, ctx->h_pos, ctx->h_q, type ? ctx->h_type : nullptr, mol ? ctx->h_mol : nullptr,
+                           ctx->h_F, st);
+        if (rc) return rc;
+        CUDA_TRY(ctx, cudaMemcpyAsync(F, ctx->h_F, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+        need_sync = true;
+    }
+    if (rc) return rc;
+    if ((rc = copy_out(ctx, energy, ctx->totals, RBE_NE, st, &need_sync))) return rc;
+    if ((rc = copy_out(ctx, virial, ctx->totals + 6, RBE_NW, st, &need_sync))) return rc;
+    if (need_sync) CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    return RBE_OK;
+}
+
+int rbe_step(rbe_ctx* ctx, uint64_t step0, int nsteps, double dt, double accel, int n, double* pos, double* vel,
+             const double* mass, const double* q, const int32_t* type, const int32_t* mol, double* F,
+             double* energy_trace, void* cuda_stream)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (nsteps < 0 || n < 1 || !pos || !vel || !mass || !q || !F || !(dt > 0) || !(accel > 0))
+        return set_err(ctx, RBE_EINVAL, "bad rbe_step arguments");
+    if (!is_device_ptr(pos) || !is_device_ptr(vel) || !is_device_ptr(mass) || !is_device_ptr(F))
+        return set_err(ctx, RBE_EINVAL, "rbe_step takes device pointers");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc = ensure(ctx, n);
+    if (rc) return rc;
+    for (int k = 0; k < nsteps; ++k) {
+        launch_vv_kick_drift(ctx, n, pos, vel, mass, F, dt, accel, 1, st);
+        rc = forces_device(ctx, step0 + (uint64_t)k + 1, n, pos, q, type, mol, F, st);
+        if (rc) return rc;
+        launch_vv_kick_drift(ctx, n, pos, vel, mass, F, dt, accel, 0, st);
+        if (energy_trace) launch_ke_trace(ctx, n, vel, mass, accel, energy_trace + 2 * (size_t)k, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(ctx, RBE_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return RBE_OK;
+}
+
+int rbe_sync_status(rbe_ctx* ctx, void* cuda_stream)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (!ctx->status) return RBE_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int bits = 0;
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    CUDA_TRY(ctx, cudaMemcpy(&bits, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(ctx, cudaMemset(ctx->status, 0, sizeof(int)));
+    int code = status_code(bits);
+    if (code) set_err(ctx, code, "device status bits 0x%x", bits);
+    return code;
+}
+
+int rbe_get_lists(rbe_ctx* ctx, int n, int32_t* n_core, int32_t* n_shell, int32_t* core, int32_t* batch,
+                  void* cuda_stream)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (!ctx->dbg_ncore || n > ctx->dbg_n_cap) return set_err(ctx, RBE_EINVAL, "no recorded lists for n = %d", n);
+    CUDA_TRY(ctx, cudaStreamSynchronize((cudaStream_t)cuda_stream));
+    if (n_core) CUDA_TRY(ctx, cudaMemcpy(n_core, ctx->dbg_ncore, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    if (n_shell) CUDA_TRY(ctx, cudaMemcpy(n_shell, ctx->dbg_nshell, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    if (core && ctx->dbg_cap_core > 0)
+        CUDA_TRY(ctx, cudaMemcpy(core, ctx->dbg_core, sizeof(int) * (size_t)n * ctx->dbg_cap_core, cudaMemcpyDeviceToHost));
+    if (batch) CUDA_TRY(ctx, cudaMemcpy(batch, ctx->dbg_batch, sizeof(int) * (size_t)n * ctx->c.p, cudaMemcpyDeviceToHost));
+    return RBE_OK;
+}
+
+int rbe_get_kspace(rbe_ctx* ctx, int32_t* m, double* rho, void* cuda_stream)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (!ctx->km) return set_err(ctx, RBE_EINVAL, "no step has run");
+    CUDA_TRY(ctx, cudaStreamSynchronize((cudaStream_t)cuda_stream));
+    if (m) {
+        std::vector<int4> h(ctx->c.P);
+        CUDA_TRY(ctx, cudaMemcpy(h.data(), ctx->km, sizeof(int4) * ctx->c.P, cudaMemcpyDeviceToHost));
+        for (int l = 0; l < ctx->c.P; ++l) { m[3 * l] = h[l].x; m[3 * l + 1] = h[l].y; m[3 * l + 2] = h[l].z; }
+    }
+    if (rho) CUDA_TRY(ctx, cudaMemcpy(rho, ctx->rho, sizeof(double2) * ctx->c.P, cudaMemcpyDeviceToHost));
+    return RBE_OK;
+}
+
+int rbe_get_info(rbe_ctx* ctx, double* out, int nout)
+{
+    if (!ctx || !out) return RBE_EINVAL;
+    double v[7] = {(double)ctx->c.n_cell, (double)ctx->c.reach, (double)ctx->c.M, ctx->c.S, (double)ctx->core_cap,
+                   (double)ctx->shell_cap, (double)ctx->last_launches};
+    for (int k = 0; k < nout && k < 7; ++k) out[k] = v[k];
+    return RBE_OK;
+}
+
+int rbe_get_profile(rbe_ctx* ctx, double* ms, int64_t* launches, int reset, void* cuda_stream)
+{
+    if (!ctx) return RBE_EINVAL;
+    CUDA_TRY(ctx, cudaStreamSynchronize((cudaStream_t)cuda_stream));
+    ProfState* ps = (ProfState*)ctx->prof;
+    for (auto& r : ps->recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            ctx->prof_ms[r.kid] += t;
+            ctx->prof_n[r.kid] += 1;
+        }
+        ps->pool.push_back(r.a);
+        ps->pool.push_back(r.b);
+    }
+    ps->recs.clear();
+    for (int k = 0; k < RBE_NKERNELS; ++k) {
+        if (ms) ms[k] = ctx->prof_ms[k];
+        if (launches) launches[k] = ctx->prof_n[k];
+    }
+    if (reset)
+        for (int k = 0; k < RBE_NKERNELS; ++k) { ctx->prof_ms[k] = 0.0; ctx->prof_n[k] = 0; }
+    return RBE_OK;
+}
+
+const char* rbe_last_error(const rbe_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+void rbe_destroy(rbe_ctx* ctx)
+{
+    if (!ctx) return;
+    if (ctx->device >= 0) {
+        ProfState* ps = (ProfState*)ctx->prof;
+        for (auto& r : ps->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto e : ps->pool) cudaEventDestroy(e);
+        free_dev(ctx);
+    }
+    delete (ProfState*)ctx->prof;
+    free(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// rbe_internal.cuh -- shared declarations of the IRBE CUDA library (sm_103a).
+//
+// Data layout in HBM (all device buffers owned by rbe_ctx, sized for n_cap
+// atoms and grown on demand):
+//   sorted order = atoms ordered by (canonical cell, caller index), built by a
+//   counting sort each step (cells of edge L/floor(L/r_c), Sec. 2.3).
+//   s4   [n]  uint4   fixed-point (sx, sy, sz) and q as FP32 bits   (16 B/atom)
+//   p4   [n]  double4_32a wrapped (x, y, z) and q in FP64              (32 B/atom)
+//   tm   [n]  int2    (type, mol)                                   (8 B/atom)
+//   perm [n]  int     sorted index -> caller index
+//   F_real [3n] double core + weighted shell force, sorted order
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rbe.h"
+
+#define RBE_MAXT 16
+#define RBE_WARPS_RBL 8          // warps per block of the pair kernel
+#define RBE_NPART_RBL 12         // Ec, Elj, Ex, W[6], Fsum[3]
+#define RBE_NPART_Q 3            // sum q^2, sum q, sum |q|
+
+// status bits latched on the device
+#define RBE_ST_OVERLAP   1
+#define RBE_ST_CAPACITY  2
+#define RBE_ST_NONNEUTRAL 4
+#define RBE_ST_NONFINITE 8
+#define RBE_ST_KSAMPLE   16
+#define RBE_ST_BADTYPE   32
+
+struct RbeConsts {
+    double L, invL, alpha, sqrt_alpha, two_sqrt_alpha_over_sqrt_pi, k_e;
+    double r_c, r_s;
+    double S;             // H^3 - 1
+    double kcoef;         // (S/P) 4 pi k_e / V  (c_l = kcoef / |k_l|^2)
+    float Lfix;           // L * 2^-32 (fixed-point unit in length, FP32)
+    uint64_t Rc2, Rs2;    // squared radii in fixed-point units
+    float rs_frac2;       // (r_s/L)^2 * (1 + 1e-5), for conservative culling
+    int n_cell, reach;
+    int p, P;
+    uint64_t seed;
+    int M;                // k truncation
+    int ntypes;
+    int shift_lj;
+};
+
+// LJ pair table (device): c12 = 4 eps sig^12, c6 = 4 eps sig^6, shift
+struct RbeLJ {
+    double c12[RBE_MAXT * RBE_MAXT];
+    double c6[RBE_MAXT * RBE_MAXT];
+    double shift[RBE_MAXT * RBE_MAXT];
+};
+
+struct rbe_ctx {
+    RbeConsts c;
+    int precision;
+    int debug, dbg_cap_core;
+    int user_core_cap, user_shell_cap;
+    int core_cap, shell_cap;
+    int profiling;
+    double eps[RBE_MAXT], sigma[RBE_MAXT];
+    // water bonds
+    int n_wmol;
+    double kb, r0, kth, th0;
+    char err[512];
+    int device;
+    // device buffers
+    int n_cap;
+    long ncells;
+    uint4* s4;
+    double4_32a* p4;
+    int2* tm;
+    int* perm;
+    int* cell_of;
+    int* slot;
+    int* cell_count;     // [ncells + 1]
+    int* cell_start;     // [ncells + 1]
+    double* F_real;      // [3n] sorted
+    double* F_bond;      // [3n] caller order
+    double* part_rbl;    // [grid_rbl * 12]
+    double* part_q;      // [grid_q * 3]
+    double* part_bond;   // [grid_bond]
+    int grid_rbl, grid_q, grid_rho, grid_bond;
+    uint64_t* kT;        // [2M+1] inverse-CDF thresholds
+    int4* km;            // [P] m
+    double4_32a* kv;         // [P] kx, ky, kz, c_l
+    double2* rho_part;   // [grid_rho * P]
+    double2* rho;        // [P]
+    double* totals;      // [32]: E[6], W[6], corr[3], spare
+    int* status;         // [1]
+    RbeLJ* lj;           // device copy
+    int lj_dirty;
+    // debug
+    int* dbg_ncore;
+    int* dbg_nshell;
+    int* dbg_core;
+    int* dbg_batch;
+    int dbg_n_cap;
+    // host staging for host-pointer calls
+    double* h_pos; double* h_q; int* h_type; int* h_mol; double* h_F;
+    int h_cap;
+    double* ke_part;     // [grid_q] kinetic energy partials (rbe_step)
+    // profiling
+    void* prof;          // std::vector of event records (C++ side)
+    double prof_ms[RBE_NKERNELS];
+    int64_t prof_n[RBE_NKERNELS];
+    int last_launches;
+    int n_sm, last_n, last_precision;
+    size_t cap_atoms[20];
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 64x64
+// multiplies with the published multipliers and Weyl key increments.
+__device__ __forceinline__ void philox4x64_10(uint64_t x0, uint64_t x1, uint64_t x2, uint64_t x3,
+                                              uint64_t k0, uint64_t k1, uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t hi0 = __umul64hi(M0, x0), lo0 = M0 * x0;
+        uint64_t hi1 = __umul64hi(M1, x2), lo1 = M1 * x2;
+        uint64_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+// Fractional coordinate and 32-bit fixed-point code of x (identical IEEE
+// operations on host and device: the products are explicitly rounded so that
+// no multiply-add contraction changes them).
+__device__ __forceinline__ void wrap_fixed(double x, double invL, double L, double& xw, uint32_t& s)
+{
+    double t = __dmul_rn(x, invL);
+    double f = __dsub_rn(t, floor(t));
+    if (f >= 1.0) f = 0.0;
+    s = (uint32_t)(unsigned long long)__dmul_rn(f, 4294967296.0);
+    xw = __dmul_rn(f, L);
+}
+
+__device__ __forceinline__ uint32_t cell_of_fixed(uint32_t s, int n_cell)
+{
+    return (uint32_t)(((uint64_t)s * (uint64_t)n_cell) >> 32);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void latch_status(int* status, int bit) { atomicOr(status, bit); }
+
+// ---------------------------------------------------------------------------
+// kernel launchers (each returns the number of kernels enqueued)
+// ---------------------------------------------------------------------------
+struct Launch;   // profiling helper (rbe_api.cu)
+void prof_begin(rbe_ctx* ctx, int kid, cudaStream_t st);
+void prof_end(rbe_ctx* ctx, int kid, cudaStream_t st);
+
+// cells / sort (k_cells.cu)
+void launch_quantize_count(rbe_ctx* ctx, int n, const double* pos, const double* q, cudaStream_t st);
+void launch_scan(rbe_ctx* ctx, cudaStream_t st);
+void launch_scatter_sort_gather(rbe_ctx* ctx, int n, const double* pos, const double* q,
+                                const int32_t* type, const int32_t* mol, cudaStream_t st);
+// pair kernel (k_rbl.cu)
+void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st);
+// Fourier part and finalisation (k_kspace.cu)
+void launch_ksample(rbe_ctx* ctx, uint64_t step, cudaStream_t st);
+void launch_rho(rbe_ctx* ctx, int n, cudaStream_t st);
+void launch_bonded(rbe_ctx* ctx, int n, const double* pos, cudaStream_t st);
+void launch_finalize(rbe_ctx* ctx, int n, cudaStream_t st);
+void launch_kforce(rbe_ctx* ctx, int n, double* F, cudaStream_t st);
+void launch_vv_kick_drift(rbe_ctx* ctx, int n, double* pos, double* vel, const double* mass,
+                          const double* F, double dt, double accel, int drift, cudaStream_t st);
+void launch_ke_trace(rbe_ctx* ctx, int n, const double* vel, const double* mass, double accel,
+                     double* trace_slot, cudaStream_t st);
+int rbl_smem_bytes(const rbe_ctx* ctx);

@@ -1,0 +1,187 @@
+"""Thin ctypes binding of librbe.so (include/rbe.h).
+
+Argument marshalling only: every step of the force evaluation runs in the
+library's CUDA kernels.  Tensors are passed by data pointer; the current torch
+CUDA stream is used unless a stream is given.  Importing this module fails
+loudly when the library is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librbe.so")
+
+OK, EINVAL, ENONNEUTRAL, EOVERLAP, ENONFINITE, ECAPACITY, ECUDA, ENOMEM = 0, -1, -2, -3, -4, -5, -6, -7
+FP64, MIXED = 0, 1
+NE, NW = 6, 6
+E_REAL, E_KSPACE, E_SELF, E_LJ, E_EXCL, E_BOND = range(6)
+KERNELS = ["quantize", "scan", "scatter", "sort", "gather", "ksample", "rho", "rhosum", "rbl", "bonded",
+           "finalize", "kforce", "vv", "misc"]
+EXPORTS = ["rbe_create", "rbe_set_coulomb", "rbe_set_lj", "rbe_set_precision", "rbe_set_water_bonds",
+           "rbe_set_capacity", "rbe_forces", "rbe_step", "rbe_sync_status", "rbe_set_debug", "rbe_get_lists",
+           "rbe_get_kspace", "rbe_get_info", "rbe_set_profiling", "rbe_get_profile", "rbe_last_error",
+           "rbe_destroy"]
+
+
+class RbeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rbe error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise RuntimeError(f"librbe.so not found at {path}: build it with paper_2204_13595_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, d, i, u64, i32p = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p
+    L.rbe_create.argtypes = [ctypes.POINTER(vp), d, d, d, d, i, i, u64]
+    L.rbe_set_coulomb.argtypes = [vp, d]
+    L.rbe_set_lj.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(d), i]
+    L.rbe_set_precision.argtypes = [vp, i]
+    L.rbe_set_water_bonds.argtypes = [vp, i, d, d, d, d]
+    L.rbe_set_capacity.argtypes = [vp, i, i]
+    L.rbe_forces.argtypes = [vp, u64, i, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rbe_step.argtypes = [vp, u64, i, d, d, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rbe_sync_status.argtypes = [vp, vp]
+    L.rbe_set_debug.argtypes = [vp, i, i]
+    L.rbe_get_lists.argtypes = [vp, i, vp, vp, vp, vp, vp]
+    L.rbe_get_kspace.argtypes = [vp, vp, vp, vp]
+    L.rbe_get_info.argtypes = [vp, ctypes.POINTER(d), i]
+    L.rbe_set_profiling.argtypes = [vp, i]
+    L.rbe_get_profile.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64), i, vp]
+    L.rbe_last_error.argtypes = [vp]
+    L.rbe_last_error.restype = ctypes.c_char_p
+    L.rbe_destroy.argtypes = [vp]
+    L.rbe_destroy.restype = None
+    return L
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Context:
+    """One IRBE context (box, alpha, r_c, r_s, p, P, seed) -- rbe_create."""
+
+    def __init__(self, L, alpha, r_c, r_s, p, P, seed, k_e=1.0, eps=None, sigma=None, shift_lj=False,
+                 precision=FP64):
+        self.L = lib()
+        h = ctypes.c_void_p()
+        rc = self.L.rbe_create(ctypes.byref(h), L, alpha, r_c, r_s, p, P, seed)
+        if rc != OK or not h.value:
+            raise RbeError(rc, "rbe_create rejected the parameters")
+        self.h = h
+        self.p, self.P = p, P
+        self._check(self.L.rbe_set_coulomb(self.h, k_e))
+        if eps is not None:
+            e = (ctypes.c_double * len(eps))(*eps)
+            s = (ctypes.c_double * len(sigma))(*sigma)
+            self._check(self.L.rbe_set_lj(self.h, len(eps), e, s, int(shift_lj)))
+        self.set_precision(precision)
+
+    @classmethod
+    def for_system(cls, s, precision=FP64, seed=None):
+        ctx = cls(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, s.seed if seed is None else seed, k_e=s.k_e,
+                  eps=s.eps, sigma=s.sigma, precision=precision)
+        if s.n_water_mol:
+            ctx.set_water_bonds(s.n_water_mol, *s.bonds)
+        return ctx
+
+    def _check(self, rc):
+        if rc != OK:
+            raise RbeError(rc, self.L.rbe_last_error(self.h).decode(errors="replace"))
+        return rc
+
+    def set_precision(self, mode):
+        self._check(self.L.rbe_set_precision(self.h, mode))
+
+    def set_water_bonds(self, n_mol, kb, r0, kth, th0):
+        self._check(self.L.rbe_set_water_bonds(self.h, n_mol, kb, r0, kth, th0))
+
+    def set_capacity(self, core, shell):
+        self._check(self.L.rbe_set_capacity(self.h, core, shell))
+
+    def set_debug(self, on, cap_core=0):
+        self._check(self.L.rbe_set_debug(self.h, int(on), cap_core))
+
+    def set_profiling(self, on):
+        self._check(self.L.rbe_set_profiling(self.h, int(on)))
+
+    def forces(self, step, pos, q, typ, mol, F, energy=None, virial=None, stream=None):
+        """rbe_forces; all of pos, q, typ, mol, F on the device or all on the host."""
+        n = int(pos.shape[0])
+        st = _stream(stream) if not isinstance(pos, np.ndarray) else (stream or 0)
+        return self._check(self.L.rbe_forces(self.h, step, n, _ptr(pos), _ptr(q), _ptr(typ), _ptr(mol), _ptr(F),
+                                             _ptr(energy), _ptr(virial), st))
+
+    def step(self, step0, nsteps, dt, accel, pos, vel, mass, q, typ, mol, F, trace=None, stream=None):
+        n = int(pos.shape[0])
+        return self._check(self.L.rbe_step(self.h, step0, nsteps, dt, accel, n, _ptr(pos), _ptr(vel), _ptr(mass),
+                                           _ptr(q), _ptr(typ), _ptr(mol), _ptr(F), _ptr(trace), _stream(stream)))
+
+    def sync_status(self, stream=None):
+        return self.L.rbe_sync_status(self.h, _stream(stream))
+
+    def get_lists(self, n, cap_core, stream=None):
+        n_core = np.zeros(n, np.int32)
+        n_shell = np.zeros(n, np.int32)
+        core = np.zeros((n, max(cap_core, 1)), np.int32)
+        batch = np.zeros((n, self.p), np.int32)
+        self._check(self.L.rbe_get_lists(self.h, n, _ptr(n_core), _ptr(n_shell), _ptr(core) if cap_core else None,
+                                         _ptr(batch), _stream(stream)))
+        return dict(n_core=n_core, n_shell=n_shell, core=core[:, :cap_core], batch=batch)
+
+    def get_kspace(self, stream=None):
+        m = np.zeros((self.P, 3), np.int32)
+        rho = np.zeros((self.P, 2))
+        self._check(self.L.rbe_get_kspace(self.h, _ptr(m), _ptr(rho), _stream(stream)))
+        return m, rho[:, 0] + 1j * rho[:, 1]
+
+    def info(self):
+        out = (ctypes.c_double * 7)()
+        self._check(self.L.rbe_get_info(self.h, out, 7))
+        keys = ["n_cell", "reach", "M", "S", "core_cap", "shell_cap", "launches"]
+        return {k: out[i] for i, k in enumerate(keys)}
+
+    def profile(self, reset=True, stream=None):
+        ms = (ctypes.c_double * len(KERNELS))()
+        nl = (ctypes.c_int64 * len(KERNELS))()
+        self._check(self.L.rbe_get_profile(self.h, ms, nl, int(reset), _stream(stream)))
+        return {k: (ms[i], nl[i]) for i, k in enumerate(KERNELS)}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.rbe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
