@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(TPB) k_sort_cells(long m, const int* __restric
 __global__ void __launch_bounds__(TPB) k_gather(int n, const int* __restrict__ perm, const double* __restrict__ pos,
                                                 const double* __restrict__ q, const int32_t* __restrict__ type,
                                                 const int32_t* __restrict__ mol, RbeConsts c, uint4* __restrict__ s4,
-                                                double4_32a* __restrict__ p4, int2* __restrict__ tm,
+                                                float4* __restrict__ f4, double4_32a* __restrict__ p4, int2* __restrict__ tm,
                                                 int* __restrict__ status)
 {
     int k = blockIdx.x * TPB + threadIdx.x;
@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(TPB) k_gather(int n, const int* __restrict__ p
     double qi = q[i];
     float qf = (float)qi;
     s4[k] = make_uint4(sx, sy, sz, __float_as_uint(qf));
+    f4[k] = make_float4((float)xw, (float)yw, (float)zw, qf);
     p4[k] = make_double4_32a(xw, yw, zw, qi);
     int t = type ? type[i] : 0;
     if (t < 0 || t >= c.ntypes) {
@@ -175,6 +176,7 @@ void launch_scatter_sort_gather(rbe_ctx* ctx, int n, const double* pos, const do
     k_sort_cells<<<(unsigned)((ctx->ncells + TPB - 1) / TPB), TPB, 0, st>>>(ctx->ncells, ctx->cell_start, ctx->perm);
     prof_end(ctx, RBE_K_SORT, st);
     prof_begin(ctx, RBE_K_GATHER, st);
-    k_gather<<<g, TPB, 0, st>>>(n, ctx->perm, pos, q, type, mol, ctx->c, ctx->s4, ctx->p4, ctx->tm, ctx->status);
+    k_gather<<<g, TPB, 0, st>>>(n, ctx->perm, pos, q, type, mol, ctx->c, ctx->s4, ctx->f4, ctx->p4, ctx->tm,
+                                 ctx->status);
     prof_end(ctx, RBE_K_GATHER, st);
 }

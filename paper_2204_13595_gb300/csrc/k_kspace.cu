@@ -317,7 +317,8 @@ __global__ void __launch_bounds__(TPB) k_kforce(int n, RbeConsts c, const uint4*
     const double qi = MIXED ? (double)p4[i].w : pi.w;
     const int gi = perm[i];
     for (int a = 0; a < 3; ++a) {
-        double v = F_real[3 * (size_t)i + a] - totals[12 + a] - qi * f[a];
+        double fr = MIXED ? (double)reinterpret_cast<const float*>(F_real)[3 * (size_t)i + a] : F_real[3 * (size_t)i + a];
+        double v = fr - totals[12 + a] - qi * f[a];
         if (gi < n_bonded_atoms) v += F_bond[3 * (size_t)gi + a];
         F[3 * (size_t)gi + a] = v;
     }

@@ -1,33 +1,47 @@
 // k_rbl.cu -- random batch list (RBL) real-space kernel, Sec. 2.3.
 //
-// One warp per atom i (sorted order), fused:
-//   1. list construction: the warp walks the rows of the cell stencil of
-//      Sec. 2.3 (reach floor(r_s/w)+1 cells, w the cell edge) in canonical
-//      (ascending cell, atom index) order; each row is one or two contiguous
-//      ranges of the cell-sorted arrays, trimmed per atom to the cells that
-//      can hold a point within r_s.  Candidates are classified by exact
-//      integer squared distance on the fixed-point coordinates into the core
-//      C(i) (r <= r_c) and shell S(i) (r_c < r <= r_s) and appended, in
-//      order, to per-warp shared-memory buffers (ballot + popc ranks);
+// Work unit = the atoms of G consecutive cells of one x-row of the cell grid
+// (cells of edge L/floor(L/r_c), the grid of Sec. 2.3).  A block takes units
+// round-robin; for each unit it stages, in shared memory, the FP32 positions
+// of every atom in the union of the unit's stencils: (2R+1)^2 rows of G+2R
+// cells, R = floor(r_s/w)+1 (Sec. 2.3's stencil reach).  Each warp then owns
+// one atom i of the unit at a time:
+//   1. list construction: the warp walks i's stencil rows in canonical order
+//      (ascending wrapped cell index, then atom index), each row trimmed to
+//      the cells that can hold a point within r_s; every row is one or two
+//      contiguous ranges of the staged arrays with a fixed periodic image
+//      shift.  Candidates are classified into the core C(i) (r <= r_c) and
+//      the shell S(i) (r_c < r <= r_s) by an FP32 distance whose rounding is
+//      bounded on the host; candidates inside that bound of r_c or r_s, and
+//      r ~ 0, are decided by the exact integer squared distance of the 32-bit
+//      fixed-point coordinates, so the sets equal the exact-integer
+//      definition bit for bit.  Members are appended in order to per-warp
+//      shared buffers (ballot + popc ranks).
 //   2. shell batch: if N_S > p, Floyd's algorithm draws p distinct ordinals
 //      in [0, N_S) from Philox words at counter (i, k/4, step, 1); otherwise
-//      the batch is all of S(i) with weight 1 (Algorithm 1, shell step);
-//   3. pair forces f_ij of Eq. (2.10) over C(i) (weight 1) and B(i) (weight
+//      the batch is all of S(i) with weight 1 (Algorithm 1, shell step).
+//   3. pair terms f_ij of Eq. (2.10) over C(i) (weight 1) and B(i) (weight
 //      N_S/p, Eq. (2.11)); same-molecule pairs take the Ewald exclusion
 //      correction instead of erfc + LJ.
+// A unit whose staged region exceeds the shared capacity reads the same
+// ranges from global memory instead (identical results, slower).
 // Outputs: F_real (core + weighted shell, before the momentum correction of
-// Eq. (2.13)) per sorted atom, and per-block partial sums of the real-space
-// energies, the virial and the net force (deterministic fixed-order sums).
+// Eq. (2.13)) per sorted atom -- FP64 on the FP64 path, FP32 on the mixed
+// path -- and per-block partial sums of the real-space energies, the virial
+// and the net force in a fixed order.
 #include <math.h>
 
 #include "rbe_internal.cuh"
 
 namespace {
 
+constexpr int WARPS = RBE_WARPS_RBL;
+
 struct RblArgs {
     int n;
     uint64_t step;
     const uint4* __restrict__ s4;
+    const float4* __restrict__ f4;
     const double4_32a* __restrict__ p4;
     const int2* __restrict__ tm;
     const int* __restrict__ perm;
@@ -37,7 +51,8 @@ struct RblArgs {
     double* __restrict__ part;
     int* __restrict__ status;
     RbeConsts c;
-    int core_cap, shell_cap, p_pad;
+    RblGeom g;
+    int core_cap, shell_cap;
     int debug, dbg_cap;
     int* __restrict__ dbg_ncore;
     int* __restrict__ dbg_nshell;
@@ -45,326 +60,608 @@ struct RblArgs {
     int* __restrict__ dbg_batch;
 };
 
-// Ascending k-th distinct cell of the stencil along one axis and its offset
-// d in [-R, R] from the atom's cell c (ring of nc cells).
-__device__ __forceinline__ void axis_cell(int k, int c, int R, int nc, bool full, int& cell, int& off)
+// Per-row description of the staged region of the current unit (64 bytes).
+struct __align__(16) RowInfo {
+    int zc, yc;            // wrapped cell coordinates of the row
+    float shy, shz;        // periodic image shift of the row (0 or +-L)
+    int sbase;             // first staged slot of the row
+    int ul;                // first unwrapped x cell staged
+    int goff[3];           // global - staged index offset for u < 0, 0 <= u < nc, u >= nc
+    float zs, ys;          // sign of the row's z / y cell offset from the unit
+    float zb, yb;          // slab boundary (fraction of L) giving the yz gap
+    int pad;
+};
+static_assert(sizeof(RowInfo) == 64, "RowInfo layout");
+
+// Shared-memory layout of k_rbl; every section starts on a 16-byte boundary.
+struct SmemLayout {
+    size_t rows, cellpos, lj, warps, wbytes, total;
+    int ga;                // atoms whose Philox words are made in one warp pass
+};
+
+__host__ __device__ inline size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline SmemLayout smem_layout(const RblGeom& g, int nt2, int p, int core_cap, int shell_cap)
 {
-    if (full) { cell = k; off = 0; return; }
-    if (c - R < 0) {
-        cell = (k <= c + R) ? k : (c - R + nc + (k - (c + R + 1)));
-    } else if (c + R >= nc) {
-        cell = (k <= c + R - nc) ? k : (c - R + (k - (c + R - nc + 1)));
-    } else {
-        cell = c - R + k;
-    }
-    int d = cell - c;
+    SmemLayout L;
+    const int p_pad = (p + 3) & ~3;
+    const int nbk = p_pad / 4;
+    L.ga = nbk >= 32 ? 1 : 32 / nbk;
+    size_t o = up16(sizeof(float4) * (size_t)g.cap_stage);
+    L.rows = o;
+    o = up16(o + sizeof(RowInfo) * (size_t)g.nrows);
+    L.cellpos = o;
+    o = up16(o + sizeof(int) * (size_t)g.nrows * (size_t)(g.cells_per_row + 1));
+    L.lj = o;
+    o = up16(o + sizeof(double) * 3 * (size_t)nt2);
+    L.warps = o;
+    L.wbytes = up16(sizeof(uint64_t) * (size_t)p_pad * L.ga + sizeof(int) * (size_t)(core_cap + shell_cap + p_pad));
+    L.total = o + L.wbytes * WARPS;
+    return L;
+}
+
+__device__ __forceinline__ int wrapc(int u, int nc) { return u < 0 ? u + nc : (u >= nc ? u - nc : u); }
+
+// Unwrapped coordinate of the k-th stencil row around cell c in ascending
+// wrapped order (ring of nc cells, 2R+1 < nc distinct rows).
+__device__ __forceinline__ int ring_row(int k, int c, int R, int nc)
+{
+    int lo = c - R;
+    int w = (lo < 0) ? ((k <= c + R) ? k : lo + nc + (k - (c + R + 1)))
+                     : ((c + R >= nc) ? ((k <= c + R - nc) ? k : lo + (k - (c + R - nc + 1))) : lo + k);
+    int d = w - c;
     if (d > R) d -= nc;
     if (d < -R) d += nc;
-    off = d;
+    return c + d;
 }
 
-// Distance (fraction of L) from fractional coordinate f in cell c to the
-// slab of the cell at offset d (unwrapped): a lower bound for any atom there.
-__device__ __forceinline__ float axis_gap(float f, int c, int d, int nc, bool full)
+// Exact squared distance of the fixed-point codes (reading of the sets C, S).
+__device__ __forceinline__ unsigned long long d2_exact(uint4 a, uint4 b)
 {
-    if (full || d == 0) return 0.0f;
-    float g = (d > 0) ? (float)(c + d) / (float)nc - f : f - (float)(c + d + 1) / (float)nc;
-    return g > 0.0f ? g : 0.0f;
+    int dx = (int)(b.x - a.x), dy = (int)(b.y - a.y), dz = (int)(b.z - a.z);
+    return (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
+           (unsigned long long)((long long)dz * dz);
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(RBE_WARPS_RBL * 32) k_rbl(RblArgs a)
+// floor(u * n / 2^64) for n < 2^32: a uniform integer in [0, n) from a 64-bit word.
+__device__ __forceinline__ uint32_t uniform_below(uint64_t u, uint32_t n)
+{
+    uint64_t lo = (uint64_t)(uint32_t)u * n;
+    uint64_t hi = (uint64_t)(uint32_t)(u >> 32) * n;
+    return (uint32_t)((hi + (lo >> 32)) >> 32);
+}
+
+// Classification of one canonical segment [beg, end) of the source array:
+// FP32 distance with exact integer decision inside the rounding bands.
+template <bool SMALL>
+__device__ __forceinline__ void classify(const float4* __restrict__ src, int beg, int end, int goff, float xie,
+                                         float yie, float zie, const RblArgs& a, int i, uint4 si, int lane,
+                                         unsigned lt_mask, int* core_buf, int* shell_buf, int& ncore, int& nshell,
+                                         bool& overlap, float Lf, float invLf)
+{
+    const RblGeom& g = a.g;
+    const unsigned FULL = 0xffffffffu;
+    for (int bb = beg; bb < end; bb += 32) {
+        const int sidx = bb + lane;
+        const bool valid = sidx < end;
+        float4 pj = src[valid ? sidx : beg];
+        float dx = pj.x - xie, dy = pj.y - yie, dz = pj.z - zie;
+        if (SMALL) {
+            dx -= Lf * rintf(dx * invLf);
+            dy -= Lf * rintf(dy * invLf);
+            dz -= Lf * rintf(dz * invLf);
+        }
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (!valid) r2 = 3.0e38f;
+        const int gj = sidx + goff;
+        // the three decisions come from the same two differences, so the
+        // definite and ambiguous regions partition the line exactly
+        const float t1 = r2 - g.rc2_mid, t2 = r2 - g.rs2_mid;
+        bool is_core = t1 < -g.rc2_band;
+        bool is_shell = t1 > g.rc2_band && t2 < -g.rs2_band;
+        const bool amb = r2 <= g.tiny2 || fabsf(t1) <= g.rc2_band || fabsf(t2) <= g.rs2_band;
+        if (__any_sync(FULL, amb)) {
+            if (amb) {
+                unsigned long long d2 = d2_exact(si, a.s4[gj]);
+                bool other = gj != i;
+                is_core = other && d2 <= a.c.Rc2;
+                is_shell = other && d2 > a.c.Rc2 && d2 <= a.c.Rs2;
+                overlap |= other && d2 == 0ull;
+            }
+        }
+        const unsigned cm = __ballot_sync(FULL, is_core);
+        const unsigned sm = __ballot_sync(FULL, is_shell);
+        const int cpos = ncore + __popc(cm & lt_mask);
+        const int spos = nshell + __popc(sm & lt_mask);
+        if (is_core && cpos < a.core_cap) core_buf[cpos] = gj;
+        if (is_shell && spos < a.shell_cap) shell_buf[spos] = gj;
+        ncore += __popc(cm);
+        nshell += __popc(sm);
+    }
+}
+
+template <bool MIXED, bool SMALL>
+__global__ void __launch_bounds__(WARPS * 32) k_rbl(RblArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const RbeConsts& c = a.c;
+    const RblGeom& g = a.g;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
+    const int nc = c.n_cell, R = c.reach;
+    const int G = g.G;
+    const int p = c.p;
+    const int p_pad = (p + 3) & ~3;
+    const int nbk = p_pad / 4;
 
-    // shared layout: LJ tables, then per-warp buffers
+    // ---- shared layout ------------------------------------------------------
     const int nt2 = c.ntypes * c.ntypes;
-    double* s_c12 = reinterpret_cast<double*>(smem);
+    const SmemLayout lay = smem_layout(g, nt2, p, a.core_cap, a.shell_cap);
+    float4* stage = reinterpret_cast<float4*>(smem);                              // [cap_stage]
+    RowInfo* rows = reinterpret_cast<RowInfo*>(smem + lay.rows);                   // [nrows]
+    int* cellpos = reinterpret_cast<int*>(smem + lay.cellpos);                     // [nrows * cpr]
+    const int cpr = g.cells_per_row + 1;
+    double* s_c12 = reinterpret_cast<double*>(smem + lay.lj);
     double* s_c6 = s_c12 + nt2;
     double* s_sh = s_c6 + nt2;
-    unsigned char* wbase = smem + sizeof(double) * 3 * ((nt2 + 1) & ~1);
-    const size_t wbytes = sizeof(uint64_t) * a.p_pad + sizeof(int) * (a.core_cap + a.shell_cap + a.p_pad);
-    uint64_t* words = reinterpret_cast<uint64_t*>(wbase + wbytes * wib);
-    int* core_buf = reinterpret_cast<int*>(words + a.p_pad);
+    uint64_t* words = reinterpret_cast<uint64_t*>(smem + lay.warps + lay.wbytes * wib);   // [ga][p_pad]
+    int* core_buf = reinterpret_cast<int*>(words + (size_t)p_pad * lay.ga);
     int* shell_buf = core_buf + a.core_cap;
     int* sel = shell_buf + a.shell_cap;
+    __shared__ int s_unit_ok;
+    __shared__ double red[WARPS][RBE_NPART_RBL];
+
     for (int t = threadIdx.x; t < nt2; t += blockDim.x) {
         int ti = t / c.ntypes, tj = t % c.ntypes;
         s_c12[t] = a.lj->c12[ti * RBE_MAXT + tj];
         s_c6[t] = a.lj->c6[ti * RBE_MAXT + tj];
         s_sh[t] = a.lj->shift[ti * RBE_MAXT + tj];
     }
-    __syncthreads();
 
-    const int nc = c.n_cell, R = c.reach;
-    const bool full = (2 * R + 1 >= nc);
-    const int naxis = full ? nc : 2 * R + 1;
+    const int naxis = SMALL ? nc : 2 * R + 1;
     const int nrows = naxis * naxis;
+    const float Lf = (float)c.L;
+    const float invLf = (float)c.invL;
     const float ncf = (float)nc;
 
     double acc_e[3] = {0.0, 0.0, 0.0};
     double acc_w[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     double acc_f[3] = {0.0, 0.0, 0.0};
-    const int warps_total = gridDim.x * RBE_WARPS_RBL;
+    float facc_e[3] = {0.f, 0.f, 0.f}, facc_w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, facc_f[3] = {0.f, 0.f, 0.f};
+    int fl_count = 0;
 
-    for (int i = blockIdx.x * RBE_WARPS_RBL + wib; i < a.n; i += warps_total) {
-        const uint4 si = a.s4[i];
-        const int cx = (int)cell_of_fixed(si.x, nc), cy = (int)cell_of_fixed(si.y, nc), cz = (int)cell_of_fixed(si.z, nc);
-        const float fx = (float)si.x * 2.3283064365386963e-10f;
-        const float fy = (float)si.y * 2.3283064365386963e-10f;
-        const float fz = (float)si.z * 2.3283064365386963e-10f;
-        int ncore = 0, nshell = 0;
-        bool overlap = false;
+    const int units_per_row = (nc + G - 1) / G;
+    const long nunits = (long)nc * nc * units_per_row;
 
-        // ---- 1. classify the stencil in canonical order ----------------------
-        for (int rb = 0; rb < nrows; rb += 32) {
-            int b1 = 0, e1 = 0, b2 = 0, e2 = 0;
-            int r = rb + lane;
-            if (r < nrows) {
-                int az = r / naxis, ay = r % naxis;
-                int zc, dz, yc, dy;
-                axis_cell(az, cz, R, nc, full, zc, dz);
-                axis_cell(ay, cy, R, nc, full, yc, dy);
-                float gz = axis_gap(fz, cz, dz, nc, full), gy = axis_gap(fy, cy, dy, nc, full);
-                float g2 = gz * gz + gy * gy;
-                if (g2 <= c.rs_frac2) {
-                    int rowbase = nc * (yc + nc * zc);
-                    if (full) {
-                        b1 = a.cell_start[rowbase];
-                        e1 = a.cell_start[rowbase + nc];
+    for (long unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+        const int ux = (int)(unit % units_per_row);
+        const int uy = (int)((unit / units_per_row) % nc);
+        const int uz = (int)(unit / ((long)units_per_row * nc));
+        const int cx0 = ux * G;
+        const int cx1 = min(cx0 + G, nc);           // exclusive
+        const int rowbase_u = nc * (uy + nc * uz);
+        const int A0 = a.cell_start[rowbase_u + cx0], A1 = a.cell_start[rowbase_u + cx1];
+        if (A0 == A1) continue;                     // uniform across the block
+
+        // ---- row table of the unit -------------------------------------------
+        __syncthreads();
+        const int ul = SMALL ? 0 : cx0 - R;
+        const int uh = SMALL ? nc - 1 : cx1 - 1 + R;       // inclusive
+        const int ncr = uh - ul + 1;                       // staged cells per row
+        // (a) one thread per (row, cell): cell sizes; the row's descriptor
+        for (int t = threadIdx.x; t < nrows * ncr; t += blockDim.x) {
+            const int r = t / ncr, k = t - r * ncr;
+            const int az = r / naxis, ay = r - az * naxis;
+            const int zu = SMALL ? az : ring_row(az, uz, R, nc);
+            const int yu = SMALL ? ay : ring_row(ay, uy, R, nc);
+            const int zc = wrapc(zu, nc), yc = wrapc(yu, nc);
+            const int rb = nc * (yc + nc * zc);
+            const int w = wrapc(ul + k, nc);
+            cellpos[r * cpr + k] = a.cell_start[rb + w + 1] - a.cell_start[rb + w];
+            if (k == 0) {
+                RowInfo ri;
+                ri.zc = zc;
+                ri.yc = yc;
+                ri.shz = SMALL ? 0.f : (zu < 0 ? -Lf : (zu >= nc ? Lf : 0.f));
+                ri.shy = SMALL ? 0.f : (yu < 0 ? -Lf : (yu >= nc ? Lf : 0.f));
+                ri.sbase = 0;
+                ri.ul = ul;
+                ri.goff[0] = ri.goff[1] = ri.goff[2] = 0;
+                const int dz = zu - uz, dy = yu - uy;
+                ri.zs = SMALL ? 0.f : (float)((dz > 0) - (dz < 0));
+                ri.ys = SMALL ? 0.f : (float)((dy > 0) - (dy < 0));
+                ri.zb = dz > 0 ? (float)(uz + dz) / ncf : (float)(uz + dz + 1) / ncf;
+                ri.yb = dy > 0 ? (float)(uy + dy) / ncf : (float)(uy + dy + 1) / ncf;
+                ri.pad = 0;
+                rows[r] = ri;
+            }
+        }
+        __syncthreads();
+        // (b) exclusive prefix of the cell sizes of each row
+        for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+            int* cp = cellpos + r * cpr;
+            int acc = 0;
+            for (int k = 0; k < ncr; ++k) {
+                int v = cp[k];
+                cp[k] = acc;
+                acc += v;
+            }
+            cp[ncr] = acc;
+        }
+        __syncthreads();
+        // (c) row bases in the staged array (warp 0 scans the row totals)
+        if (wib == 0) {
+            int carry = 0;
+            for (int r0 = 0; r0 < nrows; r0 += 32) {
+                const int r = r0 + lane;
+                int v = r < nrows ? cellpos[r * cpr + ncr] : 0;
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int t = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                if (r < nrows) rows[r].sbase = carry + incl - v;
+                carry += __shfl_sync(FULL, incl, 31);
+            }
+            if (lane == 0) s_unit_ok = carry <= g.cap_stage;
+        }
+        __syncthreads();
+        const bool staged = s_unit_ok;
+        // (d) global - source offsets of the three pieces of each row
+        for (int t = threadIdx.x; t < nrows * 3; t += blockDim.x) {
+            const int r = t / 3, pc = t - 3 * r;
+            const RowInfo& ri = rows[r];
+            const int* cp = cellpos + r * cpr;
+            const int ufirst = pc == 0 ? ul : (pc == 1 ? max(ul, 0) : max(ul, nc));
+            int off = 0;
+            if (staged && ufirst <= uh && (pc != 0 || ufirst < 0) && (pc != 1 || ufirst < nc)) {
+                const int rb = nc * (ri.yc + nc * ri.zc);
+                off = a.cell_start[rb + wrapc(ufirst, nc)] - (ri.sbase + cp[ufirst - ul]);
+            }
+            rows[r].goff[pc] = off;
+        }
+        // (e) stage the FP32 positions row by row
+        if (staged) {
+            for (int r = wib; r < nrows; r += WARPS) {
+                const int zc = rows[r].zc, yc = rows[r].yc, sb = rows[r].sbase;
+                const int rb = nc * (yc + nc * zc);
+                const int* cp = cellpos + r * cpr;
+                for (int pc = 0; pc < 3; ++pc) {
+                    const int u0 = pc == 0 ? ul : (pc == 1 ? max(ul, 0) : max(ul, nc));
+                    const int u1 = pc == 0 ? min(uh, -1) : (pc == 1 ? min(uh, nc - 1) : uh);
+                    if (u0 > u1) continue;
+                    const int gs = a.cell_start[rb + wrapc(u0, nc)];
+                    const int len = cp[u1 - ul + 1] - cp[u0 - ul];
+                    const int ss = sb + cp[u0 - ul];
+                    for (int k = lane; k < len; k += 32) stage[ss + k] = a.f4[gs + k];
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- atoms of the unit, one per warp at a time -----------------------
+        int kloc = 0;
+        for (int i = A0 + wib; i < A1; i += WARPS, ++kloc) {
+            // Philox words of the shell slots, made for lay.ga atoms per pass:
+            // slot k of atom gi uses word k%4 of the block at (gi, k/4, step, 1)
+            const int aslot = kloc % lay.ga;
+            if (aslot == 0) {
+                __syncwarp();
+                for (int t = lane; t < lay.ga * nbk; t += 32) {
+                    const int aa = t / nbk, b = t - aa * nbk;
+                    const int ii = i + WARPS * aa;
+                    if (ii < A1) {
+                        uint64_t w[4];
+                        philox4x64_10((uint64_t)a.perm[ii], (uint64_t)b, a.step, 1ull, c.seed, 0ull, w);
+#pragma unroll
+                        for (int qd = 0; qd < 4; ++qd) words[aa * p_pad + 4 * b + qd] = w[qd];
+                    }
+                }
+                __syncwarp();
+            }
+            const uint4 si = a.s4[i];
+            const float4 fi4 = a.f4[i];
+            const int cx = (int)cell_of_fixed(si.x, nc);
+            const float fx = (float)si.x * 2.3283064365386963e-10f;
+            const float fy = (float)si.y * 2.3283064365386963e-10f;
+            const float fz = (float)si.z * 2.3283064365386963e-10f;
+            int ncore = 0, nshell = 0;
+            bool overlap = false;
+
+            // ---- 1. classify the stencil in canonical order ------------------
+            for (int rb0 = 0; rb0 < nrows; rb0 += 32) {
+                // lane r describes row rb0 + r for this atom: up to two
+                // canonical segments [b, e) of the source array
+                int b1 = 0, e1 = 0, b2 = 0, e2 = 0, o1 = 0, o2 = 0;
+                float x1 = 0.f, x2 = 0.f, yie = 0.f, zie = 0.f;
+                const int r = rb0 + lane;
+                if (r < nrows) {
+                    const RowInfo& ri = rows[r];
+                    const int* cp = cellpos + r * cpr;
+                    yie = fi4.y - ri.shy;
+                    zie = fi4.z - ri.shz;
+                    const int rbw = nc * (ri.yc + nc * ri.zc);
+                    const int base = staged ? ri.sbase : 0;
+                    if (SMALL) {
+                        b1 = staged ? base : a.cell_start[rbw];
+                        e1 = b1 + cp[nc];
+                        o1 = ri.goff[1];
+                        x1 = fi4.x;
                     } else {
-                        float hx = sqrtf(c.rs_frac2 - g2) + 1e-5f;
-                        int dlo = (int)floorf((fx - hx) * ncf) - cx;
-                        int dhi = (int)floorf((fx + hx) * ncf) - cx;
-                        dlo = dlo < -R ? -R : dlo;
-                        dhi = dhi > R ? R : dhi;
-                        int ca = cx + dlo, cb = cx + dhi;
-                        int lo1, hi1, lo2 = 0, hi2 = -1;
-                        if (ca < 0) { lo1 = 0; hi1 = cb; lo2 = ca + nc; hi2 = nc - 1; }
-                        else if (cb >= nc) { lo1 = 0; hi1 = cb - nc; lo2 = ca; hi2 = nc - 1; }
-                        else { lo1 = ca; hi1 = cb; }
-                        b1 = a.cell_start[rowbase + lo1];
-                        e1 = a.cell_start[rowbase + hi1 + 1];
-                        if (hi2 >= lo2) {
-                            b2 = a.cell_start[rowbase + lo2];
-                            e2 = a.cell_start[rowbase + hi2 + 1];
+                        const float gz = fmaxf(0.f, ri.zs * (ri.zb - fz));
+                        const float gy = fmaxf(0.f, ri.ys * (ri.yb - fy));
+                        const float g2 = gz * gz + gy * gy;
+                        if (g2 <= c.rs_frac2) {
+                            const float hx = sqrtf(c.rs_frac2 - g2) + 1e-5f;
+                            const int dlo = max(-R, (int)floorf((fx - hx) * ncf) - cx);
+                            const int dhi = min(R, (int)floorf((fx + hx) * ncf) - cx);
+                            const int ua = cx + dlo, ub = cx + dhi;     // unwrapped, within [ul, uh]
+                            // canonical order: ascending wrapped index
+                            int lo1, hi1, lo2 = 1, hi2 = 0;
+                            if (ua < 0) { lo1 = 0; hi1 = ub; lo2 = ua; hi2 = -1; }
+                            else if (ub >= nc) { lo1 = nc; hi1 = ub; lo2 = ua; hi2 = nc - 1; }
+                            else { lo1 = ua; hi1 = ub; }
+                            {
+                                const int pc = lo1 >= nc ? 2 : 1;
+                                if (staged) { b1 = base + cp[lo1 - ul]; e1 = base + cp[hi1 - ul + 1]; }
+                                else { b1 = a.cell_start[rbw + wrapc(lo1, nc)]; e1 = b1 + cp[hi1 - ul + 1] - cp[lo1 - ul]; }
+                                o1 = ri.goff[pc];
+                                x1 = fi4.x - (pc == 2 ? Lf : 0.f);
+                            }
+                            if (lo2 <= hi2) {
+                                const int pc = lo2 < 0 ? 0 : 1;
+                                if (staged) { b2 = base + cp[lo2 - ul]; e2 = base + cp[hi2 - ul + 1]; }
+                                else { b2 = a.cell_start[rbw + wrapc(lo2, nc)]; e2 = b2 + cp[hi2 - ul + 1] - cp[lo2 - ul]; }
+                                o2 = ri.goff[pc];
+                                x2 = fi4.x - (pc == 0 ? -Lf : 0.f);
+                            }
                         }
                     }
                 }
-            }
-            int rcount = nrows - rb < 32 ? nrows - rb : 32;
-            for (int rr = 0; rr < rcount; ++rr) {
-                int rb1 = __shfl_sync(FULL, b1, rr), re1 = __shfl_sync(FULL, e1, rr);
-                int rb2 = __shfl_sync(FULL, b2, rr), re2 = __shfl_sync(FULL, e2, rr);
-#pragma unroll 1
-                for (int part = 0; part < 2; ++part) {
-                    int beg = part ? rb2 : rb1, end = part ? re2 : re1;
-                    for (int base = beg; base < end; base += 32) {
-                        int j = base + lane;
-                        bool valid = j < end;
-                        uint4 sj = valid ? a.s4[j] : si;
-                        int ddx = (int)(sj.x - si.x), ddy = (int)(sj.y - si.y), ddz = (int)(sj.z - si.z);
-                        unsigned long long d2 = (unsigned long long)((long long)ddx * ddx) +
-                                                (unsigned long long)((long long)ddy * ddy) +
-                                                (unsigned long long)((long long)ddz * ddz);
-                        bool other = valid && j != i;
-                        bool is_core = other && d2 <= c.Rc2;
-                        bool is_shell = other && d2 > c.Rc2 && d2 <= c.Rs2;
-                        overlap |= other && d2 == 0ull;
-                        unsigned cm = __ballot_sync(FULL, is_core), sm = __ballot_sync(FULL, is_shell);
-                        int cpos = ncore + __popc(cm & lt_mask), spos = nshell + __popc(sm & lt_mask);
-                        if (is_core && cpos < a.core_cap) core_buf[cpos] = j;
-                        if (is_shell && spos < a.shell_cap) shell_buf[spos] = j;
-                        ncore += __popc(cm);
-                        nshell += __popc(sm);
+                // walk the non-empty segments in canonical order
+                const unsigned m1 = __ballot_sync(FULL, e1 > b1), m2 = __ballot_sync(FULL, e2 > b2);
+                unsigned mm = m1 | m2;
+                while (mm) {
+                    const int rr = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const float ry = __shfl_sync(FULL, yie, rr), rz = __shfl_sync(FULL, zie, rr);
+                    if ((m1 >> rr) & 1u) {
+                        const int beg = __shfl_sync(FULL, b1, rr), end = __shfl_sync(FULL, e1, rr);
+                        const int go = __shfl_sync(FULL, o1, rr);
+                        const float rx = __shfl_sync(FULL, x1, rr);
+                        if (staged) classify<SMALL>(stage, beg, end, go, rx, ry, rz, a, i, si, lane, lt_mask, core_buf,
+                                                    shell_buf, ncore, nshell, overlap, Lf, invLf);
+                        else classify<SMALL>(a.f4, beg, end, go, rx, ry, rz, a, i, si, lane, lt_mask, core_buf,
+                                             shell_buf, ncore, nshell, overlap, Lf, invLf);
+                    }
+                    if ((m2 >> rr) & 1u) {
+                        const int beg = __shfl_sync(FULL, b2, rr), end = __shfl_sync(FULL, e2, rr);
+                        const int go = __shfl_sync(FULL, o2, rr);
+                        const float rx = __shfl_sync(FULL, x2, rr);
+                        if (staged) classify<SMALL>(stage, beg, end, go, rx, ry, rz, a, i, si, lane, lt_mask, core_buf,
+                                                    shell_buf, ncore, nshell, overlap, Lf, invLf);
+                        else classify<SMALL>(a.f4, beg, end, go, rx, ry, rz, a, i, si, lane, lt_mask, core_buf,
+                                             shell_buf, ncore, nshell, overlap, Lf, invLf);
                     }
                 }
             }
-        }
-        if (__any_sync(FULL, overlap) && lane == 0) latch_status(a.status, RBE_ST_OVERLAP);
-        if ((ncore > a.core_cap || nshell > a.shell_cap) && lane == 0) latch_status(a.status, RBE_ST_CAPACITY);
-        const int ncore_c = ncore < a.core_cap ? ncore : a.core_cap;
-        const int gi = a.perm[i];
+            if (__any_sync(FULL, overlap) && lane == 0) latch_status(a.status, RBE_ST_OVERLAP);
+            if ((ncore > a.core_cap || nshell > a.shell_cap) && lane == 0) latch_status(a.status, RBE_ST_CAPACITY);
+            const int ncore_c = min(ncore, a.core_cap);
+            const int gi = a.perm[i];
 
-        // ---- 2. shell batch (Floyd over ordinals) ---------------------------
-        const int p = c.p;
-        const bool sample = nshell > p;
-        const int nb = sample ? p : nshell;
-        if (sample) {
-            for (int b = lane; 4 * b < p; b += 32) {
-                uint64_t w[4];
-                philox4x64_10((uint64_t)gi, (uint64_t)b, a.step, 1ull, c.seed, 0ull, w);
-#pragma unroll
-                for (int qd = 0; qd < 4; ++qd) words[4 * b + qd] = w[qd];
+            // ---- 2. shell batch (Floyd over ordinals) -----------------------
+            const bool sample = nshell > p;
+            const int nb = sample ? p : nshell;
+            const uint64_t* wa = words + (size_t)aslot * p_pad;
+            if (sample) {
+                if (p <= 32) {
+                    // slot k on lane k; the insertions resolved in slot order
+                    const uint32_t jk = (uint32_t)(nshell - p + lane);
+                    const int tk = lane < p ? (int)uniform_below(wa[lane], jk + 1u) : -1;
+                    int mysel = -1;
+                    for (int k = 0; k < p; ++k) {
+                        const int t = __shfl_sync(FULL, tk, k);
+                        const bool dup = __any_sync(FULL, lane < k && mysel == t);
+                        if (lane == k) mysel = dup ? (int)jk : t;
+                    }
+                    if (lane < p) sel[lane] = mysel;
+                } else {
+                    for (int k = 0; k < p; ++k) {
+                        const uint32_t jj = (uint32_t)(nshell - p + k);
+                        const int t = (int)uniform_below(wa[k], jj + 1u);
+                        bool dup = false;
+                        for (int l = lane; l < k; l += 32) dup |= (sel[l] == t);
+                        dup = __any_sync(FULL, dup);
+                        if (lane == 0) sel[k] = dup ? (int)jj : t;
+                        __syncwarp();
+                    }
+                }
             }
             __syncwarp();
-            for (int k = 0; k < p; ++k) {
-                uint64_t jj = (uint64_t)(nshell - p + k);
-                int t = (int)__umul64hi(words[k], jj + 1ull);
-                bool dup = false;
-                for (int l = lane; l < k; l += 32) dup |= (sel[l] == t);
-                dup = __any_sync(FULL, dup);
-                if (lane == 0) sel[k] = dup ? (int)jj : t;
-                __syncwarp();
-            }
-        }
-        __syncwarp();
-        const double wsh = sample ? (double)nshell / (double)p : 1.0;
 
-        // ---- 3. pair terms over C(i) and B(i) -------------------------------
-        double fi[3] = {0.0, 0.0, 0.0};
-        const int npairs = ncore_c + nb;
-        if (MIXED) {
-            const float qi = __uint_as_float(si.w);
+            // ---- 3. pair terms over C(i) and B(i) -----------------------------
+            // Eq. (2.10) with the Coulomb factor erfc (erfc - 1 = -erf for a
+            // same-molecule pair, the Ewald exclusion correction) and LJ.
+            const int npairs = ncore_c + nb;
             const int2 ti = a.tm[i];
-            const float kef = (float)c.k_e, saf = (float)c.sqrt_alpha, tsaf = (float)c.two_sqrt_alpha_over_sqrt_pi;
-            float ff[3] = {0.f, 0.f, 0.f}, fe[3] = {0.f, 0.f, 0.f}, fw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int t = lane; t < npairs; t += 32) {
-                int j;
-                float w;
-                if (t < ncore_c) { j = core_buf[t]; w = 1.0f; }
-                else {
-                    int k = t - ncore_c;
-                    int ord = sample ? sel[k] : k;
-                    ord = ord < a.shell_cap ? ord : a.shell_cap - 1;
-                    j = shell_buf[ord];
-                    w = (float)wsh;
-                }
-                const uint4 sj = a.s4[j];
-                const int2 tj = a.tm[j];
-                float dx = (float)(int)(sj.x - si.x) * c.Lfix;
-                float dy = (float)(int)(sj.y - si.y) * c.Lfix;
-                float dz = (float)(int)(sj.z - si.z) * c.Lfix;
-                float r2 = dx * dx + dy * dy + dz * dz;
-                float rinv = rsqrtf(r2);
-                float r = r2 * rinv;
-                float qq = kef * qi * __uint_as_float(sj.w);
-                float ar = saf * r;
-                float gauss = tsaf * expf(-ar * ar);
-                float s, uc = 0.f, ul = 0.f, ux = 0.f;
-                if (ti.y == tj.y) {
-                    float er = erff(ar);
-                    s = -qq * (gauss * rinv - er * rinv * rinv) * rinv;
-                    ux = -qq * er * rinv;
-                } else {
-                    float ec = erfcf(ar);
-                    s = -qq * (ec * rinv * rinv + gauss * rinv) * rinv;
-                    uc = qq * ec * rinv;
-                    int tt = ti.x * c.ntypes + tj.x;
-                    float c12 = (float)s_c12[tt], c6 = (float)s_c6[tt];
-                    if (c12 != 0.f || c6 != 0.f) {
-                        float ir2 = rinv * rinv;
-                        float ir6 = ir2 * ir2 * ir2;
-                        s += -(12.f * c12 * ir6 * ir6 - 6.f * c6 * ir6) * ir2;
-                        ul = c12 * ir6 * ir6 - c6 * ir6 - (float)s_sh[tt];
+            if (MIXED) {
+                const float wsh = sample ? (float)nshell / (float)p : 1.0f;
+                const float qi = __uint_as_float(si.w);
+                const float kef = (float)c.k_e, saf = (float)c.sqrt_alpha, tsaf = (float)c.two_sqrt_alpha_over_sqrt_pi;
+                float ff[3] = {0.f, 0.f, 0.f};
+                for (int t = lane; t < npairs; t += 32) {
+                    int j;
+                    float w;
+                    if (t < ncore_c) { j = core_buf[t]; w = 1.0f; }
+                    else {
+                        const int k = t - ncore_c;
+                        const int ord = sample ? sel[k] : k;
+                        j = shell_buf[min(ord, a.shell_cap - 1)];
+                        w = wsh;
                     }
+                    const uint4 sj = a.s4[j];
+                    const int2 tj = a.tm[j];
+                    const float dx = (float)(int)(sj.x - si.x) * c.Lfix;
+                    const float dy = (float)(int)(sj.y - si.y) * c.Lfix;
+                    const float dz = (float)(int)(sj.z - si.z) * c.Lfix;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const float rinv = rsqrtf(r2);
+                    const float r = r2 * rinv;
+                    const float qq = kef * qi * __uint_as_float(sj.w);
+                    const float ar = saf * r;
+                    const float gauss = tsaf * __expf(-ar * ar);
+                    const bool ex = ti.y == tj.y;
+                    const float ec = erfcf(ar) - (ex ? 1.0f : 0.0f);
+                    const float ucoul = qq * ec * rinv;
+                    float s = -qq * (ec * rinv + gauss) * rinv * rinv;
+                    const int tt = ti.x * c.ntypes + tj.x;
+                    const float c12 = ex ? 0.f : (float)s_c12[tt], c6 = ex ? 0.f : (float)s_c6[tt];
+                    const float ir2 = rinv * rinv;
+                    const float ir6 = ir2 * ir2 * ir2;
+                    s -= (12.f * c12 * ir6 - 6.f * c6) * ir6 * ir2;
+                    const float ulj = (c12 * ir6 - c6) * ir6 - (ex ? 0.f : (float)s_sh[tt]);
+                    const float gx = w * s * dx, gy = w * s * dy, gz = w * s * dz;
+                    ff[0] += gx; ff[1] += gy; ff[2] += gz;
+                    facc_e[0] += ex ? 0.f : w * ucoul;
+                    facc_e[1] += w * ulj;
+                    facc_e[2] += ex ? w * ucoul : 0.f;
+                    facc_w[0] += dx * gx; facc_w[1] += dy * gy; facc_w[2] += dz * gz;
+                    facc_w[3] += dx * gy; facc_w[4] += dx * gz; facc_w[5] += dy * gz;
                 }
-                float gx = w * s * dx, gy = w * s * dy, gz = w * s * dz;
-                ff[0] += gx; ff[1] += gy; ff[2] += gz;
-                fe[0] += w * uc; fe[1] += w * ul; fe[2] += w * ux;
-                fw[0] += dx * gx; fw[1] += dy * gy; fw[2] += dz * gz;
-                fw[3] += dx * gy; fw[4] += dx * gz; fw[5] += dy * gz;
-            }
 #pragma unroll
-            for (int q = 0; q < 3; ++q) { fi[q] = (double)ff[q]; acc_e[q] += (double)fe[q]; }
-#pragma unroll
-            for (int q = 0; q < 6; ++q) acc_w[q] += (double)fw[q];
-        } else {
-            const double4_32a pi = a.p4[i];
-            const int2 ti = a.tm[i];
-            for (int t = lane; t < npairs; t += 32) {
-                int j;
-                double w;
-                if (t < ncore_c) { j = core_buf[t]; w = 1.0; }
-                else {
-                    int k = t - ncore_c;
-                    int ord = sample ? sel[k] : k;
-                    ord = ord < a.shell_cap ? ord : a.shell_cap - 1;
-                    j = shell_buf[ord];
-                    w = wsh;
+                for (int q = 0; q < 3; ++q) ff[q] = warp_sum(ff[q]);
+                if (lane == 0) {
+                    float* Fr = reinterpret_cast<float*>(a.F_real);
+                    Fr[3 * (size_t)i + 0] = ff[0];
+                    Fr[3 * (size_t)i + 1] = ff[1];
+                    Fr[3 * (size_t)i + 2] = ff[2];
+                    facc_f[0] += ff[0]; facc_f[1] += ff[1]; facc_f[2] += ff[2];
                 }
-                const double4_32a pj = a.p4[j];
-                const int2 tj = a.tm[j];
-                double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                dx -= c.L * rint(dx * c.invL);
-                dy -= c.L * rint(dy * c.invL);
-                dz -= c.L * rint(dz * c.invL);
-                double r2 = dx * dx + dy * dy + dz * dz;
-                double r = sqrt(r2);
-                double rinv = 1.0 / r;
-                double qq = c.k_e * pi.w * pj.w;
-                double ar = c.sqrt_alpha * r;
-                double gauss = c.two_sqrt_alpha_over_sqrt_pi * exp(-ar * ar);
-                double s, uc = 0.0, ul = 0.0, ux = 0.0;
-                if (ti.y == tj.y) {
-                    double er = erf(ar);
-                    s = -qq * (gauss * rinv - er * rinv * rinv) * rinv;
-                    ux = -qq * er * rinv;
-                } else {
-                    double ec = erfc(ar);
-                    s = -qq * (ec * rinv * rinv + gauss * rinv) * rinv;
-                    uc = qq * ec * rinv;
-                    int tt = ti.x * c.ntypes + tj.x;
-                    double c12 = s_c12[tt], c6 = s_c6[tt];
-                    if (c12 != 0.0 || c6 != 0.0) {
-                        double ir2 = rinv * rinv;
-                        double ir6 = ir2 * ir2 * ir2;
-                        s += -(12.0 * c12 * ir6 * ir6 - 6.0 * c6 * ir6) * ir2;
-                        ul = c12 * ir6 * ir6 - c6 * ir6 - s_sh[tt];
+                // flush the FP32 per-lane sums into FP64 every 16 atoms
+                if (++fl_count == 16) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) { acc_e[q] += (double)facc_e[q]; facc_e[q] = 0.f; }
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) { acc_w[q] += (double)facc_w[q]; facc_w[q] = 0.f; }
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) { acc_f[q] += (double)facc_f[q]; facc_f[q] = 0.f; }
+                    fl_count = 0;
+                }
+            } else {
+                const double wsh = sample ? (double)nshell / (double)p : 1.0;
+                const double4_32a pi = a.p4[i];
+                double fi[3] = {0.0, 0.0, 0.0};
+                for (int t = lane; t < npairs; t += 32) {
+                    int j;
+                    double w;
+                    if (t < ncore_c) { j = core_buf[t]; w = 1.0; }
+                    else {
+                        const int k = t - ncore_c;
+                        const int ord = sample ? sel[k] : k;
+                        j = shell_buf[min(ord, a.shell_cap - 1)];
+                        w = wsh;
                     }
+                    const double4_32a pj = a.p4[j];
+                    const int2 tj = a.tm[j];
+                    double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                    dx -= c.L * rint(dx * c.invL);
+                    dy -= c.L * rint(dy * c.invL);
+                    dz -= c.L * rint(dz * c.invL);
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    const double r = sqrt(r2);
+                    const double rinv = 1.0 / r;
+                    const double qq = c.k_e * pi.w * pj.w;
+                    const double ar = c.sqrt_alpha * r;
+                    const double gauss = c.two_sqrt_alpha_over_sqrt_pi * exp(-ar * ar);
+                    const bool ex = ti.y == tj.y;
+                    // the exclusion term -erf is evaluated directly (not as
+                    // erfc - 1) to keep its full FP64 relative accuracy
+                    const double ec = ex ? -erf(ar) : erfc(ar);
+                    const double ucoul = qq * ec * rinv;
+                    double s = -qq * (ec * rinv + gauss) * rinv * rinv;
+                    const int tt = ti.x * c.ntypes + tj.x;
+                    const double c12 = ex ? 0.0 : s_c12[tt], c6 = ex ? 0.0 : s_c6[tt];
+                    const double ir2 = rinv * rinv;
+                    const double ir6 = ir2 * ir2 * ir2;
+                    s -= (12.0 * c12 * ir6 - 6.0 * c6) * ir6 * ir2;
+                    const double ulj = (c12 * ir6 - c6) * ir6 - (ex ? 0.0 : s_sh[tt]);
+                    const double gx = w * s * dx, gy = w * s * dy, gz = w * s * dz;
+                    fi[0] += gx; fi[1] += gy; fi[2] += gz;
+                    acc_e[0] += ex ? 0.0 : w * ucoul;
+                    acc_e[1] += w * ulj;
+                    acc_e[2] += ex ? w * ucoul : 0.0;
+                    acc_w[0] += dx * gx; acc_w[1] += dy * gy; acc_w[2] += dz * gz;
+                    acc_w[3] += dx * gy; acc_w[4] += dx * gz; acc_w[5] += dy * gz;
                 }
-                double gx = w * s * dx, gy = w * s * dy, gz = w * s * dz;
-                fi[0] += gx; fi[1] += gy; fi[2] += gz;
-                acc_e[0] += w * uc; acc_e[1] += w * ul; acc_e[2] += w * ux;
-                acc_w[0] += dx * gx; acc_w[1] += dy * gy; acc_w[2] += dz * gz;
-                acc_w[3] += dx * gy; acc_w[4] += dx * gz; acc_w[5] += dy * gz;
-            }
-        }
 #pragma unroll
-        for (int q = 0; q < 3; ++q) fi[q] = warp_sum(fi[q]);
-        if (lane == 0) {
-            a.F_real[3 * (size_t)i + 0] = fi[0];
-            a.F_real[3 * (size_t)i + 1] = fi[1];
-            a.F_real[3 * (size_t)i + 2] = fi[2];
-            acc_f[0] += fi[0]; acc_f[1] += fi[1]; acc_f[2] += fi[2];
-        }
+                for (int q = 0; q < 3; ++q) fi[q] = warp_sum(fi[q]);
+                if (lane == 0) {
+                    a.F_real[3 * (size_t)i + 0] = fi[0];
+                    a.F_real[3 * (size_t)i + 1] = fi[1];
+                    a.F_real[3 * (size_t)i + 2] = fi[2];
+                    acc_f[0] += fi[0]; acc_f[1] += fi[1]; acc_f[2] += fi[2];
+                }
+            }
 
-        // ---- debug record (caller index order) ------------------------------
-        if (a.debug) {
-            if (lane == 0) { a.dbg_ncore[gi] = ncore; a.dbg_nshell[gi] = nshell; }
-            for (int t = lane; t < a.dbg_cap; t += 32)
-                a.dbg_core[(size_t)gi * a.dbg_cap + t] = t < ncore_c ? a.perm[core_buf[t]] : -1;
-            for (int k = lane; k < p; k += 32) {
-                int id = -1;
-                if (k < nb) {
-                    int ord = sample ? sel[k] : k;
-                    ord = ord < a.shell_cap ? ord : a.shell_cap - 1;
-                    id = a.perm[shell_buf[ord]];
+            // ---- debug record (caller index order) ---------------------------
+            if (a.debug) {
+                if (lane == 0) { a.dbg_ncore[gi] = ncore; a.dbg_nshell[gi] = nshell; }
+                for (int t = lane; t < a.dbg_cap; t += 32)
+                    a.dbg_core[(size_t)gi * a.dbg_cap + t] = t < ncore_c ? a.perm[core_buf[t]] : -1;
+                for (int k = lane; k < p; k += 32) {
+                    int id = -1;
+                    if (k < nb) {
+                        const int ord = sample ? sel[k] : k;
+                        id = a.perm[shell_buf[min(ord, a.shell_cap - 1)]];
+                    }
+                    a.dbg_batch[(size_t)gi * p + k] = id;
                 }
-                a.dbg_batch[(size_t)gi * p + k] = id;
             }
+            __syncwarp();
         }
-        __syncwarp();
     }
 
     // ---- deterministic block partials ---------------------------------------
-    __shared__ double red[RBE_WARPS_RBL][RBE_NPART_RBL];
+    if (MIXED) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc_e[q] += (double)facc_e[q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc_w[q] += (double)facc_w[q];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc_f[q] += (double)facc_f[q];
+    }
     double v[RBE_NPART_RBL] = {acc_e[0], acc_e[1], acc_e[2], acc_w[0], acc_w[1], acc_w[2],
                                acc_w[3], acc_w[4], acc_w[5], acc_f[0], acc_f[1], acc_f[2]};
 #pragma unroll
     for (int q = 0; q < RBE_NPART_RBL; ++q) v[q] = warp_sum(v[q]);
+    __syncthreads();
     if (lane == 0)
         for (int q = 0; q < RBE_NPART_RBL; ++q) red[wib][q] = v[q];
     __syncthreads();
     if (threadIdx.x < RBE_NPART_RBL) {
         double s = 0.0;
-        for (int w = 0; w < RBE_WARPS_RBL; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < WARPS; ++w) s += red[w][threadIdx.x];
         a.part[blockIdx.x * RBE_NPART_RBL + threadIdx.x] = s;
     }
+}
+
+template <bool MIXED, bool SMALL>
+void launch_t(rbe_ctx* ctx, const RblArgs& a, int smem, cudaStream_t st)
+{
+    cudaFuncSetAttribute(k_rbl<MIXED, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_rbl<MIXED, SMALL><<<ctx->grid_rbl, WARPS * 32, smem, st>>>(a);
+}
+
+template <bool MIXED, bool SMALL>
+int occupancy_t(int smem)
+{
+    int nb = 0;
+    cudaFuncSetAttribute(k_rbl<MIXED, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbl<MIXED, SMALL>, WARPS * 32, smem);
+    return nb;
 }
 
 }  // namespace
@@ -372,10 +669,7 @@ __global__ void __launch_bounds__(RBE_WARPS_RBL * 32) k_rbl(RblArgs a)
 int rbl_smem_bytes(const rbe_ctx* ctx)
 {
     int nt2 = ctx->c.ntypes * ctx->c.ntypes;
-    int p_pad = (ctx->c.p + 3) & ~3;
-    size_t head = sizeof(double) * 3 * ((nt2 + 1) & ~1);
-    size_t wbytes = sizeof(uint64_t) * p_pad + sizeof(int) * (ctx->core_cap + ctx->shell_cap + p_pad);
-    return (int)(head + wbytes * RBE_WARPS_RBL);
+    return (int)smem_layout(ctx->rbl, nt2, ctx->c.p, ctx->core_cap, ctx->shell_cap).total;
 }
 
 void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st)
@@ -383,20 +677,23 @@ void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st)
     RblArgs a;
     a.n = n;
     a.step = step;
-    a.s4 = ctx->s4; a.p4 = ctx->p4; a.tm = ctx->tm; a.perm = ctx->perm; a.cell_start = ctx->cell_start;
+    a.s4 = ctx->s4; a.f4 = ctx->f4; a.p4 = ctx->p4; a.tm = ctx->tm; a.perm = ctx->perm;
+    a.cell_start = ctx->cell_start;
     a.lj = ctx->lj; a.F_real = ctx->F_real; a.part = ctx->part_rbl; a.status = ctx->status;
     a.c = ctx->c;
-    a.core_cap = ctx->core_cap; a.shell_cap = ctx->shell_cap; a.p_pad = (ctx->c.p + 3) & ~3;
+    a.g = ctx->rbl;
+    a.core_cap = ctx->core_cap; a.shell_cap = ctx->shell_cap;
     a.debug = ctx->debug; a.dbg_cap = ctx->dbg_cap_core;
     a.dbg_ncore = ctx->dbg_ncore; a.dbg_nshell = ctx->dbg_nshell; a.dbg_core = ctx->dbg_core; a.dbg_batch = ctx->dbg_batch;
     int smem = rbl_smem_bytes(ctx);
     prof_begin(ctx, RBE_K_RBL, st);
+    const bool small = ctx->rbl.small;
     if (ctx->precision == RBE_MIXED) {
-        cudaFuncSetAttribute(k_rbl<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_rbl<true><<<ctx->grid_rbl, RBE_WARPS_RBL * 32, smem, st>>>(a);
+        if (small) launch_t<true, true>(ctx, a, smem, st);
+        else launch_t<true, false>(ctx, a, smem, st);
     } else {
-        cudaFuncSetAttribute(k_rbl<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_rbl<false><<<ctx->grid_rbl, RBE_WARPS_RBL * 32, smem, st>>>(a);
+        if (small) launch_t<false, true>(ctx, a, smem, st);
+        else launch_t<false, false>(ctx, a, smem, st);
     }
     prof_end(ctx, RBE_K_RBL, st);
 }
@@ -404,13 +701,9 @@ void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st)
 int rbl_blocks_per_sm(const rbe_ctx* ctx)
 {
     int smem = rbl_smem_bytes(ctx);
-    int nb = 0;
-    if (ctx->precision == RBE_MIXED) {
-        cudaFuncSetAttribute(k_rbl<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbl<true>, RBE_WARPS_RBL * 32, smem);
-    } else {
-        cudaFuncSetAttribute(k_rbl<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbl<false>, RBE_WARPS_RBL * 32, smem);
-    }
+    const bool small = ctx->rbl.small;
+    int nb;
+    if (ctx->precision == RBE_MIXED) nb = small ? occupancy_t<true, true>(smem) : occupancy_t<true, false>(smem);
+    else nb = small ? occupancy_t<false, true>(smem) : occupancy_t<false, false>(smem);
     return nb > 0 ? nb : 1;
 }

@@ -19,8 +19,6 @@
 
 #include "rbe_internal.cuh"
 
-int rbl_blocks_per_sm(const rbe_ctx* ctx);
-
 namespace {
 
 const double PI = 3.14159265358979323846;
@@ -97,14 +95,14 @@ void refresh_consts(rbe_ctx* ctx)
 
 void free_dev(rbe_ctx* ctx)
 {
-    void* ptrs[] = {ctx->s4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
+    void* ptrs[] = {ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
                     ctx->F_real, ctx->F_bond, ctx->part_rbl, ctx->part_q, ctx->part_bond, ctx->kT, ctx->km, ctx->kv,
                     ctx->rho_part, ctx->rho, ctx->totals, ctx->status, ctx->lj, ctx->dbg_ncore, ctx->dbg_nshell,
                     ctx->dbg_core, ctx->dbg_batch, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
                     ctx->ke_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    ctx->s4 = nullptr; ctx->p4 = nullptr; ctx->tm = nullptr; ctx->perm = nullptr; ctx->cell_of = nullptr;
+    ctx->s4 = nullptr; ctx->f4 = nullptr; ctx->p4 = nullptr; ctx->tm = nullptr; ctx->perm = nullptr; ctx->cell_of = nullptr;
     ctx->slot = nullptr; ctx->cell_count = nullptr; ctx->cell_start = nullptr; ctx->F_real = nullptr;
     ctx->F_bond = nullptr; ctx->part_rbl = nullptr; ctx->part_q = nullptr; ctx->part_bond = nullptr;
     ctx->kT = nullptr; ctx->km = nullptr; ctx->kv = nullptr; ctx->rho_part = nullptr; ctx->rho = nullptr;
@@ -143,6 +141,44 @@ void auto_caps(rbe_ctx* ctx, int n)
     int sc = ctx->user_shell_cap > 0 ? ctx->user_shell_cap : round32(2.0 * ms + 6.0 * sqrt(ms) + 32.0);
     ctx->core_cap = (cc + 31) / 32 * 32;
     ctx->shell_cap = (sc + 31) / 32 * 32;
+}
+
+// Work-unit geometry of the RBL kernel and the rounding bound of its FP32
+// classification prefilter.  Positions are FP32 copies of the wrapped FP64
+// coordinates (error <= L 2^-24 each, plus L 2^-32 from the fixed-point code),
+// so each displacement component is off by at most da = 3 L 2^-23 + r 2^-24
+// and r^2 by at most 2 sqrt(3) r da + 3 da^2 + 3 r^2 2^-23; the bands are four
+// times that bound wide, and inside them the exact integer test decides.
+void rbl_geometry(rbe_ctx* ctx, int n)
+{
+    RblGeom& g = ctx->rbl;
+    const RbeConsts& c = ctx->c;
+    const int nc = c.n_cell, R = c.reach;
+    g.small = (2 * R + 1 >= nc) ? 1 : 0;
+    double apc = (double)n / ((double)nc * nc * nc);
+    int G = (int)lrint(48.0 / (apc > 1e-9 ? apc : 1e-9));
+    G = G < 1 ? 1 : (G > nc ? nc : G);
+    g.G = G;
+    g.cells_per_row = g.small ? nc : G + 2 * R;
+    int naxis = g.small ? nc : 2 * R + 1;
+    g.nrows = naxis * naxis;
+    double region = g.small ? (double)n : (double)g.cells_per_row * g.nrows * apc;
+    int cap = (int)ceil(1.3 * region + 256.0);
+    cap = (cap + 63) / 64 * 64;
+    // keep the staged block below ~120 KB of shared memory
+    int maxcap = (120 * 1024) / 16;
+    g.cap_stage = cap < maxcap ? cap : maxcap;
+    auto bound = [&](double r) {
+        double da = 3.0 * c.L * 1.1920928955078125e-07 + r * 5.9604644775390625e-08;
+        return 4.0 * (2.0 * sqrt(3.0) * r * da + 3.0 * da * da + 3.0 * r * r * 1.1920928955078125e-07);
+    };
+    double rc2 = c.r_c * c.r_c, rs2 = c.r_s * c.r_s;
+    // band centres in FP32; the widths also absorb the rounding of the centres
+    g.rc2_mid = (float)rc2;
+    g.rc2_band = (float)(bound(c.r_c) + fabs((double)g.rc2_mid - rc2));
+    g.rs2_mid = (float)rs2;
+    g.rs2_band = (float)(bound(c.r_s) + fabs((double)g.rs2_mid - rs2));
+    g.tiny2 = (float)(1e-6 * rc2 + bound(0.0));
 }
 
 // Reallocates *p only when `count` exceeds the recorded capacity *cap.
@@ -202,6 +238,7 @@ int ensure(rbe_ctx* ctx, int n)
     }
     if (n != ctx->last_n || ctx->precision != ctx->last_precision) {
         auto_caps(ctx, n);
+        rbl_geometry(ctx, n);
         if (rbl_smem_bytes(ctx) > 220 * 1024)
             return set_err(ctx, RBE_ECAPACITY, "list capacities (%d core, %d shell) exceed shared memory",
                            ctx->core_cap, ctx->shell_cap);
@@ -219,6 +256,7 @@ int ensure(rbe_ctx* ctx, int n)
     int gb = ctx->n_wmol > 0 ? (ctx->n_wmol + 255) / 256 : 0;
     ctx->grid_bond = gb < 4 * ctx->n_sm ? gb : 4 * ctx->n_sm;
     if ((rc = grow(ctx, &ctx->s4, &ctx->cap_atoms[0], n))) return rc;
+    if ((rc = grow(ctx, &ctx->f4, &ctx->cap_atoms[17], n))) return rc;
     if ((rc = grow(ctx, &ctx->p4, &ctx->cap_atoms[1], n))) return rc;
     if ((rc = grow(ctx, &ctx->tm, &ctx->cap_atoms[2], n))) return rc;
     if ((rc = grow(ctx, &ctx->perm, &ctx->cap_atoms[3], n))) return rc;
@@ -339,7 +377,7 @@ int rbe_create(rbe_ctx** out, double box_L, double alpha, double r_c, double r_s
         return RBE_EINVAL;
     int n_cell = (int)floor(box_L / r_c);
     long ncells = (long)n_cell * n_cell * n_cell;
-    if (n_cell < 1 || ncells > (1L << 26) || p > 4096 || P > (1 << 20)) return RBE_EINVAL;
+    if (n_cell < 1 || ncells > (1L << 26) || p > 512 || P > (1 << 20)) return RBE_EINVAL;
     rbe_ctx* ctx = (rbe_ctx*)calloc(1, sizeof(rbe_ctx));
     if (!ctx) return RBE_ENOMEM;
     ctx->prof = new ProfState();

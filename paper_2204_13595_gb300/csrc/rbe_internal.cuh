@@ -5,6 +5,7 @@
 //   sorted order = atoms ordered by (canonical cell, caller index), built by a
 //   counting sort each step (cells of edge L/floor(L/r_c), Sec. 2.3).
 //   s4   [n]  uint4   fixed-point (sx, sy, sz) and q as FP32 bits   (16 B/atom)
+//   f4   [n]  float4  FP32 wrapped (x, y, z) and q                 (16 B/atom)
 //   p4   [n]  double4_32a wrapped (x, y, z) and q in FP64              (32 B/atom)
 //   tm   [n]  int2    (type, mol)                                   (8 B/atom)
 //   perm [n]  int     sorted index -> caller index
@@ -44,6 +45,19 @@ struct RbeConsts {
     int shift_lj;
 };
 
+// Geometry of the RBL kernel's work units and of its FP32 classification
+// prefilter (rbe_api.cu derives it from the box, the cutoffs and the density).
+struct RblGeom {
+    int G;                 // cells per work unit along x
+    int cells_per_row;     // staged cells per stencil row (G + 2R, or n_cell for small boxes)
+    int nrows;             // stencil rows of a unit
+    int cap_stage;         // staged atoms that fit in shared memory
+    int small;             // 1 when the stencil covers the whole box (2R+1 >= n_cell)
+    float rc2_mid, rc2_band;   // r_c^2 and the FP32 rounding bound around it (A^2)
+    float rs2_mid, rs2_band;   // same for r_s^2
+    float tiny2;           // below this squared distance the exact test decides
+};
+
 // LJ pair table (device): c12 = 4 eps sig^12, c6 = 4 eps sig^6, shift
 struct RbeLJ {
     double c12[RBE_MAXT * RBE_MAXT];
@@ -68,6 +82,7 @@ struct rbe_ctx {
     int n_cap;
     long ncells;
     uint4* s4;
+    float4* f4;
     double4_32a* p4;
     int2* tm;
     int* perm;
@@ -75,7 +90,7 @@ struct rbe_ctx {
     int* slot;
     int* cell_count;     // [ncells + 1]
     int* cell_start;     // [ncells + 1]
-    double* F_real;      // [3n] sorted
+    double* F_real;      // [3n] sorted (FP32 [3n] on the mixed path)
     double* F_bond;      // [3n] caller order
     double* part_rbl;    // [grid_rbl * 12]
     double* part_q;      // [grid_q * 3]
@@ -106,6 +121,7 @@ struct rbe_ctx {
     int64_t prof_n[RBE_NKERNELS];
     int last_launches;
     int n_sm, last_n, last_precision;
+    RblGeom rbl;
     size_t cap_atoms[20];
 };
 
@@ -182,3 +198,4 @@ void launch_vv_kick_drift(rbe_ctx* ctx, int n, double* pos, double* vel, const d
 void launch_ke_trace(rbe_ctx* ctx, int n, const double* vel, const double* mass, double accel,
                      double* trace_slot, cudaStream_t st);
 int rbl_smem_bytes(const rbe_ctx* ctx);
+int rbl_blocks_per_sm(const rbe_ctx* ctx);

@@ -112,10 +112,10 @@ def test_deterministic_and_host_pointer_path(case):
 def test_batch_covers_shell_reduces_to_truncated_sum():
     """p >= max N_S: real space equals the plain truncated sum (Eq. (2.11), N_S/p -> 1)."""
     s = systems.electrolyte()
-    out = gpu_forces(s, 3, p=600)
-    ref = oracle.rbe_forces(s.pos, s.q, s.type, s.mol, params(s, p=600), 3)
+    out = gpu_forces(s, 3, p=400)
+    ref = oracle.rbe_forces(s.pos, s.q, s.type, s.mol, params(s, p=400), 3)
     assert cond_err(out["F"], ref) < F_TOL
-    ex = oracle.ewald_exact(s.pos, s.q, s.type, s.mol, params(s, p=600), s.r_s, 0)
+    ex = oracle.ewald_exact(s.pos, s.q, s.type, s.mol, params(s, p=400), s.r_s, 0)
     assert out["E"][0] == pytest.approx(ex["E"][0], rel=1e-12)
     assert out["E"][3] == pytest.approx(ex["E"][3], rel=1e-12)
 
@@ -169,3 +169,33 @@ def test_status_errors_without_faults():
     s = systems.electrolyte(n=500, L=12.6, seed=3)
     s.pos[11, 1] = np.nan
     assert gpu_forces(s, 0)["status"] == rbe.ENONFINITE
+
+
+def test_lists_exact_at_the_radii():
+    """Pairs placed within 1e-9..1e-5 (relative) of r_c and r_s, in large and
+    small boxes: the FP32 prefilter of the list kernel must defer to the exact
+    fixed-point rule there, so the lists stay bit-exact."""
+    rng = np.random.default_rng(17)
+    for L, n_bg in ((20.0, 1500), (57.3, 6000)):
+        s = systems.electrolyte(n=2, L=L, seed=1)
+        base = rng.random((n_bg, 3)) * L
+        extra = []
+        for r0 in (s.r_c, s.r_s):
+            for d in (-1e-5, -1e-7, -1e-9, 0.0, 1e-9, 1e-7, 1e-5):
+                for _ in range(8):
+                    a = rng.random(3) * L
+                    u = rng.normal(size=3)
+                    u /= np.linalg.norm(u)
+                    extra += [a, a + r0 * (1 + d) * u]
+        pos = np.concatenate([base, np.array(extra)]) % L
+        n = len(pos) - len(pos) % 2
+        s.pos = pos[:n]
+        s.q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+        s.type = np.zeros(n, np.int32)
+        s.mass = np.ones(n)
+        out = gpu_forces(s, 5, debug_cap=128)
+        ol = oracle.lists(s.pos, params(s), 5, cap_core=128)
+        assert (out["lists"]["n_core"] == ol["n_core"]).all()
+        assert (out["lists"]["n_shell"] == ol["n_shell"]).all()
+        assert (out["lists"]["core"] == ol["core"]).all()
+        assert (out["lists"]["batch"] == ol["batch"]).all()
