@@ -192,6 +192,28 @@ int rbe_get_profile(rbe_ctx* ctx, double* ms, int64_t* launches, int reset, void
 
 const char* rbe_last_error(const rbe_ctx* ctx);
 
+/* Structure factors rho_l = sum_j q_j exp(i k_l . r_j), k_l = 2 pi m_l / box_L,
+ * for P given integer vectors m[P][3], from n atoms pos[n][3], q[n]; writes
+ * rho[P][2] (re, im).  FP64, the same arithmetic as the FP64 context path.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let the library allocate device memory (their device memory is
+ * owned by another allocator or a fixed budget, or allocation and its
+ * implicit synchronisation are not allowed where they call).  It allocates
+ * nothing: its scratch is a static device array of RBE_NOALLOC_BLOCKS x
+ * RBE_NOALLOC_PMAX complex partial sums (2 MiB) that every GPU loading the
+ * library holds until the process exits.  All pointers are device pointers
+ * owned by the caller; work is enqueued on cuda_stream and the call returns
+ * without waiting.  The first call on a device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture.  Calls share the array: calls whose kernels overlap on the GPU
+ * race.  Returns RBE_EINVAL for bad arguments, RBE_ELIMIT when P exceeds
+ * RBE_NOALLOC_PMAX, RBE_ECUDA when the set-up or a launch fails. */
+#define RBE_ELIMIT        -8   /* size beyond a compiled maximum                */
+#define RBE_NOALLOC_BLOCKS 256
+#define RBE_NOALLOC_PMAX   512
+int rbe_rho_noalloc(int n, const double* pos, const double* q, double box_L, int P, const int32_t* m,
+                    double* rho, void* cuda_stream);
+
 /* Releases the context and its device memory (after the caller's streams are
  * idle). */
 void rbe_destroy(rbe_ctx* ctx);

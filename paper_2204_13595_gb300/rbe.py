@@ -24,7 +24,9 @@ KERNELS = ["quantize", "scan", "scatter", "sort", "gather", "ksample", "rho", "r
 EXPORTS = ["rbe_create", "rbe_set_coulomb", "rbe_set_lj", "rbe_set_precision", "rbe_set_water_bonds",
            "rbe_set_capacity", "rbe_forces", "rbe_step", "rbe_sync_status", "rbe_set_debug", "rbe_get_lists",
            "rbe_get_kspace", "rbe_get_info", "rbe_set_profiling", "rbe_get_profile", "rbe_last_error",
-           "rbe_destroy"]
+           "rbe_destroy", "rbe_rho_noalloc"]
+ELIMIT = -8
+NOALLOC_BLOCKS, NOALLOC_PMAX = 256, 512
 
 
 class RbeError(RuntimeError):
@@ -57,6 +59,7 @@ def load(path: str = LIB_PATH):
     L.rbe_last_error.restype = ctypes.c_char_p
     L.rbe_destroy.argtypes = [vp]
     L.rbe_destroy.restype = None
+    L.rbe_rho_noalloc.argtypes = [i, vp, vp, d, i, vp, vp, vp]
     return L
 
 
@@ -84,6 +87,16 @@ def _stream(stream):
         return stream if isinstance(stream, int) else stream.cuda_stream
     import torch
     return torch.cuda.current_stream().cuda_stream
+
+
+def rho_noalloc(pos, q, box_L, m, rho, stream=None):
+    """rbe_rho_noalloc: structure factors into rho[P,2] without any device
+    allocation (scratch is a static device array; see include/rbe.h)."""
+    rc = lib().rbe_rho_noalloc(int(pos.shape[0]), _ptr(pos), _ptr(q), float(box_L), int(m.shape[0]), _ptr(m),
+                               _ptr(rho), _stream(stream))
+    if rc != OK:
+        raise RbeError(rc, "rbe_rho_noalloc failed" + (" (P above RBE_NOALLOC_PMAX)" if rc == ELIMIT else ""))
+    return rc
 
 
 class Context:
