@@ -228,8 +228,8 @@ def run_ours(args):
 
     clocks_proc = _clock_sampler() if rank == 0 else None
     ms_mixed, prof, launches = timed(mixed, args.steps, args.warmup, profile=True)
-    clocks = _clock_summary(clocks_proc, local) if rank == 0 else None
     ms_f64, _, _ = timed(f64, max(3, min(args.steps, 10)), max(3, min(args.warmup, 3)))
+    clocks = _clock_summary(clocks_proc, local) if rank == 0 else None
 
     # end to end through the same C ABI with pinned host buffers
     hp = torch.tensor(s.pos, dtype=torch.float64).pin_memory()

@@ -162,11 +162,13 @@ def _unbiased(orc, s, nseeds):
     Fs = np.empty((nseeds, s.n, 3))
     Fr = np.empty((nseeds, s.n, 3))
     Es = np.empty(nseeds)
+    Ws = np.empty((nseeds, 6))
     for k in range(nseeds):
         out = orc.rbe_forces(s.pos, s.q, s.type, s.mol, _params(orc, s, seed=1000 + k), 0)
         Fs[k] = out["F"]
         Fr[k] = out["F_real"] - out["corr"]
         Es[k] = out["E"].sum()
+        Ws[k] = out["W"]
     # Total force.  The Fourier part of every atom is driven by the same P
     # k samples, so the components' z-scores are strongly correlated: only
     # per-component bounds (Bonferroni max, |z|>3 fraction) are tested here.
@@ -183,6 +185,10 @@ def _unbiased(orc, s, nseeds):
     assert np.mean(np.abs(z) > 3) < 0.006
     ze = (Es.mean() - tgt["E"].sum()) / (Es.std(ddof=1) / math.sqrt(nseeds))
     assert abs(ze) < 4.0
+    # the reweighted virial is unbiased for the exact (truncated real + full
+    # reciprocal) Ewald virial, whose trace is pinned by the scaling test
+    zw = (Ws.mean(0) - tgt["W"]) / (Ws.std(0, ddof=1) / math.sqrt(nseeds))
+    assert np.abs(zw).max() < 4.5
 
 
 def test_unbiased_electrolyte_2000_seeds(orc, elec):
