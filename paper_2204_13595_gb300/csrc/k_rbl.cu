@@ -134,6 +134,32 @@ __device__ __forceinline__ uint32_t uniform_below(uint64_t u, uint32_t n)
 // Classification of one canonical segment [beg, end) of the source array:
 // FP32 distance with exact integer decision inside the rounding bands.
 template <bool SMALL>
+__device__ __forceinline__ void dist_class(const float4 pj, bool valid, float xie, float yie, float zie,
+                                           const RblGeom& g, float Lf, float invLf, bool& is_core, bool& is_shell,
+                                           bool& amb)
+{
+    float dx = pj.x - xie, dy = pj.y - yie, dz = pj.z - zie;
+    if (SMALL) {
+        dx -= Lf * rintf(dx * invLf);
+        dy -= Lf * rintf(dy * invLf);
+        dz -= Lf * rintf(dz * invLf);
+    }
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (!valid) r2 = 3.0e38f;
+    // sorted FP32 thresholds tiny2 < rc2_lo <= rc2_hi < rs2_lo <= rs2_hi,
+    // rounded outward on the host: (tiny2, rc2_lo) definite core,
+    // (rc2_hi, rs2_lo) definite shell, above rs2_hi out; the rest is decided
+    // exactly.  All decisions compare the same r2, so they partition exactly.
+    is_core = r2 > g.tiny2 && r2 < g.rc2_lo;
+    is_shell = r2 > g.rc2_hi && r2 < g.rs2_lo;
+    amb = !is_core && !is_shell && r2 <= g.rs2_hi;
+}
+
+// Classification of one canonical segment [beg, end) of the source array:
+// FP32 distance with exact integer decision inside the rounding bands.  Two
+// chunks of 32 candidates are processed per iteration (their loads and
+// arithmetic are independent) and appended in order.
+template <bool SMALL>
 __device__ __forceinline__ void classify(const float4* __restrict__ src, int beg, int end, int goff, float xie,
                                          float yie, float zie, const RblArgs& a, int i, uint4 si, int lane,
                                          unsigned lt_mask, int* core_buf, int* shell_buf, int& ncore, int& nshell,
@@ -141,47 +167,47 @@ __device__ __forceinline__ void classify(const float4* __restrict__ src, int beg
 {
     const RblGeom& g = a.g;
     const unsigned FULL = 0xffffffffu;
-    for (int bb = beg; bb < end; bb += 32) {
-        const int sidx = bb + lane;
-        const bool valid = sidx < end;
-        float4 pj = src[valid ? sidx : beg];
-        float dx = pj.x - xie, dy = pj.y - yie, dz = pj.z - zie;
-        if (SMALL) {
-            dx -= Lf * rintf(dx * invLf);
-            dy -= Lf * rintf(dy * invLf);
-            dz -= Lf * rintf(dz * invLf);
-        }
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (!valid) r2 = 3.0e38f;
-        const int gj = sidx + goff;
-        // the three decisions come from the same two differences, so the
-        // definite and ambiguous regions partition the line exactly
-        const float t1 = r2 - g.rc2_mid, t2 = r2 - g.rs2_mid;
-        bool is_core = t1 < -g.rc2_band;
-        bool is_shell = t1 > g.rc2_band && t2 < -g.rs2_band;
-        const bool amb = r2 <= g.tiny2 || fabsf(t1) <= g.rc2_band || fabsf(t2) <= g.rs2_band;
-        if (__any_sync(FULL, amb)) {
-            if (amb) {
-                unsigned long long d2 = d2_exact(si, a.s4[gj]);
-                bool other = gj != i;
-                is_core = other && d2 <= a.c.Rc2;
-                is_shell = other && d2 > a.c.Rc2 && d2 <= a.c.Rs2;
+    for (int bb = beg; bb < end; bb += 64) {
+        const int sa = bb + lane, sb = bb + 32 + lane;
+        const bool va = sa < end, vb = sb < end;
+        const float4 pa = src[va ? sa : beg];
+        const float4 pb = src[vb ? sb : beg];
+        bool ca, sha, ma, cb, shb, mb;
+        dist_class<SMALL>(pa, va, xie, yie, zie, g, Lf, invLf, ca, sha, ma);
+        dist_class<SMALL>(pb, vb, xie, yie, zie, g, Lf, invLf, cb, shb, mb);
+        const int ga = sa + goff, gb = sb + goff;
+        if (__any_sync(FULL, ma || mb)) {
+            if (ma) {
+                unsigned long long d2 = d2_exact(si, a.s4[ga]);
+                bool other = ga != i;
+                ca = other && d2 <= a.c.Rc2;
+                sha = other && d2 > a.c.Rc2 && d2 <= a.c.Rs2;
+                overlap |= other && d2 == 0ull;
+            }
+            if (mb) {
+                unsigned long long d2 = d2_exact(si, a.s4[gb]);
+                bool other = gb != i;
+                cb = other && d2 <= a.c.Rc2;
+                shb = other && d2 > a.c.Rc2 && d2 <= a.c.Rs2;
                 overlap |= other && d2 == 0ull;
             }
         }
-        const unsigned cm = __ballot_sync(FULL, is_core);
-        const unsigned sm = __ballot_sync(FULL, is_shell);
-        const int cpos = ncore + __popc(cm & lt_mask);
-        const int spos = nshell + __popc(sm & lt_mask);
-        if (is_core && cpos < a.core_cap) core_buf[cpos] = gj;
-        if (is_shell && spos < a.shell_cap) shell_buf[spos] = gj;
-        ncore += __popc(cm);
-        nshell += __popc(sm);
+        const unsigned cma = __ballot_sync(FULL, ca), sma = __ballot_sync(FULL, sha);
+        const unsigned cmb = __ballot_sync(FULL, cb), smb = __ballot_sync(FULL, shb);
+        const int nca = __popc(cma), nsa = __popc(sma);
+        const int cpa = ncore + __popc(cma & lt_mask), spa = nshell + __popc(sma & lt_mask);
+        const int cpb = ncore + nca + __popc(cmb & lt_mask), spb = nshell + nsa + __popc(smb & lt_mask);
+        if (ca && cpa < a.core_cap) core_buf[cpa] = ga;
+        if (sha && spa < a.shell_cap) shell_buf[spa] = ga;
+        if (cb && cpb < a.core_cap) core_buf[cpb] = gb;
+        if (shb && spb < a.shell_cap) shell_buf[spb] = gb;
+        ncore += nca + __popc(cmb);
+        nshell += nsa + __popc(smb);
     }
 }
 
 template <bool MIXED, bool SMALL>
-__global__ void __launch_bounds__(WARPS * 32) k_rbl(RblArgs a)
+__global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const RbeConsts& c = a.c;

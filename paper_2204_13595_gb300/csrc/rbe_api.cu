@@ -156,29 +156,34 @@ void rbl_geometry(rbe_ctx* ctx, int n)
     const int nc = c.n_cell, R = c.reach;
     g.small = (2 * R + 1 >= nc) ? 1 : 0;
     double apc = (double)n / ((double)nc * nc * nc);
-    int G = (int)lrint(48.0 / (apc > 1e-9 ? apc : 1e-9));
-    G = G < 1 ? 1 : (G > nc ? nc : G);
-    g.G = G;
-    g.cells_per_row = g.small ? nc : G + 2 * R;
     int naxis = g.small ? nc : 2 * R + 1;
     g.nrows = naxis * naxis;
-    double region = g.small ? (double)n : (double)g.cells_per_row * g.nrows * apc;
-    int cap = (int)ceil(1.3 * region + 256.0);
-    cap = (cap + 63) / 64 * 64;
-    // keep the staged block below ~120 KB of shared memory
-    int maxcap = (120 * 1024) / 16;
-    g.cap_stage = cap < maxcap ? cap : maxcap;
+    // shared memory per block: two resident blocks per SM
+    const int target = 110 * 1024;
+    int G = (int)lrint(48.0 / (apc > 1e-9 ? apc : 1e-9));
+    G = G < 1 ? 1 : (G > nc ? nc : G);
+    for (;; --G) {
+        g.G = G;
+        g.cells_per_row = g.small ? nc : G + 2 * R;
+        double region = g.small ? (double)n : (double)g.cells_per_row * g.nrows * apc;
+        int cap = (int)ceil(1.3 * region + 256.0);
+        cap = (cap + 63) / 64 * 64;
+        const int maxcap = (96 * 1024) / 16;
+        g.cap_stage = cap < maxcap ? cap : maxcap;
+        if (G == 1 || rbl_smem_bytes(ctx) <= target) break;
+    }
     auto bound = [&](double r) {
         double da = 3.0 * c.L * 1.1920928955078125e-07 + r * 5.9604644775390625e-08;
         return 4.0 * (2.0 * sqrt(3.0) * r * da + 3.0 * da * da + 3.0 * r * r * 1.1920928955078125e-07);
     };
     double rc2 = c.r_c * c.r_c, rs2 = c.r_s * c.r_s;
-    // band centres in FP32; the widths also absorb the rounding of the centres
-    g.rc2_mid = (float)rc2;
-    g.rc2_band = (float)(bound(c.r_c) + fabs((double)g.rc2_mid - rc2));
-    g.rs2_mid = (float)rs2;
-    g.rs2_band = (float)(bound(c.r_s) + fabs((double)g.rs2_mid - rs2));
-    g.tiny2 = (float)(1e-6 * rc2 + bound(0.0));
+    // thresholds rounded outward: the FP32 value of a band's lower edge is
+    // at most, and of its upper edge at least, the exact edge
+    g.rc2_lo = nextafterf((float)(rc2 - bound(c.r_c)), 0.0f);
+    g.rc2_hi = nextafterf((float)(rc2 + bound(c.r_c)), 3.0e38f);
+    g.rs2_lo = nextafterf((float)(rs2 - bound(c.r_s)), 0.0f);
+    g.rs2_hi = nextafterf((float)(rs2 + bound(c.r_s)), 3.0e38f);
+    g.tiny2 = nextafterf((float)(1e-6 * rc2 + bound(0.0)), 3.0e38f);
 }
 
 // Reallocates *p only when `count` exceeds the recorded capacity *cap.

@@ -53,8 +53,8 @@ struct RblGeom {
     int nrows;             // stencil rows of a unit
     int cap_stage;         // staged atoms that fit in shared memory
     int small;             // 1 when the stencil covers the whole box (2R+1 >= n_cell)
-    float rc2_mid, rc2_band;   // r_c^2 and the FP32 rounding bound around it (A^2)
-    float rs2_mid, rs2_band;   // same for r_s^2
+    float rc2_lo, rc2_hi;  // r_c^2 minus / plus the FP32 rounding bound (A^2), rounded outward
+    float rs2_lo, rs2_hi;  // same for r_s^2
     float tiny2;           // below this squared distance the exact test decides
 };
 
