@@ -19,6 +19,9 @@ Parity status of each function (what pins it; tests/test_oracle_*.py):
                     RBE energy gradient by finite differences (frozen draws);
                     sum_i F_i = 0; unbiasedness over seeds with the exact
                     finite-sample variance (Eqs. (2.11), (2.9), (2.14))
+  rbe_adjoint       central finite differences of the estimator with frozen
+                    draws (charges, per-type eps and sigma through the
+                    Lorentz-Berthelot pair table)
   water_bonded      central finite differences
   vv_run            time reversibility and energy of a harmonic dimer
 """
@@ -116,6 +119,8 @@ def lib():
             L.orc_rho.argtypes = [ctypes.c_int, _P(d), _P(d), d, ctypes.c_int, _P(i32), _P(d)]
             L.orc_rbe_forces.argtypes = [ctypes.c_int, _P(d), _P(d), _P(i32), _P(i32), _P(Params), u64,
                                          _P(d), _P(d), _P(d), _P(d), _P(d), _P(d), _P(i32), _P(d), _P(d)]
+            L.orc_rbe_adjoint.argtypes = [ctypes.c_int, _P(d), _P(d), _P(i32), _P(i32), _P(Params), u64, _P(d),
+                                          _P(d), _P(d), _P(d), _P(d), _P(d), _P(d)]
             L.orc_ewald_exact.argtypes = [ctypes.c_int, _P(d), _P(d), _P(i32), _P(i32), _P(Params),
                                           d, ctypes.c_int, _P(d), _P(d), _P(d)]
             L.orc_direct_coulomb.argtypes = [ctypes.c_int, _P(d), _P(d), d, d, ctypes.c_int]
@@ -233,6 +238,24 @@ def rbe_forces(pos, q, typ, mol, pr, step):
                               _ptr(corr, c), _ptr(m, ctypes.c_int32), _ptr(rh, c), _ptr(Fa, c))
     return dict(F=F, F_real=Fr, F_long=Fl, F_abs=Fa, E=E, W=W, corr=corr, m=m, rho=rh[:, 0] + 1j * rh[:, 1],
                 status=st)
+
+
+def rbe_adjoint(pos, q, typ, mol, pr, step, gF=None):
+    """Gradients of the estimator energy E and of L = sum_i gF_i . F_i with the
+    draws of (seed, step) frozen: dEdq[n], dLdq[n] and, per ordered type pair
+    (a, b), dEde, dEds, dLde, dLds [MAXT, MAXT] w.r.t. eps_ab and sigma_ab."""
+    pos, q = _f64(pos), _f64(q)
+    typ, mol = _i32(typ), _i32(mol)
+    n = pos.shape[0]
+    g = None if gF is None else _f64(gF)
+    out = {k: np.zeros(n) for k in ("dEdq", "dLdq")}
+    out.update({k: np.zeros((MAXT, MAXT)) for k in ("dEde", "dEds", "dLde", "dLds")})
+    c = ctypes.c_double
+    st = lib().orc_rbe_adjoint(n, _ptr(pos, c), _ptr(q, c), _ptr(typ, ctypes.c_int32), _ptr(mol, ctypes.c_int32),
+                               ctypes.byref(pr), step, _ptr(g, c), _ptr(out["dEdq"], c), _ptr(out["dLdq"], c),
+                               _ptr(out["dEde"], c), _ptr(out["dEds"], c), _ptr(out["dLde"], c), _ptr(out["dLds"], c))
+    out["status"] = st
+    return out
 
 
 def ewald_exact(pos, q, typ, mol, pr, r_cut, kmax):

@@ -1026,3 +1026,203 @@ int orc_vv_run(int n, double* pos, double* vel, const double* mass, const double
     }
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradients of the estimator with frozen draws (derivatives of R8 and of   */
+/* Eqs. (2.9)-(2.13) with respect to charges and LJ pair parameters)        */
+/* ------------------------------------------------------------------------ */
+/* For the estimator energy E = sum of E[0..4] and the force functional
+ * L = sum_i v_i . F_i (v = gF, may be NULL) at fixed (seed, step):
+ *   dEdq[n], dLdq[n]                      gradient w.r.t. each charge;
+ *   dEde[T*T], dEds[T*T], dLde, dLds     gradient w.r.t. the mixed pair
+ *       parameters eps_ab, sigma_ab of the ordered type pair (a, b) = (t_i, t_j)
+ *       of each pair term (T = ORC_MAXT row stride).
+ * Lists and draws are those of orc_rbe_forces at the same step.  The momentum
+ * correction enters L through the centred v_i - mean(v) on the real-space
+ * force (Eq. (2.13)); the Fourier part uses
+ *   tau_l = sum_i q_i (v_i . k_l) exp(i k_l . r_i). */
+int orc_rbe_adjoint(int n, const double* pos, const double* q, const int32_t* type, const int32_t* mol,
+                    const orc_params* pr, uint64_t step, const double* gF,
+                    double* dEdq, double* dLdq, double* dEde, double* dEds, double* dLde, double* dLds)
+{
+    grid_storage gs;
+    build_grid(n, pos, pr, &gs);
+    orc_grid g = {n, gs.s, gs.cell, gs.Rc2, gs.Rs2, gs.n_cell, gs.cell_start, gs.cell_atoms};
+    pair_consts pc;
+    make_pair_consts(pr, &pc);
+    const int T = ORC_MAXT;
+    double vbar[3] = {0, 0, 0};
+    if (gF) {
+        for (int a = 0; a < 3; ++a) {
+            ksum k = {0, 0};
+            for (int i = 0; i < n; ++i) ksum_add(&k, gF[3 * i + a]);
+            vbar[a] = ksum_get(&k) / (double)n;
+        }
+    }
+    /* per ordered pair contributions, accumulated per atom i (own part) and
+     * per (i, slot) for the transposed part, then summed sequentially */
+    double* own_E = (double*)calloc((size_t)n, sizeof(double));
+    double* own_L = (double*)calloc((size_t)n, sizeof(double));
+    typedef struct { int j; double cE, cL; } tr_rec;
+    int cap_tr = 1024;
+    tr_rec* tr = (tr_rec*)malloc(sizeof(tr_rec) * (size_t)n * (size_t)cap_tr);
+    int* ntr = (int*)calloc((size_t)n, sizeof(int));
+    double* lj_at = (double*)calloc((size_t)n * 4 * T * T, sizeof(double)); /* per atom: dEde dEds dLde dLds */
+    int status = 0;
+#pragma omp parallel
+    {
+        int32_t* cand = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+        atom_lists al;
+        al.core = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+        al.shell = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+        al.batch = (int32_t*)malloc(sizeof(int32_t) * (size_t)(pr->p + 1));
+        uint64_t* words = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(pr->p + 4));
+        uint64_t* ord = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(pr->p + 4));
+        int local_status = 0;
+#pragma omp for schedule(dynamic, 64)
+        for (int i = 0; i < n; ++i) {
+            cand_list c = {0, cand};
+            candidates_cells(&g, i, gs.reach, &c);
+            classify_and_sample(&g, i, cand, c.count, pr->p, pr->seed, step, &al, words, ord);
+            double w_shell = (al.n_shell <= pr->p) ? 1.0 : (double)al.n_shell / (double)pr->p;
+            double vt[3] = {0, 0, 0};
+            if (gF) for (int a = 0; a < 3; ++a) vt[a] = gF[3 * i + a] - vbar[a];
+            double* lj = lj_at + (size_t)i * 4 * T * T;
+            for (int part = 0; part < 2; ++part) {
+                int cnt = part == 0 ? al.n_core : al.n_batch;
+                const int32_t* ids = part == 0 ? al.core : al.batch;
+                double w = part == 0 ? 1.0 : w_shell;
+                for (int t = 0; t < cnt; ++t) {
+                    int j = ids[t];
+                    double d[3];
+                    min_image(pos + 3 * i, pos + 3 * j, pr->L, d);
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    double r = sqrt(r2);
+                    int excl = mol ? (mol[i] == mol[j]) : 0;
+                    double ar = pc.sqrt_alpha * r;
+                    double gauss = pc.two_sqrt_alpha_over_sqrt_pi * exp(-ar * ar);
+                    /* Coulomb kernel per unit k_e q_i q_j: energy phi, force h d */
+                    double phi, h;
+                    if (excl) {
+                        double er = erf(ar);
+                        phi = -er / r;
+                        h = -(gauss / r - er / r2) / r;
+                    } else {
+                        double ec = erfc(ar);
+                        phi = ec / r;
+                        h = -(ec / r2 + gauss / r) / r;
+                    }
+                    double vd = vt[0] * d[0] + vt[1] * d[1] + vt[2] * d[2];
+                    double ke = pc.coul_pref;
+                    /* own part (derivative w.r.t. q_i) */
+                    own_E[i] += 0.5 * w * ke * q[j] * phi;
+                    own_L[i] += w * ke * q[j] * h * vd;
+                    /* transposed part (derivative w.r.t. q_j) */
+                    if (ntr[i] < cap_tr) {
+                        tr[(size_t)i * cap_tr + ntr[i]].j = j;
+                        tr[(size_t)i * cap_tr + ntr[i]].cE = 0.5 * w * ke * q[i] * phi;
+                        tr[(size_t)i * cap_tr + ntr[i]].cL = w * ke * q[i] * h * vd;
+                        ntr[i]++;
+                    } else {
+                        local_status |= 1;
+                    }
+                    /* LJ pair parameters */
+                    if (!excl) {
+                        int ti = type[i], tj = type[j];
+                        double e = pc.eps_ij[ti * ORC_MAXT + tj], sg = pc.sig_ij[ti * ORC_MAXT + tj];
+                        double sr = sg / r, sr6 = pow(sr, 6.0), sr12 = sr6 * sr6;
+                        /* u = 4 e (sr12 - sr6) - shift ; h_lj d with h_lj = -e (48 sg^12/r^14 - 24 sg^6/r^8) */
+                        double du_de = 4.0 * (sr12 - sr6);
+                        double du_ds = 4.0 * e * (12.0 * sr12 - 6.0 * sr6) / sg;
+                        if (pc.shift_lj) {
+                            double ss = sg / pc.r_s, ss6 = pow(ss, 6.0), ss12 = ss6 * ss6;
+                            du_de -= 4.0 * (ss12 - ss6);
+                            du_ds -= 4.0 * e * (12.0 * ss12 - 6.0 * ss6) / sg;
+                        }
+                        double dh_de = -(48.0 * sr12 - 24.0 * sr6) / r2;
+                        double dh_ds = -e * (576.0 * sr12 - 144.0 * sr6) / (r2 * sg);
+                        int k = ti * T + tj;
+                        lj[0 * T * T + k] += 0.5 * w * du_de;
+                        lj[1 * T * T + k] += 0.5 * w * du_ds;
+                        lj[2 * T * T + k] += w * dh_de * vd;
+                        lj[3 * T * T + k] += w * dh_ds * vd;
+                    }
+                }
+            }
+        }
+#pragma omp critical
+        status |= local_status;
+        free(cand); free(al.core); free(al.shell); free(al.batch); free(words); free(ord);
+    }
+    /* Fourier part */
+    int32_t* m = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)pr->P);
+    double* rho = (double*)malloc(sizeof(double) * 2 * (size_t)pr->P);
+    double* tau = (double*)calloc(2 * (size_t)pr->P, sizeof(double));
+    orc_sample_k(pr->seed, step, pr->P, pr->alpha, pr->L, m);
+    orc_rho(n, pos, q, pr->L, pr->P, m, rho);
+    double L = pr->L, V = L * L * L;
+    double S = orc_S(pr->alpha, L);
+    double twopi_L = 2.0 * ORC_PI / L;
+    if (gF) {
+#pragma omp parallel for schedule(static)
+        for (int l = 0; l < pr->P; ++l) {
+            double kx = twopi_L * m[3 * l], ky = twopi_L * m[3 * l + 1], kz = twopi_L * m[3 * l + 2];
+            ksum re = {0, 0}, im = {0, 0};
+            for (int i = 0; i < n; ++i) {
+                double th = kx * pos[3 * i] + ky * pos[3 * i + 1] + kz * pos[3 * i + 2];
+                double vk = gF[3 * i] * kx + gF[3 * i + 1] * ky + gF[3 * i + 2] * kz;
+                ksum_add(&re, q[i] * vk * cos(th));
+                ksum_add(&im, q[i] * vk * sin(th));
+            }
+            tau[2 * l] = ksum_get(&re);
+            tau[2 * l + 1] = ksum_get(&im);
+        }
+    }
+    double self = -2.0 * pr->k_e * sqrt(pr->alpha / ORC_PI);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i) {
+        double gE = 0.0, gL = 0.0;
+        for (int l = 0; l < pr->P; ++l) {
+            double kx = twopi_L * m[3 * l], ky = twopi_L * m[3 * l + 1], kz = twopi_L * m[3 * l + 2];
+            double k2 = kx * kx + ky * ky + kz * kz;
+            double c = (S / (double)pr->P) * 4.0 * ORC_PI * pr->k_e / (V * k2);
+            double th = kx * pos[3 * i] + ky * pos[3 * i + 1] + kz * pos[3 * i + 2];
+            double cs = cos(th), sn = sin(th);
+            /* dE_k/dq_i = sum_l c_l Re(conj(rho_l) e^{i th}) */
+            gE += c * (rho[2 * l] * cs + rho[2 * l + 1] * sn);
+            if (gF) {
+                double vk = gF[3 * i] * kx + gF[3 * i + 1] * ky + gF[3 * i + 2] * kz;
+                /* Im(e^{-i th} rho) and Im(e^{i th} conj(tau)) */
+                double im1 = cs * rho[2 * l + 1] - sn * rho[2 * l];
+                double im2 = sn * tau[2 * l] - cs * tau[2 * l + 1];
+                gL += -c * (vk * im1 + im2);
+            }
+        }
+        if (dEdq) dEdq[i] = gE + self * q[i];
+        if (dLdq) dLdq[i] = gL;
+    }
+    /* pair parts: own then transposed, sequential over atoms */
+    for (int i = 0; i < n; ++i) {
+        if (dEdq) dEdq[i] += own_E[i];
+        if (dLdq) dLdq[i] += own_L[i];
+    }
+    for (int i = 0; i < n; ++i)
+        for (int t = 0; t < ntr[i]; ++t) {
+            const tr_rec* rcd = tr + (size_t)i * cap_tr + t;
+            if (dEdq) dEdq[rcd->j] += rcd->cE;
+            if (dLdq) dLdq[rcd->j] += rcd->cL;
+        }
+    double* outs[4] = {dEde, dEds, dLde, dLds};
+    for (int o = 0; o < 4; ++o) {
+        if (!outs[o]) continue;
+        for (int k = 0; k < T * T; ++k) {
+            ksum s = {0, 0};
+            for (int i = 0; i < n; ++i) ksum_add(&s, lj_at[(size_t)i * 4 * T * T + (size_t)o * T * T + k]);
+            outs[o][k] = ksum_get(&s);
+        }
+    }
+    free(own_E); free(own_L); free(tr); free(ntr); free(lj_at);
+    free(m); free(rho); free(tau);
+    free_grid(&gs);
+    return status;
+}
