@@ -142,6 +142,24 @@ int rbe_step(rbe_ctx* ctx, uint64_t step0, int nsteps, double dt, double accel, 
              double* pos, double* vel, const double* mass, const double* q, const int32_t* type,
              const int32_t* mol, double* F, double* energy_trace, void* cuda_stream);
 
+/* Gradients of the force step at MD step `step` with its random draws frozen
+ * (the same lists, shell batches and k samples as rbe_forces at that step;
+ * the paper's estimator, Eqs. (2.9)-(2.13), differentiated term by term):
+ *   dEdq[n]   = dE/dq_i, E the sum of the RBE_E_REAL..RBE_E_EXCL components;
+ *   dLdq[n]   = dL/dq_i with L = sum_i gF_i . F_i (a vector-Jacobian product
+ *               of the non-bonded force; gF may be NULL for L = 0);
+ *   dEdeps, dEdsig, dLdeps, dLdsig [ntypes] = the same w.r.t. the per-type
+ *               LJ parameters through Lorentz-Berthelot mixing (host arrays;
+ *               the call waits; a type with eps = 0 paired with eps > 0 has
+ *               an infinite eps derivative, reported as HUGE_VAL).
+ * pos, q, type, mol, gF, dEdq, dLdq are device pointers; any output may be
+ * NULL.  Pair terms are recomputed, not stored; the part of a pair that
+ * belongs to the other atom's charge is added atomically, so dEdq and dLdq
+ * are exact to rounding but not bitwise reproducible run to run. */
+int rbe_adjoint(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const double* q, const int32_t* type,
+                const int32_t* mol, const double* gF, double* dEdq, double* dLdq, double* dEdeps, double* dEdsig,
+                double* dLdeps, double* dLdsig, void* cuda_stream);
+
 /* Waits for cuda_stream, returns the first latched device error (or RBE_OK)
  * and clears the status word. */
 int rbe_sync_status(rbe_ctx* ctx, void* cuda_stream);

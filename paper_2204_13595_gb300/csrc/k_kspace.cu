@@ -442,3 +442,213 @@ void launch_ke_trace(rbe_ctx* ctx, int n, const double* vel, const double* mass,
     k_trace<<<1, TPB, 0, st>>>(ctx->ke_part, ctx->grid_q, ctx->totals, accel, trace_slot);
     prof_end(ctx, RBE_K_MISC, st);
 }
+
+// ---------------------------------------------------------------------------
+// Adjoint of the force step (gradients with the draws frozen)
+// ---------------------------------------------------------------------------
+namespace {
+
+// Upstream force gradient into sorted order, with block sums for its mean.
+__global__ void __launch_bounds__(TPB) k_gather_v(int n, const int* __restrict__ perm, const double* __restrict__ gF,
+                                                  double* __restrict__ vs, double* __restrict__ part_v)
+{
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int k = blockIdx.x * TPB + threadIdx.x; k < n; k += gridDim.x * TPB) {
+        const int i = perm[k];
+        for (int a = 0; a < 3; ++a) {
+            const double v = gF ? gF[3 * (size_t)i + a] : 0.0;
+            vs[3 * (size_t)k + a] = v;
+            s[a] += v;
+        }
+    }
+    __shared__ double red[3][TPB / 32];
+    for (int a = 0; a < 3; ++a) s[a] = warp_sum(s[a]);
+    if ((threadIdx.x & 31) == 0)
+        for (int a = 0; a < 3; ++a) red[a][threadIdx.x >> 5] = s[a];
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < TPB / 32; ++w) t += red[threadIdx.x][w];
+        part_v[blockIdx.x * 3 + threadIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_vbar(int n, int nblk, const double* __restrict__ part_v,
+                                              double* __restrict__ totals)
+{
+    __shared__ double sh[TPB];
+    for (int a = 0; a < 3; ++a) {
+        const double s = block_sum_col(part_v, nblk, 3, a, sh);
+        if (threadIdx.x == 0) totals[16 + a] = s / (double)n;
+    }
+}
+
+// tau_l = sum_i q_i (v_i . k_l) exp(i k_l . r_i): block partials, as k_rho.
+template <bool MIXED>
+__global__ void k_tau(int n, int chunk, RbeConsts c, const uint4* __restrict__ s4, const double4_32a* __restrict__ p4,
+                      const double* __restrict__ vs, const int4* __restrict__ km, const double4_32a* __restrict__ kv,
+                      double2* __restrict__ part)
+{
+    __shared__ double4_32a tile_d[TILE];
+    __shared__ double tile_v[TILE][3];
+    __shared__ uint4 tile_u[MIXED ? TILE : 1];
+    const int b0 = blockIdx.x * chunk;
+    const int b1 = min(n, b0 + chunk);
+    for (int l0 = 0; l0 < c.P; l0 += blockDim.x) {
+        const int l = l0 + threadIdx.x;
+        const bool act = l < c.P;
+        const int4 m = act ? km[l] : make_int4(0, 0, 0, 0);
+        const double4_32a k = act ? kv[l] : make_double4_32a(0, 0, 0, 0);
+        double re = 0.0, im = 0.0;
+        for (int t0 = b0; t0 < b1; t0 += TILE) {
+            const int cnt = min(TILE, b1 - t0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+                tile_d[e] = p4[t0 + e];
+                if (MIXED) tile_u[e] = s4[t0 + e];
+                for (int a = 0; a < 3; ++a) tile_v[e][a] = vs[3 * (size_t)(t0 + e) + a];
+            }
+            __syncthreads();
+            if (act) {
+                for (int e = 0; e < cnt; ++e) {
+                    const double4_32a p = tile_d[e];
+                    const double wv = p.w * (k.x * tile_v[e][0] + k.y * tile_v[e][1] + k.z * tile_v[e][2]);
+                    double sn, cs;
+                    if (MIXED) {
+                        const uint4 s = tile_u[e];
+                        const uint32_t ph = (uint32_t)m.x * s.x + (uint32_t)m.y * s.y + (uint32_t)m.z * s.z;
+                        float fs, fc;
+                        __sincosf((float)(int)ph * 1.4629180792671596e-09f, &fs, &fc);
+                        sn = fs; cs = fc;
+                    } else {
+                        double t = ((double)m.x * p.x + (double)m.y * p.y + (double)m.z * p.z) * c.invL;
+                        t -= rint(t);
+                        sincospi(2.0 * t, &sn, &cs);
+                    }
+                    re += wv * cs;
+                    im += wv * sn;
+                }
+            }
+        }
+        if (act) part[(size_t)blockIdx.x * c.P + l] = make_double2(re, im);
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_tau_sum(int nblk, int P, const double2* __restrict__ part,
+                                                 double2* __restrict__ tau)
+{
+    const int l = blockIdx.x * TPB + threadIdx.x;
+    if (l >= P) return;
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        const double2 v = part[(size_t)b * P + l];
+        re += v.x;
+        im += v.y;
+    }
+    tau[l] = make_double2(re, im);
+}
+
+// Per atom: Fourier and self parts, plus the pair parts, into caller order.
+//   dE_k/dq_i = sum_l c_l Re(conj(rho_l) e^{i th}),  dE_self/dq_i = -2 k_e sqrt(a/pi) q_i
+//   dL/dq_i  -= sum_l c_l [(v_i . k_l) Im(e^{-i th} rho_l) + Im(e^{i th} conj(tau_l))]
+template <bool MIXED>
+__global__ void __launch_bounds__(TPB) k_kadj(int n, RbeConsts c, const uint4* __restrict__ s4,
+                                              const double4_32a* __restrict__ p4, const int* __restrict__ perm,
+                                              const int4* __restrict__ km, const double4_32a* __restrict__ kv,
+                                              const double2* __restrict__ rho, const double2* __restrict__ tau,
+                                              const double* __restrict__ vs, const double* __restrict__ gq_own,
+                                              const double* __restrict__ gq_tr, double* __restrict__ dEdq,
+                                              double* __restrict__ dLdq)
+{
+    constexpr int KT = 128;
+    __shared__ double4_32a sk[KT];
+    __shared__ int4 sm[KT];
+    __shared__ double4_32a srt[KT];   // rho re, rho im, tau re, tau im
+    const int i = blockIdx.x * TPB + threadIdx.x;
+    const bool act = i < n;
+    const double4_32a pi = act ? p4[i] : make_double4_32a(0, 0, 0, 0);
+    const uint4 si = act ? s4[i] : make_uint4(0, 0, 0, 0);
+    const double vx = act ? vs[3 * (size_t)i] : 0.0, vy = act ? vs[3 * (size_t)i + 1] : 0.0;
+    const double vz = act ? vs[3 * (size_t)i + 2] : 0.0;
+    double gE = 0.0, gL = 0.0;
+    for (int l0 = 0; l0 < c.P; l0 += KT) {
+        const int cnt = min(KT, c.P - l0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += TPB) {
+            sk[k] = kv[l0 + k];
+            sm[k] = km[l0 + k];
+            const double2 r = rho[l0 + k], t = tau[l0 + k];
+            srt[k] = make_double4_32a(r.x, r.y, t.x, t.y);
+        }
+        __syncthreads();
+        if (act) {
+            for (int k = 0; k < cnt; ++k) {
+                const double4_32a kk = sk[k];
+                double sn, cs;
+                if (MIXED) {
+                    const int4 m = sm[k];
+                    const uint32_t ph = (uint32_t)m.x * si.x + (uint32_t)m.y * si.y + (uint32_t)m.z * si.z;
+                    float fs, fc;
+                    __sincosf((float)(int)ph * 1.4629180792671596e-09f, &fs, &fc);
+                    sn = fs; cs = fc;
+                } else {
+                    const int4 m = sm[k];
+                    double t = ((double)m.x * pi.x + (double)m.y * pi.y + (double)m.z * pi.z) * c.invL;
+                    t -= rint(t);
+                    sincospi(2.0 * t, &sn, &cs);
+                }
+                const double4_32a rt = srt[k];
+                gE += kk.w * (rt.x * cs + rt.y * sn);
+                const double vk = vx * kk.x + vy * kk.y + vz * kk.z;
+                const double im1 = cs * rt.y - sn * rt.x;
+                const double im2 = sn * rt.z - cs * rt.w;
+                gL -= kk.w * (vk * im1 + im2);
+            }
+        }
+    }
+    if (!act) return;
+    const int gi = perm[i];
+    const double self = -2.0 * c.k_e * sqrt(c.alpha / 3.14159265358979323846) * pi.w;
+    if (dEdq) dEdq[gi] = gE + self + gq_own[2 * (size_t)i] + gq_tr[2 * (size_t)i];
+    if (dLdq) dLdq[gi] = gL + gq_own[2 * (size_t)i + 1] + gq_tr[2 * (size_t)i + 1];
+}
+
+}  // namespace
+
+void launch_adj_prep(rbe_ctx* ctx, int n, const double* gF, cudaStream_t st)
+{
+    prof_begin(ctx, RBE_K_MISC, st);
+    k_gather_v<<<ctx->grid_q, TPB, 0, st>>>(n, ctx->perm, gF, ctx->vs, ctx->part_v);
+    prof_end(ctx, RBE_K_MISC, st);
+    prof_begin(ctx, RBE_K_MISC, st);
+    k_vbar<<<1, TPB, 0, st>>>(n, ctx->grid_q, ctx->part_v, ctx->totals);
+    prof_end(ctx, RBE_K_MISC, st);
+    const int P = ctx->c.P;
+    const int threads = ((P < 1024 ? P : 1024) + 31) / 32 * 32;
+    const int chunk = (n + ctx->grid_rho - 1) / ctx->grid_rho;
+    prof_begin(ctx, RBE_K_RHO, st);
+    if (ctx->precision == RBE_MIXED)
+        k_tau<true><<<ctx->grid_rho, threads, 0, st>>>(n, chunk, ctx->c, ctx->s4, ctx->p4, ctx->vs, ctx->km, ctx->kv,
+                                                       ctx->tau_part);
+    else
+        k_tau<false><<<ctx->grid_rho, threads, 0, st>>>(n, chunk, ctx->c, ctx->s4, ctx->p4, ctx->vs, ctx->km, ctx->kv,
+                                                        ctx->tau_part);
+    prof_end(ctx, RBE_K_RHO, st);
+    prof_begin(ctx, RBE_K_RHOSUM, st);
+    k_tau_sum<<<(P + TPB - 1) / TPB, TPB, 0, st>>>(ctx->grid_rho, P, ctx->tau_part, ctx->tau);
+    prof_end(ctx, RBE_K_RHOSUM, st);
+}
+
+void launch_adj_final(rbe_ctx* ctx, int n, double* dEdq, double* dLdq, cudaStream_t st)
+{
+    prof_begin(ctx, RBE_K_KFORCE, st);
+    if (ctx->precision == RBE_MIXED)
+        k_kadj<true><<<(n + TPB - 1) / TPB, TPB, 0, st>>>(n, ctx->c, ctx->s4, ctx->p4, ctx->perm, ctx->km, ctx->kv,
+                                                           ctx->rho, ctx->tau, ctx->vs, ctx->gq_own, ctx->gq_tr, dEdq,
+                                                           dLdq);
+    else
+        k_kadj<false><<<(n + TPB - 1) / TPB, TPB, 0, st>>>(n, ctx->c, ctx->s4, ctx->p4, ctx->perm, ctx->km, ctx->kv,
+                                                            ctx->rho, ctx->tau, ctx->vs, ctx->gq_own, ctx->gq_tr, dEdq,
+                                                            dLdq);
+    prof_end(ctx, RBE_K_KFORCE, st);
+}

@@ -54,6 +54,12 @@ struct RblArgs {
     RblGeom g;
     int core_cap, shell_cap;
     int debug, dbg_cap;
+    // adjoint mode
+    const double* __restrict__ vs;       // [3n] upstream gradient, sorted
+    const double* __restrict__ vbar;     // [3] its mean
+    double* __restrict__ gq_own;         // [2n]
+    double* __restrict__ gq_tr;          // [2n]
+    double* __restrict__ part_lj;        // [grid * 4 * nt2]
     int* __restrict__ dbg_ncore;
     int* __restrict__ dbg_nshell;
     int* __restrict__ dbg_core;
@@ -93,7 +99,7 @@ __host__ __device__ inline SmemLayout smem_layout(const RblGeom& g, int nt2, int
     L.cellpos = o;
     o = up16(o + sizeof(int) * (size_t)g.nrows * (size_t)(g.cells_per_row + 1));
     L.lj = o;
-    o = up16(o + sizeof(double) * 3 * (size_t)nt2);
+    o = up16(o + sizeof(double) * 11 * (size_t)nt2);
     L.warps = o;
     L.wbytes = up16(sizeof(uint64_t) * (size_t)p_pad * L.ga + sizeof(int) * (size_t)(core_cap + shell_cap + p_pad));
     L.total = o + L.wbytes * WARPS;
@@ -206,7 +212,7 @@ __device__ __forceinline__ void classify(const float4* __restrict__ src, int beg
     }
 }
 
-template <bool MIXED, bool SMALL>
+template <bool MIXED, bool SMALL, bool ADJ>
 __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -231,6 +237,11 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
     double* s_c12 = reinterpret_cast<double*>(smem + lay.lj);
     double* s_c6 = s_c12 + nt2;
     double* s_sh = s_c6 + nt2;
+    double* s_eps = s_sh + nt2;             // adjoint: eps_ab, sigma_ab, d shift
+    double* s_sig = s_eps + nt2;
+    double* s_dsde = s_sig + nt2;
+    double* s_dsds = s_dsde + nt2;
+    double* s_glj = s_dsds + nt2;           // adjoint: [4][nt2] block accumulators
     uint64_t* words = reinterpret_cast<uint64_t*>(smem + lay.warps + lay.wbytes * wib);   // [ga][p_pad]
     int* core_buf = reinterpret_cast<int*>(words + (size_t)p_pad * lay.ga);
     int* shell_buf = core_buf + a.core_cap;
@@ -243,6 +254,13 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
         s_c12[t] = a.lj->c12[ti * RBE_MAXT + tj];
         s_c6[t] = a.lj->c6[ti * RBE_MAXT + tj];
         s_sh[t] = a.lj->shift[ti * RBE_MAXT + tj];
+        if (ADJ) {
+            s_eps[t] = a.lj->eps[ti * RBE_MAXT + tj];
+            s_sig[t] = a.lj->sig[ti * RBE_MAXT + tj];
+            s_dsde[t] = a.lj->dshift_de[ti * RBE_MAXT + tj];
+            s_dsds[t] = a.lj->dshift_ds[ti * RBE_MAXT + tj];
+            for (int q = 0; q < 4; ++q) s_glj[q * nt2 + t] = 0.0;
+        }
     }
 
     const int naxis = SMALL ? nc : 2 * R + 1;
@@ -513,7 +531,91 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
             // same-molecule pair, the Ewald exclusion correction) and LJ.
             const int npairs = ncore_c + nb;
             const int2 ti = a.tm[i];
-            if (MIXED) {
+            if constexpr (ADJ) {
+                // Gradients of E = 1/2 sum w_ij u_ij and of L = sum_i vt_i . F_real_i
+                // (vt = v - mean v, which carries the momentum correction of
+                // Eq. (2.13)) with respect to the charges and the LJ pair
+                // parameters; the part of a pair that belongs to q_j is added
+                // to atom j's slot atomically.
+                const double vtx = a.vs[3 * (size_t)i] - a.vbar[0];
+                const double vty = a.vs[3 * (size_t)i + 1] - a.vbar[1];
+                const double vtz = a.vs[3 * (size_t)i + 2] - a.vbar[2];
+                const double ke = c.k_e;
+                const double4_32a pi = a.p4[i];
+                double gE = 0.0, gL = 0.0;
+                for (int t = lane; t < npairs; t += 32) {
+                    int j;
+                    double w;
+                    if (t < ncore_c) { j = core_buf[t]; w = 1.0; }
+                    else {
+                        const int k = t - ncore_c;
+                        const int ord = sample ? sel[k] : k;
+                        j = shell_buf[min(ord, a.shell_cap - 1)];
+                        w = sample ? (double)nshell / (double)p : 1.0;
+                    }
+                    const int2 tj = a.tm[j];
+                    const bool ex = ti.y == tj.y;
+                    double dx, dy, dz, qj, phi, h, r2;
+                    if (MIXED) {
+                        const uint4 sj = a.s4[j];
+                        const float fdx = (float)(int)(sj.x - si.x) * c.Lfix;
+                        const float fdy = (float)(int)(sj.y - si.y) * c.Lfix;
+                        const float fdz = (float)(int)(sj.z - si.z) * c.Lfix;
+                        const float fr2 = fdx * fdx + fdy * fdy + fdz * fdz;
+                        const float rinv = rsqrtf(fr2);
+                        const float ar = (float)c.sqrt_alpha * fr2 * rinv;
+                        const float gauss = (float)c.two_sqrt_alpha_over_sqrt_pi * __expf(-ar * ar);
+                        const float ec = erfcf(ar) - (ex ? 1.0f : 0.0f);
+                        phi = (double)(ec * rinv);
+                        h = (double)(-(ec * rinv + gauss) * rinv * rinv);
+                        dx = fdx; dy = fdy; dz = fdz; r2 = fr2;
+                        qj = (double)__uint_as_float(sj.w);
+                    } else {
+                        const double4_32a pj = a.p4[j];
+                        dx = pj.x - pi.x; dy = pj.y - pi.y; dz = pj.z - pi.z;
+                        dx -= c.L * rint(dx * c.invL);
+                        dy -= c.L * rint(dy * c.invL);
+                        dz -= c.L * rint(dz * c.invL);
+                        r2 = dx * dx + dy * dy + dz * dz;
+                        const double rr = sqrt(r2);
+                        const double rinv = 1.0 / rr;
+                        const double ar = c.sqrt_alpha * rr;
+                        const double gauss = c.two_sqrt_alpha_over_sqrt_pi * exp(-ar * ar);
+                        const double ec = ex ? -erf(ar) : erfc(ar);
+                        phi = ec * rinv;
+                        h = -(ec * rinv + gauss) * rinv * rinv;
+                        qj = pj.w;
+                    }
+                    const double qi = MIXED ? (double)__uint_as_float(si.w) : pi.w;
+                    const double vd = vtx * dx + vty * dy + vtz * dz;
+                    gE += 0.5 * w * ke * qj * phi;
+                    gL += w * ke * qj * h * vd;
+                    atomicAdd(&a.gq_tr[2 * (size_t)j], 0.5 * w * ke * qi * phi);
+                    atomicAdd(&a.gq_tr[2 * (size_t)j + 1], w * ke * qi * h * vd);
+                    if (!ex) {
+                        const int tt = ti.x * c.ntypes + tj.x;
+                        const double e = s_eps[tt], sg = s_sig[tt];
+                        if (e != 0.0) {
+                            const double ir2 = 1.0 / r2;
+                            const double sr2 = sg * sg * ir2, sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
+                            const double du_de = 4.0 * (sr12 - sr6) - s_dsde[tt];
+                            const double du_ds = 4.0 * e * (12.0 * sr12 - 6.0 * sr6) / sg - s_dsds[tt];
+                            const double dh_de = -(48.0 * sr12 - 24.0 * sr6) * ir2;
+                            const double dh_ds = -e * (576.0 * sr12 - 144.0 * sr6) * ir2 / sg;
+                            atomicAdd(&s_glj[0 * nt2 + tt], 0.5 * w * du_de);
+                            atomicAdd(&s_glj[1 * nt2 + tt], 0.5 * w * du_ds);
+                            atomicAdd(&s_glj[2 * nt2 + tt], w * dh_de * vd);
+                            atomicAdd(&s_glj[3 * nt2 + tt], w * dh_ds * vd);
+                        }
+                    }
+                }
+                gE = warp_sum(gE);
+                gL = warp_sum(gL);
+                if (lane == 0) {
+                    a.gq_own[2 * (size_t)i] = gE;
+                    a.gq_own[2 * (size_t)i + 1] = gL;
+                }
+            } else if (MIXED) {
                 const float wsh = sample ? (float)nshell / (float)p : 1.0f;
                 const float qi = __uint_as_float(si.w);
                 const float kef = (float)c.k_e, saf = (float)c.sqrt_alpha, tsaf = (float)c.two_sqrt_alpha_over_sqrt_pi;
@@ -672,22 +774,27 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
         for (int w = 0; w < WARPS; ++w) s += red[w][threadIdx.x];
         a.part[blockIdx.x * RBE_NPART_RBL + threadIdx.x] = s;
     }
+    if (ADJ)
+        for (int t = threadIdx.x; t < 4 * nt2; t += blockDim.x)
+            a.part_lj[(size_t)blockIdx.x * 4 * nt2 + t] = s_glj[t];
 }
 
-template <bool MIXED, bool SMALL>
+template <bool MIXED, bool SMALL, bool ADJ>
 void launch_t(rbe_ctx* ctx, const RblArgs& a, int smem, cudaStream_t st)
 {
-    cudaFuncSetAttribute(k_rbl<MIXED, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_rbl<MIXED, SMALL><<<ctx->grid_rbl, WARPS * 32, smem, st>>>(a);
+    cudaFuncSetAttribute(k_rbl<MIXED, SMALL, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_rbl<MIXED, SMALL, ADJ><<<ctx->grid_rbl, WARPS * 32, smem, st>>>(a);
 }
 
 template <bool MIXED, bool SMALL>
 int occupancy_t(int smem)
 {
-    int nb = 0;
-    cudaFuncSetAttribute(k_rbl<MIXED, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbl<MIXED, SMALL>, WARPS * 32, smem);
-    return nb;
+    int nb = 0, nb2 = 0;
+    cudaFuncSetAttribute(k_rbl<MIXED, SMALL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbl<MIXED, SMALL, false>, WARPS * 32, smem);
+    cudaFuncSetAttribute(k_rbl<MIXED, SMALL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_rbl<MIXED, SMALL, true>, WARPS * 32, smem);
+    return nb < nb2 ? nb : nb2;
 }
 
 }  // namespace
@@ -698,7 +805,7 @@ int rbl_smem_bytes(const rbe_ctx* ctx)
     return (int)smem_layout(ctx->rbl, nt2, ctx->c.p, ctx->core_cap, ctx->shell_cap).total;
 }
 
-void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st)
+void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st, bool adjoint)
 {
     RblArgs a;
     a.n = n;
@@ -711,15 +818,18 @@ void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st)
     a.core_cap = ctx->core_cap; a.shell_cap = ctx->shell_cap;
     a.debug = ctx->debug; a.dbg_cap = ctx->dbg_cap_core;
     a.dbg_ncore = ctx->dbg_ncore; a.dbg_nshell = ctx->dbg_nshell; a.dbg_core = ctx->dbg_core; a.dbg_batch = ctx->dbg_batch;
+    a.vs = ctx->vs; a.vbar = ctx->totals + 16; a.gq_own = ctx->gq_own; a.gq_tr = ctx->gq_tr; a.part_lj = ctx->part_lj;
+    if (adjoint) a.debug = 0;
     int smem = rbl_smem_bytes(ctx);
     prof_begin(ctx, RBE_K_RBL, st);
     const bool small = ctx->rbl.small;
-    if (ctx->precision == RBE_MIXED) {
-        if (small) launch_t<true, true>(ctx, a, smem, st);
-        else launch_t<true, false>(ctx, a, smem, st);
+    const bool mixed = ctx->precision == RBE_MIXED;
+    if (adjoint) {
+        if (mixed) { if (small) launch_t<true, true, true>(ctx, a, smem, st); else launch_t<true, false, true>(ctx, a, smem, st); }
+        else { if (small) launch_t<false, true, true>(ctx, a, smem, st); else launch_t<false, false, true>(ctx, a, smem, st); }
     } else {
-        if (small) launch_t<false, true>(ctx, a, smem, st);
-        else launch_t<false, false>(ctx, a, smem, st);
+        if (mixed) { if (small) launch_t<true, true, false>(ctx, a, smem, st); else launch_t<true, false, false>(ctx, a, smem, st); }
+        else { if (small) launch_t<false, true, false>(ctx, a, smem, st); else launch_t<false, false, false>(ctx, a, smem, st); }
     }
     prof_end(ctx, RBE_K_RBL, st);
 }

@@ -99,7 +99,8 @@ void free_dev(rbe_ctx* ctx)
                     ctx->F_real, ctx->F_bond, ctx->part_rbl, ctx->part_q, ctx->part_bond, ctx->kT, ctx->km, ctx->kv,
                     ctx->rho_part, ctx->rho, ctx->totals, ctx->status, ctx->lj, ctx->dbg_ncore, ctx->dbg_nshell,
                     ctx->dbg_core, ctx->dbg_batch, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
-                    ctx->ke_part};
+                    ctx->ke_part, ctx->vs, ctx->gq_own, ctx->gq_tr, ctx->part_lj, ctx->part_v, ctx->tau_part,
+                    ctx->tau};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ctx->s4 = nullptr; ctx->f4 = nullptr; ctx->p4 = nullptr; ctx->tm = nullptr; ctx->perm = nullptr; ctx->cell_of = nullptr;
@@ -109,8 +110,11 @@ void free_dev(rbe_ctx* ctx)
     ctx->totals = nullptr; ctx->status = nullptr; ctx->lj = nullptr; ctx->dbg_ncore = nullptr;
     ctx->dbg_nshell = nullptr; ctx->dbg_core = nullptr; ctx->dbg_batch = nullptr; ctx->h_pos = nullptr;
     ctx->h_q = nullptr; ctx->h_type = nullptr; ctx->h_mol = nullptr; ctx->h_F = nullptr; ctx->ke_part = nullptr;
+    ctx->vs = nullptr; ctx->gq_own = nullptr; ctx->gq_tr = nullptr; ctx->part_lj = nullptr; ctx->part_v = nullptr;
+    ctx->tau_part = nullptr; ctx->tau = nullptr;
     ctx->n_cap = 0; ctx->dbg_n_cap = 0; ctx->h_cap = 0;
     for (int k = 0; k < 20; ++k) ctx->cap_atoms[k] = 0;
+    for (int k = 0; k < 8; ++k) ctx->cap_adj[k] = 0;
 }
 
 template <typename T>
@@ -237,6 +241,10 @@ int ensure(rbe_ctx* ctx, int n)
                 h.c6[a * RBE_MAXT + b] = 4.0 * e * s6;
                 double sr6 = pow(s / ctx->c.r_s, 6.0);
                 h.shift[a * RBE_MAXT + b] = ctx->c.shift_lj ? 4.0 * e * (sr6 * sr6 - sr6) : 0.0;
+                h.eps[a * RBE_MAXT + b] = e;
+                h.sig[a * RBE_MAXT + b] = s;
+                h.dshift_de[a * RBE_MAXT + b] = ctx->c.shift_lj ? 4.0 * (sr6 * sr6 - sr6) : 0.0;
+                h.dshift_ds[a * RBE_MAXT + b] = ctx->c.shift_lj ? 4.0 * e * (12.0 * sr6 * sr6 - 6.0 * sr6) / s : 0.0;
             }
         CUDA_TRY(ctx, cudaMemcpy(ctx->lj, &h, sizeof(h), cudaMemcpyHostToDevice));
         ctx->lj_dirty = 0;
@@ -541,6 +549,74 @@ int rbe_step(rbe_ctx* ctx, uint64_t step0, int nsteps, double dt, double accel, 
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(ctx, RBE_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return RBE_OK;
+}
+
+int rbe_adjoint(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const double* q, const int32_t* type,
+                const int32_t* mol, const double* gF, double* dEdq, double* dLdq, double* dEdeps, double* dEdsig,
+                double* dLdeps, double* dLdsig, void* cuda_stream)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (n < 1 || !pos || !q) return set_err(ctx, RBE_EINVAL, "n >= 1 and pos, q are required");
+    if (!is_device_ptr(pos) || !is_device_ptr(q) || (type && !is_device_ptr(type)) || (mol && !is_device_ptr(mol)) ||
+        (gF && !is_device_ptr(gF)) || (dEdq && !is_device_ptr(dEdq)) || (dLdq && !is_device_ptr(dLdq)))
+        return set_err(ctx, RBE_EINVAL, "rbe_adjoint takes device pointers for per-atom arrays");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc = ensure(ctx, n);
+    if (rc) return rc;
+    const int nt2 = ctx->c.ntypes * ctx->c.ntypes;
+    if ((rc = grow(ctx, &ctx->vs, &ctx->cap_atoms[18], 3 * (size_t)n))) return rc;
+    if ((rc = grow(ctx, &ctx->gq_own, &ctx->cap_atoms[19], 2 * (size_t)n))) return rc;
+    if ((rc = grow(ctx, &ctx->gq_tr, &ctx->cap_adj[0], 2 * (size_t)n))) return rc;
+    if ((rc = grow(ctx, &ctx->part_lj, &ctx->cap_adj[1], (size_t)ctx->grid_rbl * 4 * nt2))) return rc;
+    if ((rc = grow(ctx, &ctx->part_v, &ctx->cap_adj[2], (size_t)ctx->grid_q * 3))) return rc;
+    if ((rc = grow(ctx, &ctx->tau_part, &ctx->cap_adj[3], (size_t)ctx->grid_rho * ctx->c.P))) return rc;
+    if ((rc = grow(ctx, &ctx->tau, &ctx->cap_adj[4], (size_t)ctx->c.P))) return rc;
+    ctx->last_launches = 0;
+    // the forward set-up of the same step: identical lists, batches, k samples
+    launch_quantize_count(ctx, n, pos, q, st);
+    launch_scan(ctx, st);
+    launch_scatter_sort_gather(ctx, n, pos, q, type, mol, st);
+    launch_ksample(ctx, step, st);
+    launch_rho(ctx, n, st);
+    launch_adj_prep(ctx, n, gF, st);
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->gq_tr, 0, sizeof(double) * 2 * (size_t)n, st));
+    launch_rbl(ctx, n, step, st, true);
+    launch_adj_final(ctx, n, dEdq, dLdq, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(ctx, RBE_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    // LJ pair-parameter partials: fixed-order sum, then the Lorentz-Berthelot
+    // chain rule to per-type parameters (eps_ab = sqrt(eps_a eps_b),
+    // sigma_ab = (sigma_a + sigma_b)/2)
+    std::vector<double> part((size_t)ctx->grid_rbl * 4 * nt2);
+    CUDA_TRY(ctx, cudaMemcpyAsync(part.data(), ctx->part_lj, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    const int T = ctx->c.ntypes;
+    std::vector<double> g(4 * (size_t)nt2, 0.0);
+    for (int b = 0; b < ctx->grid_rbl; ++b)
+        for (int k = 0; k < 4 * nt2; ++k) g[k] += part[(size_t)b * 4 * nt2 + k];
+    double* outs[4] = {dEdeps, dEdsig, dLdeps, dLdsig};
+    for (int o = 0; o < 4; ++o) {
+        if (!outs[o]) continue;
+        const double* go = g.data() + (size_t)o * nt2;
+        for (int a2 = 0; a2 < T; ++a2) {
+            double acc = 0.0;
+            for (int b2 = 0; b2 < T; ++b2) {
+                const double sym = a2 == b2 ? go[a2 * T + a2] : go[a2 * T + b2] + go[b2 * T + a2];
+                double dpar;
+                if (o == 0 || o == 2) {   // eps
+                    if (a2 == b2) dpar = 1.0;
+                    else if (ctx->eps[b2] == 0.0) dpar = 0.0;
+                    else if (ctx->eps[a2] == 0.0) dpar = HUGE_VAL;
+                    else dpar = ctx->eps[b2] / (2.0 * sqrt(ctx->eps[a2] * ctx->eps[b2]));
+                } else {                  // sigma
+                    dpar = a2 == b2 ? 1.0 : 0.5;
+                }
+                if (sym != 0.0) acc += sym * dpar;
+            }
+            outs[o][a2] = acc;
+        }
+    }
     return RBE_OK;
 }
 

@@ -58,11 +58,17 @@ struct RblGeom {
     float tiny2;           // below this squared distance the exact test decides
 };
 
-// LJ pair table (device): c12 = 4 eps sig^12, c6 = 4 eps sig^6, shift
+// LJ pair table (device): c12 = 4 eps sig^12, c6 = 4 eps sig^6, shift; for
+// the adjoint also the mixed eps_ab, sigma_ab and the derivatives of the
+// energy shift with respect to them
 struct RbeLJ {
     double c12[RBE_MAXT * RBE_MAXT];
     double c6[RBE_MAXT * RBE_MAXT];
     double shift[RBE_MAXT * RBE_MAXT];
+    double eps[RBE_MAXT * RBE_MAXT];
+    double sig[RBE_MAXT * RBE_MAXT];
+    double dshift_de[RBE_MAXT * RBE_MAXT];
+    double dshift_ds[RBE_MAXT * RBE_MAXT];
 };
 
 struct rbe_ctx {
@@ -115,6 +121,14 @@ struct rbe_ctx {
     double* h_pos; double* h_q; int* h_type; int* h_mol; double* h_F;
     int h_cap;
     double* ke_part;     // [grid_q] kinetic energy partials (rbe_step)
+    // adjoint buffers (rbe_adjoint)
+    double* vs;          // [3n] upstream force gradient, sorted order
+    double* gq_own;      // [2n] dE/dq, dL/dq from the atom's own pairs (sorted)
+    double* gq_tr;       // [2n] same from the pairs of other atoms (sorted)
+    double* part_lj;     // [grid_rbl * 4 * nt2] LJ pair-parameter partials
+    double* part_v;      // [grid_q * 3] partial sums of the upstream gradient
+    double2* tau_part;   // [grid_rho * P]
+    double2* tau;        // [P]
     // profiling
     void* prof;          // std::vector of event records (C++ side)
     double prof_ms[RBE_NKERNELS];
@@ -123,6 +137,7 @@ struct rbe_ctx {
     int n_sm, last_n, last_precision;
     RblGeom rbl;
     size_t cap_atoms[20];
+    size_t cap_adj[8];
 };
 
 // ---------------------------------------------------------------------------
@@ -186,7 +201,10 @@ void launch_scan(rbe_ctx* ctx, cudaStream_t st);
 void launch_scatter_sort_gather(rbe_ctx* ctx, int n, const double* pos, const double* q,
                                 const int32_t* type, const int32_t* mol, cudaStream_t st);
 // pair kernel (k_rbl.cu)
-void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st);
+void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st, bool adjoint = false);
+// adjoint (k_kspace.cu)
+void launch_adj_prep(rbe_ctx* ctx, int n, const double* gF, cudaStream_t st);
+void launch_adj_final(rbe_ctx* ctx, int n, double* dEdq, double* dLdq, cudaStream_t st);
 // Fourier part and finalisation (k_kspace.cu)
 void launch_ksample(rbe_ctx* ctx, uint64_t step, cudaStream_t st);
 void launch_rho(rbe_ctx* ctx, int n, cudaStream_t st);

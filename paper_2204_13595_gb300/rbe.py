@@ -24,7 +24,7 @@ KERNELS = ["quantize", "scan", "scatter", "sort", "gather", "ksample", "rho", "r
 EXPORTS = ["rbe_create", "rbe_set_coulomb", "rbe_set_lj", "rbe_set_precision", "rbe_set_water_bonds",
            "rbe_set_capacity", "rbe_forces", "rbe_step", "rbe_sync_status", "rbe_set_debug", "rbe_get_lists",
            "rbe_get_kspace", "rbe_get_info", "rbe_set_profiling", "rbe_get_profile", "rbe_last_error",
-           "rbe_destroy", "rbe_rho_noalloc"]
+           "rbe_destroy", "rbe_rho_noalloc", "rbe_adjoint"]
 ELIMIT = -8
 NOALLOC_BLOCKS, NOALLOC_PMAX = 256, 512
 
@@ -60,6 +60,7 @@ def load(path: str = LIB_PATH):
     L.rbe_destroy.argtypes = [vp]
     L.rbe_destroy.restype = None
     L.rbe_rho_noalloc.argtypes = [i, vp, vp, d, i, vp, vp, vp]
+    L.rbe_adjoint.argtypes = [vp, u64, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     return L
 
 
@@ -111,11 +112,10 @@ class Context:
             raise RbeError(rc, "rbe_create rejected the parameters")
         self.h = h
         self.p, self.P = p, P
+        self.ntypes = 1
         self._check(self.L.rbe_set_coulomb(self.h, k_e))
         if eps is not None:
-            e = (ctypes.c_double * len(eps))(*eps)
-            s = (ctypes.c_double * len(sigma))(*sigma)
-            self._check(self.L.rbe_set_lj(self.h, len(eps), e, s, int(shift_lj)))
+            self.set_lj(eps, sigma, shift_lj)
         self.set_precision(precision)
 
     @classmethod
@@ -158,6 +158,25 @@ class Context:
         return self._check(self.L.rbe_step(self.h, step0, nsteps, dt, accel, n, _ptr(pos), _ptr(vel), _ptr(mass),
                                            _ptr(q), _ptr(typ), _ptr(mol), _ptr(F), _ptr(trace), _stream(stream)))
 
+    def adjoint(self, step, pos, q, typ, mol, gF=None, stream=None):
+        """rbe_adjoint: gradients at frozen draws.  Returns dEdq, dLdq (device
+        tensors, caller order) and the per-type dEdeps, dEdsig, dLdeps, dLdsig."""
+        import torch
+        n = int(pos.shape[0])
+        dEdq = torch.empty(n, dtype=torch.float64, device=pos.device)
+        dLdq = torch.empty(n, dtype=torch.float64, device=pos.device)
+        T = self.ntypes
+        outs = [np.zeros(T) for _ in range(4)]
+        self._check(self.L.rbe_adjoint(self.h, step, n, _ptr(pos), _ptr(q), _ptr(typ), _ptr(mol), _ptr(gF),
+                                       _ptr(dEdq), _ptr(dLdq), *[_ptr(o) for o in outs], _stream(stream)))
+        return dict(dEdq=dEdq, dLdq=dLdq, dEdeps=outs[0], dEdsig=outs[1], dLdeps=outs[2], dLdsig=outs[3])
+
+    def set_lj(self, eps, sigma, shift_lj=False):
+        e = (ctypes.c_double * len(eps))(*[float(x) for x in eps])
+        s = (ctypes.c_double * len(sigma))(*[float(x) for x in sigma])
+        self._check(self.L.rbe_set_lj(self.h, len(eps), e, s, int(shift_lj)))
+        self.ntypes = len(eps)
+
     def sync_status(self, stream=None):
         return self.L.rbe_sync_status(self.h, _stream(stream))
 
@@ -198,3 +217,54 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+class RbeForces:
+    """Differentiable IRBE force step (torch.autograd.Function wrapper).
+
+    ``RbeForces.apply(ctx, step, pos, q, typ, mol, eps, sigma)`` returns
+    (F [n,3], E scalar: the sum of the non-bonded energy components) for the
+    charges ``q`` (device tensor) and per-type LJ parameters ``eps``,
+    ``sigma`` (CPU tensors).  Gradients flow to q, eps and sigma through
+    rbe_adjoint with the draws of ``step`` frozen; positions are inputs only.
+    """
+
+    @staticmethod
+    def apply(ctx, step, pos, q, typ, mol, eps, sigma):
+        return _rbe_function().apply(ctx, step, pos, q, typ, mol, eps, sigma)
+
+
+_FN = None
+
+
+def _rbe_function():
+    global _FN
+    if _FN is not None:
+        return _FN
+    import torch
+
+    class _F(torch.autograd.Function):
+        @staticmethod
+        def forward(actx, ctx, step, pos, q, typ, mol, eps, sigma):
+            ctx.set_lj(eps.detach().cpu().tolist(), sigma.detach().cpu().tolist())
+            F = torch.empty_like(pos)
+            E = torch.zeros(NE, dtype=torch.float64, device=pos.device)
+            qd = q.detach().contiguous()
+            ctx.forces(step, pos, qd, typ, mol, F, E)
+            actx.rbe = (ctx, step, pos, qd, typ, mol)
+            actx.lj_dev = eps.device
+            return F, E[:E_BOND].sum()
+
+        @staticmethod
+        def backward(actx, gF, gE):
+            ctx, step, pos, q, typ, mol = actx.rbe
+            gFc = None if gF is None else gF.contiguous()
+            g = ctx.adjoint(step, pos, q, typ, mol, gFc)
+            ge = 0.0 if gE is None else float(gE)
+            dq = g["dLdq"] + ge * g["dEdq"]
+            de = torch.tensor(g["dLdeps"] + ge * g["dEdeps"], dtype=torch.float64, device=actx.lj_dev)
+            ds = torch.tensor(g["dLdsig"] + ge * g["dEdsig"], dtype=torch.float64, device=actx.lj_dev)
+            return None, None, None, dq, None, None, de, ds
+
+    _FN = _F
+    return _FN

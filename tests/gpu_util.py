@@ -75,3 +75,22 @@ def rms_rel(a, ref):
 
 __all__ = ["params", "to_dev", "gpu_forces", "rel_err_components", "rms_rel", "cond_err", "ek_scale", "systems",
            "oracle", "rbe"]
+
+
+def type_grads(g_eps, g_sig, eps, sigma):
+    """Lorentz-Berthelot chain rule from the oracle's ordered pair-table
+    gradients to per-type eps and sigma gradients."""
+    T = len(eps)
+    ge, gs = np.zeros(T), np.zeros(T)
+    for a in range(T):
+        for b in range(T):
+            if a == b:
+                ge[a] += g_eps[a, a]
+                gs[a] += g_sig[a, a]
+                continue
+            sym_e = g_eps[a, b] + g_eps[b, a]
+            sym_s = g_sig[a, b] + g_sig[b, a]
+            if sym_e != 0.0:
+                ge[a] += sym_e * (0.0 if eps[b] == 0.0 else (np.inf if eps[a] == 0.0 else eps[b] / (2 * np.sqrt(eps[a] * eps[b]))))
+            gs[a] += 0.5 * sym_s
+    return ge, gs
