@@ -85,3 +85,30 @@ def test_adjoint_electrolyte_all_charges(orc):
         fdE[m], fdL[m] = (Ep - Em) / (2 * h), (Lp - Lm) / (2 * h)
     assert np.allclose(g["dEdq"], fdE, rtol=1e-6, atol=1e-6 * np.abs(fdE).max())
     assert np.allclose(g["dLdq"], fdL, rtol=1e-5, atol=1e-5 * np.abs(fdL).max())
+
+
+@pytest.mark.parametrize("shift", [0, 1])
+def test_adjoint_euler_homogeneity(orc, shift):
+    """At frozen draws the Coulomb energy and forces are homogeneous of degree 2
+    in the charges and the LJ energy and forces of degree 1 in the pair
+    well depths eps_ab (the shift of Eq. (2.10) scales with eps_ab too), so by
+    Euler's theorem q.dE/dq = 2 E_coul and sum_ab eps_ab dE/deps_ab = E_LJ, and
+    the same for L = sum_i gF_i . F_i (the momentum correction is linear in F)."""
+    s = systems.water(334, seed=9)
+    rng = np.random.default_rng(5)
+    v = rng.normal(size=s.pos.shape)
+    pr = _pr(orc, s, shift=shift)
+    g = orc.rbe_adjoint(s.pos, s.q, s.type, s.mol, pr, 2, v)
+    out = orc.rbe_forces(s.pos, s.q, s.type, s.mol, pr, 2)
+    E = out["E"]
+    e_coul = E[0] + E[1] + E[2] + E[4]
+    T = len(s.eps)
+    eps_ab = np.sqrt(np.outer(s.eps, s.eps))
+    lj_E = float((eps_ab * g["dEde"][:T, :T]).sum())
+    lj_L = float((eps_ab * g["dLde"][:T, :T]).sum())
+    L = float((v * out["F"]).sum())
+    assert float(s.q @ g["dEdq"]) == pytest.approx(2 * e_coul, rel=1e-11)
+    assert lj_E == pytest.approx(E[3], rel=1e-11)
+    # L has no separate Coulomb/LJ split in the output; the two Euler sums add up to L.
+    scale = float(np.abs(s.q * g["dLdq"]).sum()) + float(np.abs(eps_ab * g["dLde"][:T, :T]).sum())
+    assert abs(0.5 * float(s.q @ g["dLdq"]) + lj_L - L) <= 1e-11 * scale
