@@ -13,6 +13,13 @@ FP64 path is timed beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The same line carries a "batch" object: 64 independent replicas of uneven
+size (1,000 to 50,000 atoms, log-uniform, electrolyte and water, each its own
+box, alpha and P) stepped together for 500 velocity-Verlet steps by the
+batched path (one launch per stage, a persistent pair kernel over all
+replicas, one CUDA graph per step, tiling autotuned), against looping the
+single-system rbe_step over the replicas; aggregate atom-steps/s of both.
+
 --impl reference times the plain CPU oracle (the same estimator in FP64 C)
 on the host cores, one full force evaluation of the same system per step.
 Under torchrun every rank runs an independent replica (the path does not
@@ -154,6 +161,85 @@ def run_reference(args):
     return 0
 
 
+BATCH_STEPS = 500
+
+
+def _batch_leg(flush):
+    """64-replica batched stepping against the looped single-system path."""
+    import torch
+
+    from paper_2204_13595_gb300 import rbe, systems
+
+    t0 = time.perf_counter()
+    suite = systems.batch_replicas()
+    gen_s = time.perf_counter() - t0
+    dev = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device="cuda")
+
+    def state():
+        return [dict(pos=dev(x.pos), vel=dev(x.vel), mass=dev(x.mass), q=dev(x.q), typ=dev(x.type, torch.int32),
+                     mol=None if x.mol is None else dev(x.mol, torch.int32),
+                     F=torch.zeros((x.n, 3), dtype=torch.float64, device="cuda")) for x in suite]
+
+    ctxs = [rbe.Context.for_system(x, precision=rbe.MIXED) for x in suite]
+    A, B = state(), state()
+    bt = rbe.Batch(ctxs)
+    bt.bind([d["pos"] for d in A], [d["q"] for d in A], [d["typ"] for d in A], [d["mol"] for d in A],
+            [d["F"] for d in A], vel=[d["vel"] for d in A], mass=[d["mass"] for d in A],
+            dt=[x.dt for x in suite], accel=[x.accel for x in suite])
+    t0 = time.perf_counter()
+    tune = bt.autotune(step=0)
+    tune_s = time.perf_counter() - t0
+    natoms = sum(x.n for x in suite)
+    stream = torch.cuda.current_stream()
+
+    # batched: warm-up, then BATCH_STEPS graph replays, each timed with events
+    # on the stream, L2 flushed between replays (outside the events)
+    bt.forces(0)
+    bt.step(0, 3)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(BATCH_STEPS)]
+    for k in range(BATCH_STEPS):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        bt.step(3 + k, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    batched_ms = sum(a.elapsed_time(b) for a, b in ev) / BATCH_STEPS
+    if bt.sync_status()[0] != 0:
+        raise RuntimeError("device status error in the batched run")
+
+    # looped single-system path on an identical copy: per replica rbe_step
+    # over the same steps (the loop inside the library), one timed region
+    for x, c, d in zip(suite, ctxs, B):
+        c.forces(0, d["pos"], d["q"], d["typ"], d["mol"], d["F"])
+        c.step(0, 3, x.dt, x.accel, d["pos"], d["vel"], d["mass"], d["q"], d["typ"], d["mol"], d["F"])
+    torch.cuda.synchronize()
+    flush.fill_(0.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for x, c, d in zip(suite, ctxs, B):
+        c.step(3, BATCH_STEPS, x.dt, x.accel, d["pos"], d["vel"], d["mass"], d["q"], d["typ"], d["mol"], d["F"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    looped_ms = e0.elapsed_time(e1) / BATCH_STEPS
+    same = all(torch.equal(a["pos"], b["pos"]) and torch.equal(a["F"], b["F"]) for a, b in zip(A, B))
+    info = bt.info()
+    bt.close()
+    return {
+        "workload": "64 replicas, 1,000-50,000 atoms log-uniform (electrolyte P=100 / water P=200), mixed, "
+                    f"{BATCH_STEPS} velocity-Verlet steps",
+        "replicas": len(suite), "atoms": natoms, "steps": BATCH_STEPS,
+        "atom_steps_per_s": natoms * 1e3 / batched_ms, "ms_per_step": batched_ms,
+        "looped_atom_steps_per_s": natoms * 1e3 / looped_ms, "looped_ms_per_step": looped_ms,
+        "speedup_vs_looped": looped_ms / batched_ms,
+        "bitwise_equal_to_looped": bool(same),
+        "launches_per_step": int(info["launches_per_step"]), "pair_tasks": int(info["tasks"]),
+        "autotune": tune, "autotune_s": tune_s, "generate_s": gen_s,
+        "timing": "batched: CUDA events per graph replay, L2 flushed between replays; looped: one event pair "
+                  "around all replicas' rbe_step calls",
+    }
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -229,6 +315,7 @@ def run_ours(args):
     clocks_proc = _clock_sampler() if rank == 0 else None
     ms_mixed, prof, launches = timed(mixed, args.steps, args.warmup, profile=True)
     ms_f64, _, _ = timed(f64, max(3, min(args.steps, 10)), max(3, min(args.warmup, 3)))
+    batch = _batch_leg(flush) if ws == 1 else None
     clocks = _clock_summary(clocks_proc, local) if rank == 0 else None
 
     # end to end through the same C ABI with pinned host buffers
@@ -289,6 +376,7 @@ def run_ours(args):
                          "sample": "one full FP64 oracle force evaluation of the same 1.2M-atom system"},
         "e2e": {"value": ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks, "gpu_launches": launches * args.steps,
+        "batch": batch,
     }
     print(json.dumps(line))
     if ws > 1:

@@ -236,6 +236,78 @@ int rbe_rho_noalloc(int n, const double* pos, const double* q, double box_L, int
  * idle). */
 void rbe_destroy(rbe_ctx* ctx);
 
+/* Work decomposition of the RBL pair kernel (Sec. 2.3 stencil walk): a work
+ * unit is a run of cells along x holding about atoms_per_unit atoms (0: 48);
+ * the kernel's grid has ceil(units / units_per_slot) slots (0: a persistent
+ * grid of resident blocks x SMs slots).  Results do not depend on the unit
+ * width except through the order of the block partials of energies, virial
+ * and net force (rounding only).  rbe_batch_autotune sets these. */
+int rbe_set_rbl_tiling(rbe_ctx* ctx, int atoms_per_unit, int units_per_slot);
+
+/* ---------------------------------------------------------------------------
+ * Batched execution: many independent systems ("replicas", each its own
+ * context: box, alpha, cutoffs, p, P, seed, LJ table, bonds) stepped together.
+ * Every stage of the force step is one launch over all replicas, and the RBL
+ * pair kernel is one persistent launch whose blocks take (replica, slot)
+ * tasks from a work queue ordered by decreasing cost; one MD step is captured
+ * once as a CUDA graph and replayed.  Each replica's forces, energies and
+ * trajectory are bit for bit those of rbe_forces / rbe_step on its context
+ * (same grids, same reduction order).
+ * ------------------------------------------------------------------------- */
+typedef struct rbe_batch rbe_batch;
+
+/* A batch over nrep >= 1 distinct contexts (not owned: destroy them after
+ * the batch).  All contexts must share one precision mode and have
+ * debug recording off when the batch is bound. */
+int rbe_batch_create(rbe_batch** out, int nrep, rbe_ctx* const* ctxs);
+
+/* Binds replica r to n[r] atoms and its caller-owned device arrays:
+ * pos[r], q[r], F[r] required; type[r], mol[r] optional (NULL); vel[r] and
+ * mass[r] required by rbe_batch_step only (NULL otherwise); dt[r] and
+ * accel[r] are the velocity-Verlet time step and force-to-acceleration
+ * factor of replica r (may be NULL when only forces are wanted).  All
+ * pointer arrays are host arrays of nrep entries.  Sets up every context for
+ * its n (as rbe_forces would) and uploads the batch plan; re-bind after
+ * changing a context's parameters. */
+int rbe_batch_bind(rbe_batch* b, const int* n, double* const* pos, const double* const* q,
+                   const int32_t* const* type, const int32_t* const* mol, double* const* F, double* const* vel,
+                   const double* const* mass, const double* dt, const double* accel);
+
+/* Forces (and each context's energies/virial/status) of every replica at MD
+ * step `step`; energy may be NULL or a host array [nrep][RBE_NE] (the call
+ * then waits for the stream). */
+int rbe_batch_forces(rbe_batch* b, uint64_t step, double* energy, void* cuda_stream);
+
+/* nsteps of velocity Verlet for every replica (the step of rbe_step; on
+ * entry F must hold the forces at (pos, step0)), as nsteps replays of one
+ * captured CUDA graph.  energy_trace: NULL or a device array
+ * [nrep][nsteps][2] of (potential, kinetic / accel) per step. */
+int rbe_batch_step(rbe_batch* b, uint64_t step0, int nsteps, double* energy_trace, void* cuda_stream);
+
+/* Project-written autotuner of the pair kernel's tiling: for each family of
+ * replicas (same cutoffs, p and precision) it times the batched pair kernel
+ * over candidate atoms_per_unit and units_per_slot values, keeps the
+ * fastest, sets them on the contexts (rbe_set_rbl_tiling) and re-binds.
+ * Runs force steps at step `step` (the bound positions are not moved).
+ * out (may be NULL, nout entries): per family the chosen atoms_per_unit,
+ * units_per_slot and the kernel time in ms, then the untuned time. */
+int rbe_batch_autotune(rbe_batch* b, uint64_t step, double* out, int nout, void* cuda_stream);
+
+/* Plan facts: out[0] replicas, [1] total atoms, [2] pair-kernel tasks,
+ * [3] pair-kernel blocks, [4] its dynamic shared memory (bytes), [5] kernel
+ * launches per MD step, [6] families. */
+int rbe_batch_info(rbe_batch* b, double* out, int nout);
+
+/* Waits for cuda_stream; status[r] (may be NULL) receives each replica's
+ * latched status (as rbe_sync_status, which clears it); returns the first
+ * non-OK status or RBE_OK. */
+int rbe_batch_sync_status(rbe_batch* b, int* status, void* cuda_stream);
+
+const char* rbe_batch_last_error(const rbe_batch* b);
+
+/* Releases the batch (after the caller's streams are idle). */
+void rbe_batch_destroy(rbe_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,15 +11,19 @@ namespace {
 
 constexpr int TPB = 256;
 
+// Every kernel body below takes its block index and the block count of its
+// replica's grid explicitly (bx, nbx), so that the single-system kernel and
+// the batched one (one launch over many replicas) run the same code.
+
 // Wrap, quantise, bin; latch non-finite input; per-block sums of q^2, q, |q|.
-__global__ void __launch_bounds__(TPB) k_quantize_count(int n, const double* __restrict__ pos,
-                                                        const double* __restrict__ q, RbeConsts c,
-                                                        int* __restrict__ cell_count, int* __restrict__ cell_of,
-                                                        int* __restrict__ slot, double* __restrict__ part_q,
-                                                        int* __restrict__ status)
+__device__ __forceinline__ void quantize_count_body(int bx, int nbx, int n, const double* __restrict__ pos,
+                                                    const double* __restrict__ q, const RbeConsts& c,
+                                                    int* __restrict__ cell_count, int* __restrict__ cell_of,
+                                                    int* __restrict__ slot, double* __restrict__ part_q,
+                                                    int* __restrict__ status)
 {
     double sq2 = 0.0, sq = 0.0, sabs = 0.0;
-    for (int i = blockIdx.x * TPB + threadIdx.x; i < n; i += gridDim.x * TPB) {
+    for (int i = bx * TPB + threadIdx.x; i < n; i += nbx * TPB) {
         double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
         double qi = q[i];
         if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) {
@@ -47,12 +51,21 @@ __global__ void __launch_bounds__(TPB) k_quantize_count(int n, const double* __r
     if (threadIdx.x < 3) {
         double a = 0.0;
         for (int k = 0; k < TPB / 32; ++k) a += red[threadIdx.x][k];
-        part_q[blockIdx.x * RBE_NPART_Q + threadIdx.x] = a;
+        part_q[bx * RBE_NPART_Q + threadIdx.x] = a;
     }
 }
 
+__global__ void __launch_bounds__(TPB) k_quantize_count(int n, const double* __restrict__ pos,
+                                                        const double* __restrict__ q, RbeConsts c,
+                                                        int* __restrict__ cell_count, int* __restrict__ cell_of,
+                                                        int* __restrict__ slot, double* __restrict__ part_q,
+                                                        int* __restrict__ status)
+{
+    quantize_count_body(blockIdx.x, gridDim.x, n, pos, q, c, cell_count, cell_of, slot, part_q, status);
+}
+
 // Exclusive scan of cell_count[0..m) into start[0..m] (single block).
-__global__ void __launch_bounds__(1024) k_scan(long m, const int* __restrict__ count, int* __restrict__ start)
+__device__ __forceinline__ void scan_body(long m, const int* __restrict__ count, int* __restrict__ start)
 {
     __shared__ int wsum[32];
     __shared__ int carry;
@@ -97,17 +110,29 @@ __global__ void __launch_bounds__(1024) k_scan(long m, const int* __restrict__ c
     if (threadIdx.x == 0) start[m] = carry;
 }
 
-__global__ void __launch_bounds__(TPB) k_scatter(int n, const int* __restrict__ cell_of, const int* __restrict__ slot,
-                                                 const int* __restrict__ start, int* __restrict__ perm)
+__global__ void __launch_bounds__(1024) k_scan(long m, const int* __restrict__ count, int* __restrict__ start)
 {
-    int i = blockIdx.x * TPB + threadIdx.x;
+    scan_body(m, count, start);
+}
+
+__device__ __forceinline__ void scatter_body(int bx, int n, const int* __restrict__ cell_of,
+                                             const int* __restrict__ slot, const int* __restrict__ start,
+                                             int* __restrict__ perm)
+{
+    int i = bx * TPB + threadIdx.x;
     if (i < n) perm[start[cell_of[i]] + slot[i]] = i;
 }
 
-// Canonical in-cell order: ascending caller index (insertion sort, cells are small).
-__global__ void __launch_bounds__(TPB) k_sort_cells(long m, const int* __restrict__ start, int* __restrict__ perm)
+__global__ void __launch_bounds__(TPB) k_scatter(int n, const int* __restrict__ cell_of, const int* __restrict__ slot,
+                                                 const int* __restrict__ start, int* __restrict__ perm)
 {
-    long c = (long)blockIdx.x * TPB + threadIdx.x;
+    scatter_body(blockIdx.x, n, cell_of, slot, start, perm);
+}
+
+// Canonical in-cell order: ascending caller index (insertion sort, cells are small).
+__device__ __forceinline__ void sort_cells_body(int bx, long m, const int* __restrict__ start, int* __restrict__ perm)
+{
+    long c = (long)bx * TPB + threadIdx.x;
     if (c >= m) return;
     int b = start[c], e = start[c + 1];
     for (int k = b + 1; k < e; ++k) {
@@ -118,13 +143,19 @@ __global__ void __launch_bounds__(TPB) k_sort_cells(long m, const int* __restric
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_gather(int n, const int* __restrict__ perm, const double* __restrict__ pos,
-                                                const double* __restrict__ q, const int32_t* __restrict__ type,
-                                                const int32_t* __restrict__ mol, RbeConsts c, uint4* __restrict__ s4,
-                                                float4* __restrict__ f4, double4_32a* __restrict__ p4, int2* __restrict__ tm,
-                                                int* __restrict__ status)
+__global__ void __launch_bounds__(TPB) k_sort_cells(long m, const int* __restrict__ start, int* __restrict__ perm)
 {
-    int k = blockIdx.x * TPB + threadIdx.x;
+    sort_cells_body(blockIdx.x, m, start, perm);
+}
+
+__device__ __forceinline__ void gather_body(int bx, int n, const int* __restrict__ perm, const double* __restrict__ pos,
+                                            const double* __restrict__ q, const int32_t* __restrict__ type,
+                                            const int32_t* __restrict__ mol, const RbeConsts& c,
+                                            uint4* __restrict__ s4, float4* __restrict__ f4,
+                                            double4_32a* __restrict__ p4, int2* __restrict__ tm,
+                                            int* __restrict__ status)
+{
+    int k = bx * TPB + threadIdx.x;
     if (k >= n) return;
     int i = perm[k];
     double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
@@ -145,6 +176,64 @@ __global__ void __launch_bounds__(TPB) k_gather(int n, const int* __restrict__ p
         t = 0;
     }
     tm[k] = make_int2(t, mol ? mol[i] : -(i + 1));
+}
+
+__global__ void __launch_bounds__(TPB) k_gather(int n, const int* __restrict__ perm, const double* __restrict__ pos,
+                                                const double* __restrict__ q, const int32_t* __restrict__ type,
+                                                const int32_t* __restrict__ mol, RbeConsts c, uint4* __restrict__ s4,
+                                                float4* __restrict__ f4, double4_32a* __restrict__ p4, int2* __restrict__ tm,
+                                                int* __restrict__ status)
+{
+    gather_body(blockIdx.x, n, perm, pos, q, type, mol, c, s4, f4, p4, tm, status);
+}
+
+// ---- batched forms: one launch over all replicas of a plan -----------------
+// Block grids per replica: BK_CELLS = ceil((ncells + 1) / TPB), BK_ATOMS =
+// ceil(n / TPB), BK_Q = grid_q, BK_REP = 1.
+
+__global__ void __launch_bounds__(TPB) k_zero_counts_b(const RepDev* __restrict__ R, const int* __restrict__ off,
+                                                       int nrep)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    long c = (long)bx * TPB + threadIdx.x;
+    if (c <= d.ncells) d.cell_count[c] = 0;
+}
+
+__global__ void __launch_bounds__(TPB) k_quantize_count_b(const RepDev* __restrict__ R, const int* __restrict__ off,
+                                                          int nrep)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    quantize_count_body(bx, nbx, d.n, d.pos, d.q, d.c, d.cell_count, d.cell_of, d.slot, d.part_q, d.status);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_b(const RepDev* __restrict__ R)
+{
+    const RepDev& d = R[blockIdx.x];
+    scan_body(d.ncells, d.cell_count, d.cell_start);
+}
+
+__global__ void __launch_bounds__(TPB) k_scatter_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    scatter_body(bx, d.n, d.cell_of, d.slot, d.cell_start, d.perm);
+}
+
+__global__ void __launch_bounds__(TPB) k_sort_cells_b(const RepDev* __restrict__ R, const int* __restrict__ off,
+                                                      int nrep)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    sort_cells_body(bx, d.ncells, d.cell_start, d.perm);
+}
+
+__global__ void __launch_bounds__(TPB) k_gather_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    gather_body(bx, d.n, d.perm, d.pos, d.q, d.type, d.mol, d.c, d.s4, d.f4, d.p4, d.tm, d.status);
 }
 
 }  // namespace
@@ -179,4 +268,15 @@ void launch_scatter_sort_gather(rbe_ctx* ctx, int n, const double* pos, const do
     k_gather<<<g, TPB, 0, st>>>(n, ctx->perm, pos, q, type, mol, ctx->c, ctx->s4, ctx->f4, ctx->p4, ctx->tm,
                                  ctx->status);
     prof_end(ctx, RBE_K_GATHER, st);
+}
+
+void launch_cells_batch(const BatchPlan& bp, cudaStream_t st)
+{
+    const int nr = bp.nrep;
+    k_zero_counts_b<<<bp.total[BK_CELLS], TPB, 0, st>>>(bp.rep, bp.off[BK_CELLS], nr);
+    k_quantize_count_b<<<bp.total[BK_Q], TPB, 0, st>>>(bp.rep, bp.off[BK_Q], nr);
+    k_scan_b<<<nr, 1024, 0, st>>>(bp.rep);
+    k_scatter_b<<<bp.total[BK_ATOMS], TPB, 0, st>>>(bp.rep, bp.off[BK_ATOMS], nr);
+    k_sort_cells_b<<<bp.total[BK_CELLS], TPB, 0, st>>>(bp.rep, bp.off[BK_CELLS], nr);
+    k_gather_b<<<bp.total[BK_ATOMS], TPB, 0, st>>>(bp.rep, bp.off[BK_ATOMS], nr);
 }

@@ -39,12 +39,15 @@ __device__ __forceinline__ int inv_cdf(uint64_t u, const uint64_t* __restrict__ 
     return lo - M;
 }
 
-__global__ void __launch_bounds__(TPB) k_sample(RbeConsts c, uint64_t step, const uint64_t* __restrict__ T,
-                                                int4* __restrict__ km, double4_32a* __restrict__ kv,
-                                                int* __restrict__ status)
+// Kernel bodies take their block index and their replica's block count
+// explicitly (bx, nbx) so that the single-system kernels and the batched ones
+// (one launch over many replicas, at the end of this file) share them.
+__device__ __forceinline__ void sample_body(int bx, int nbx, const RbeConsts& c, uint64_t step,
+                                            const uint64_t* __restrict__ T, int4* __restrict__ km,
+                                            double4_32a* __restrict__ kv, int* __restrict__ status)
 {
     const double twopi_L = 2.0 * 3.14159265358979323846 / c.L;
-    for (int l = blockIdx.x * TPB + threadIdx.x; l < c.P; l += gridDim.x * TPB) {
+    for (int l = bx * TPB + threadIdx.x; l < c.P; l += nbx * TPB) {
         int mx = 1, my = 0, mz = 0;
         bool ok = false;
         for (uint64_t t = 0; t < 1024 && !ok; ++t) {
@@ -61,14 +64,22 @@ __global__ void __launch_bounds__(TPB) k_sample(RbeConsts c, uint64_t step, cons
     }
 }
 
+__global__ void __launch_bounds__(TPB) k_sample(RbeConsts c, uint64_t step, const uint64_t* __restrict__ T,
+                                                int4* __restrict__ km, double4_32a* __restrict__ kv,
+                                                int* __restrict__ status)
+{
+    sample_body(blockIdx.x, gridDim.x, c, step, T, km, kv, status);
+}
+
 // rho partial sums: block b owns atoms [b*chunk, min(n,(b+1)*chunk)).
 template <bool MIXED>
-__global__ void k_rho(int n, int chunk, RbeConsts c, const uint4* __restrict__ s4, const double4_32a* __restrict__ p4,
-                      const int4* __restrict__ km, double2* __restrict__ part)
+__device__ __forceinline__ void rho_body(int bx, int n, int chunk, const RbeConsts& c, const uint4* __restrict__ s4,
+                                         const double4_32a* __restrict__ p4, const int4* __restrict__ km,
+                                         double2* __restrict__ part)
 {
     __shared__ double4_32a tile_d[MIXED ? 1 : TILE];
     __shared__ uint4 tile_u[MIXED ? TILE : 1];
-    const int b0 = blockIdx.x * chunk;
+    const int b0 = bx * chunk;
     const int b1 = min(n, b0 + chunk);
     for (int l0 = 0; l0 < c.P; l0 += blockDim.x) {
         const int l = l0 + threadIdx.x;
@@ -113,17 +124,24 @@ __global__ void k_rho(int n, int chunk, RbeConsts c, const uint4* __restrict__ s
                 }
             }
         }
-        if (act) part[(size_t)blockIdx.x * c.P + l] = make_double2(re, im);
+        if (act) part[(size_t)bx * c.P + l] = make_double2(re, im);
     }
+}
+
+template <bool MIXED>
+__global__ void k_rho(int n, int chunk, RbeConsts c, const uint4* __restrict__ s4, const double4_32a* __restrict__ p4,
+                      const int4* __restrict__ km, double2* __restrict__ part)
+{
+    rho_body<MIXED>(blockIdx.x, n, chunk, c, s4, p4, km, part);
 }
 
 // Fixed-order sum over blocks; per-k energy and virial terms of the
 // reweighted reciprocal sum (E_k = sum_l c_l/2 |rho_l|^2).
-__global__ void __launch_bounds__(TPB) k_rho_sum(int nblk, RbeConsts c, const double2* __restrict__ part,
-                                                 const double4_32a* __restrict__ kv, double2* __restrict__ rho,
-                                                 double* __restrict__ kterms)
+__device__ __forceinline__ void rho_sum_body(int bx, int nblk, const RbeConsts& c, const double2* __restrict__ part,
+                                             const double4_32a* __restrict__ kv, double2* __restrict__ rho,
+                                             double* __restrict__ kterms)
 {
-    int l = blockIdx.x * TPB + threadIdx.x;
+    int l = bx * TPB + threadIdx.x;
     if (l >= c.P) return;
     double re = 0.0, im = 0.0;
     for (int b = 0; b < nblk; ++b) {
@@ -146,13 +164,20 @@ __global__ void __launch_bounds__(TPB) k_rho_sum(int nblk, RbeConsts c, const do
     o[6] = e * (-bb * k.y * k.z);
 }
 
+__global__ void __launch_bounds__(TPB) k_rho_sum(int nblk, RbeConsts c, const double2* __restrict__ part,
+                                                 const double4_32a* __restrict__ kv, double2* __restrict__ rho,
+                                                 double* __restrict__ kterms)
+{
+    rho_sum_body(blockIdx.x, nblk, c, part, kv, rho, kterms);
+}
+
 // Harmonic water: molecule m = atoms (3m, 3m+1, 3m+2) = (O, H, H).
-__global__ void __launch_bounds__(TPB) k_bonded(int nmol, const double* __restrict__ pos, RbeConsts c, double kb,
-                                                double r0, double kth, double th0, double* __restrict__ Fb,
-                                                double* __restrict__ part)
+__device__ __forceinline__ void bonded_body(int bx, int nbx, int nmol, const double* __restrict__ pos,
+                                            const RbeConsts& c, double kb, double r0, double kth, double th0,
+                                            double* __restrict__ Fb, double* __restrict__ part)
 {
     double u = 0.0;
-    for (int mI = blockIdx.x * TPB + threadIdx.x; mI < nmol; mI += gridDim.x * TPB) {
+    for (int mI = bx * TPB + threadIdx.x; mI < nmol; mI += nbx * TPB) {
         int o = 3 * mI;
         double d1[3], d2[3];
         for (int a = 0; a < 3; ++a) {
@@ -192,8 +217,15 @@ __global__ void __launch_bounds__(TPB) k_bonded(int nmol, const double* __restri
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < TPB / 32; ++w) s += red[w];
-        part[blockIdx.x] = s;
+        part[bx] = s;
     }
+}
+
+__global__ void __launch_bounds__(TPB) k_bonded(int nmol, const double* __restrict__ pos, RbeConsts c, double kb,
+                                                double r0, double kth, double th0, double* __restrict__ Fb,
+                                                double* __restrict__ part)
+{
+    bonded_body(blockIdx.x, gridDim.x, nmol, pos, c, kb, r0, kth, th0, Fb, part);
 }
 
 // Fixed-order block reduction of a strided column.
@@ -213,11 +245,10 @@ __device__ double block_sum_col(const double* __restrict__ src, int nrow, int st
 }
 
 // totals: E[0..5], W[6..11], corr[12..14]
-__global__ void __launch_bounds__(TPB) k_finalize(int n, RbeConsts c, const double* __restrict__ part_rbl, int grid_rbl,
-                                                  const double* __restrict__ part_q, int grid_q,
-                                                  const double* __restrict__ kterms,
-                                                  const double* __restrict__ part_bond, int grid_bond,
-                                                  double* __restrict__ totals, int* __restrict__ status)
+__device__ __forceinline__ void finalize_body(int n, const RbeConsts& c, const double* __restrict__ part_rbl,
+                                              int grid_rbl, const double* __restrict__ part_q, int grid_q,
+                                              const double* __restrict__ kterms, const double* __restrict__ part_bond,
+                                              int grid_bond, double* __restrict__ totals, int* __restrict__ status)
 {
     __shared__ double sh[TPB];
     double r[RBE_NPART_RBL];
@@ -243,13 +274,22 @@ __global__ void __launch_bounds__(TPB) k_finalize(int n, RbeConsts c, const doub
     }
 }
 
+__global__ void __launch_bounds__(TPB) k_finalize(int n, RbeConsts c, const double* __restrict__ part_rbl, int grid_rbl,
+                                                  const double* __restrict__ part_q, int grid_q,
+                                                  const double* __restrict__ kterms,
+                                                  const double* __restrict__ part_bond, int grid_bond,
+                                                  double* __restrict__ totals, int* __restrict__ status)
+{
+    finalize_body(n, c, part_rbl, grid_rbl, part_q, grid_q, kterms, part_bond, grid_bond, totals, status);
+}
+
 template <bool MIXED>
-__global__ void __launch_bounds__(TPB) k_kforce(int n, RbeConsts c, const uint4* __restrict__ s4,
-                                                const double4_32a* __restrict__ p4, const int* __restrict__ perm,
-                                                const int4* __restrict__ km, const double4_32a* __restrict__ kv,
-                                                const double2* __restrict__ rho, const double* __restrict__ F_real,
-                                                const double* __restrict__ totals, const double* __restrict__ F_bond,
-                                                int n_bonded_atoms, double* __restrict__ F)
+__device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, const uint4* __restrict__ s4,
+                                            const double4_32a* __restrict__ p4, const int* __restrict__ perm,
+                                            const int4* __restrict__ km, const double4_32a* __restrict__ kv,
+                                            const double2* __restrict__ rho, const double* __restrict__ F_real,
+                                            const double* __restrict__ totals, const double* __restrict__ F_bond,
+                                            int n_bonded_atoms, double* __restrict__ F)
 {
     constexpr int KT = 256;
     __shared__ double4_32a sk_d[MIXED ? 1 : KT];      // kx, ky, kz, unused
@@ -257,7 +297,7 @@ __global__ void __launch_bounds__(TPB) k_kforce(int n, RbeConsts c, const uint4*
     __shared__ int4 sm[KT];
     __shared__ float4 sk_f[MIXED ? KT : 1];       // kx, ky, kz, c Im rho
     __shared__ float sb_f[MIXED ? KT : 1];        // c Re rho
-    const int i = blockIdx.x * TPB + threadIdx.x;
+    const int i = bx * TPB + threadIdx.x;
     const bool act = i < n;
     uint4 si = make_uint4(0, 0, 0, 0);
     double4_32a pi = make_double4_32a(0, 0, 0, 0);
@@ -324,11 +364,22 @@ __global__ void __launch_bounds__(TPB) k_kforce(int n, RbeConsts c, const uint4*
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_vv(int n, double* __restrict__ pos, double* __restrict__ vel,
-                                            const double* __restrict__ mass, const double* __restrict__ F, double hdta,
-                                            double dt, int drift)
+template <bool MIXED>
+__global__ void __launch_bounds__(TPB) k_kforce(int n, RbeConsts c, const uint4* __restrict__ s4,
+                                                const double4_32a* __restrict__ p4, const int* __restrict__ perm,
+                                                const int4* __restrict__ km, const double4_32a* __restrict__ kv,
+                                                const double2* __restrict__ rho, const double* __restrict__ F_real,
+                                                const double* __restrict__ totals, const double* __restrict__ F_bond,
+                                                int n_bonded_atoms, double* __restrict__ F)
 {
-    int i = blockIdx.x * TPB + threadIdx.x;
+    kforce_body<MIXED>(blockIdx.x, n, c, s4, p4, perm, km, kv, rho, F_real, totals, F_bond, n_bonded_atoms, F);
+}
+
+__device__ __forceinline__ void vv_body(int bx, int n, double* __restrict__ pos, double* __restrict__ vel,
+                                        const double* __restrict__ mass, const double* __restrict__ F, double hdta,
+                                        double dt, int drift)
+{
+    int i = bx * TPB + threadIdx.x;
     if (i >= n) return;
     double m = mass[i];
     for (int a = 0; a < 3; ++a) {
@@ -338,11 +389,18 @@ __global__ void __launch_bounds__(TPB) k_vv(int n, double* __restrict__ pos, dou
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_ke(int n, const double* __restrict__ vel, const double* __restrict__ mass,
-                                            double* __restrict__ part)
+__global__ void __launch_bounds__(TPB) k_vv(int n, double* __restrict__ pos, double* __restrict__ vel,
+                                            const double* __restrict__ mass, const double* __restrict__ F, double hdta,
+                                            double dt, int drift)
+{
+    vv_body(blockIdx.x, n, pos, vel, mass, F, hdta, dt, drift);
+}
+
+__device__ __forceinline__ void ke_body(int bx, int nbx, int n, const double* __restrict__ vel,
+                                        const double* __restrict__ mass, double* __restrict__ part)
 {
     double s = 0.0;
-    for (int i = blockIdx.x * TPB + threadIdx.x; i < n; i += gridDim.x * TPB)
+    for (int i = bx * TPB + threadIdx.x; i < n; i += nbx * TPB)
         for (int a = 0; a < 3; ++a) s += 0.5 * mass[i] * vel[3 * i + a] * vel[3 * i + a];
     __shared__ double red[TPB / 32];
     s = warp_sum(s);
@@ -351,12 +409,18 @@ __global__ void __launch_bounds__(TPB) k_ke(int n, const double* __restrict__ ve
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < TPB / 32; ++w) t += red[w];
-        part[blockIdx.x] = t;
+        part[bx] = t;
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_trace(const double* __restrict__ part, int nblk, const double* __restrict__ totals,
-                                               double accel, double* __restrict__ out)
+__global__ void __launch_bounds__(TPB) k_ke(int n, const double* __restrict__ vel, const double* __restrict__ mass,
+                                            double* __restrict__ part)
+{
+    ke_body(blockIdx.x, gridDim.x, n, vel, mass, part);
+}
+
+__device__ __forceinline__ void trace_body(const double* __restrict__ part, int nblk, const double* __restrict__ totals,
+                                           double accel, double* __restrict__ out)
 {
     __shared__ double sh[TPB];
     double ke = block_sum_col(part, nblk, 1, 0, sh);
@@ -364,6 +428,101 @@ __global__ void __launch_bounds__(TPB) k_trace(const double* __restrict__ part, 
         out[0] = totals[0] + totals[1] + totals[2] + totals[3] + totals[4] + totals[5];
         out[1] = ke / accel;
     }
+}
+
+__global__ void __launch_bounds__(TPB) k_trace(const double* __restrict__ part, int nblk, const double* __restrict__ totals,
+                                               double accel, double* __restrict__ out)
+{
+    trace_body(part, nblk, totals, accel, out);
+}
+
+// ---- batched forms: one launch over all replicas of a plan -----------------
+// Per-replica grids: BK_KS = ceil(P / TPB) (sampling and the rho sum),
+// BK_RHO = grid_rho, BK_BOND = grid_bond (0 without bonds), BK_ATOMS =
+// ceil(n / TPB), BK_Q = grid_q, BK_REP = 1.
+
+__global__ void k_ctl_b(BatchCtl* ctl, int op, unsigned long long step0, double* trace, int nsteps)
+{
+    if (op == 0) {          // set: the next batched step uses step0
+        ctl->step = step0;
+        ctl->step0 = step0;
+        ctl->trace = trace;
+        ctl->nsteps = nsteps;
+    } else if (op == 1) {   // advance by one MD step
+        ctl->step += 1;
+    }
+    ctl->rbl_next = 0;      // every op empties the pair kernel's work queue
+}
+
+__global__ void __launch_bounds__(TPB) k_sample_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep,
+                                                  const BatchCtl* __restrict__ ctl)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    sample_body(bx, nbx, d.c, ctl->step, d.kT, d.km, d.kv, d.status);
+}
+
+template <bool MIXED>
+__global__ void k_rho_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    rho_body<MIXED>(bx, d.n, d.rho_chunk, d.c, d.s4, d.p4, d.km, d.rho_part);
+}
+
+__global__ void __launch_bounds__(TPB) k_rho_sum_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    rho_sum_body(bx, d.grid_rho, d.c, d.rho_part, d.kv, d.rho, d.totals + 32);
+}
+
+__global__ void __launch_bounds__(TPB) k_bonded_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    bonded_body(bx, nbx, d.nmol, d.pos, d.c, d.kb, d.r0, d.kth, d.th0, d.F_bond, d.part_bond);
+}
+
+__global__ void __launch_bounds__(TPB) k_finalize_b(const RepDev* __restrict__ R)
+{
+    const RepDev& d = R[blockIdx.x];
+    finalize_body(d.n, d.c, d.part_rbl, d.grid_rbl, d.part_q, d.grid_q, d.totals + 32, d.part_bond, d.grid_bond,
+                  d.totals, d.status);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(TPB) k_kforce_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    kforce_body<MIXED>(bx, d.n, d.c, d.s4, d.p4, d.perm, d.km, d.kv, d.rho, d.F_real, d.totals, d.F_bond,
+                       d.n_bonded_atoms, d.F);
+}
+
+__global__ void __launch_bounds__(TPB) k_vv_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep,
+                                              int drift)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    vv_body(bx, d.n, d.pos, d.vel, d.mass, d.F, 0.5 * d.dt * d.accel, d.dt, drift);
+}
+
+__global__ void __launch_bounds__(TPB) k_ke_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    ke_body(bx, nbx, d.n, d.vel, d.mass, d.ke_part);
+}
+
+// Trace entry k = step - step0 - 1 of replica r: [potential, kinetic / accel].
+__global__ void __launch_bounds__(TPB) k_trace_b(const RepDev* __restrict__ R, const BatchCtl* __restrict__ ctl)
+{
+    const RepDev& d = R[blockIdx.x];
+    const long long k = (long long)(ctl->step - ctl->step0) - 1;
+    if (!ctl->trace || k < 0 || k >= ctl->nsteps) return;
+    trace_body(d.ke_part, d.grid_q, d.totals, d.accel,
+               ctl->trace + ((size_t)blockIdx.x * ctl->nsteps + (size_t)k) * 2);
 }
 
 }  // namespace
@@ -441,6 +600,45 @@ void launch_ke_trace(rbe_ctx* ctx, int n, const double* vel, const double* mass,
     prof_begin(ctx, RBE_K_MISC, st);
     k_trace<<<1, TPB, 0, st>>>(ctx->ke_part, ctx->grid_q, ctx->totals, accel, trace_slot);
     prof_end(ctx, RBE_K_MISC, st);
+}
+
+void launch_ctl_batch(const BatchPlan& bp, int op, unsigned long long step0, double* trace, int nsteps,
+                      cudaStream_t st)
+{
+    k_ctl_b<<<1, 1, 0, st>>>(bp.ctl, op, step0, trace, nsteps);
+}
+
+void launch_kspace_pre_batch(const BatchPlan& bp, cudaStream_t st)
+{
+    const int nr = bp.nrep;
+    k_sample_b<<<bp.total[BK_KS], TPB, 0, st>>>(bp.rep, bp.off[BK_KS], nr, bp.ctl);
+    if (bp.precision == RBE_MIXED)
+        k_rho_b<true><<<bp.total[BK_RHO], bp.rho_threads, 0, st>>>(bp.rep, bp.off[BK_RHO], nr);
+    else
+        k_rho_b<false><<<bp.total[BK_RHO], bp.rho_threads, 0, st>>>(bp.rep, bp.off[BK_RHO], nr);
+    k_rho_sum_b<<<bp.total[BK_KS], TPB, 0, st>>>(bp.rep, bp.off[BK_KS], nr);
+    if (bp.total[BK_BOND] > 0) k_bonded_b<<<bp.total[BK_BOND], TPB, 0, st>>>(bp.rep, bp.off[BK_BOND], nr);
+}
+
+void launch_kspace_post_batch(const BatchPlan& bp, cudaStream_t st)
+{
+    const int nr = bp.nrep;
+    k_finalize_b<<<nr, TPB, 0, st>>>(bp.rep);
+    if (bp.precision == RBE_MIXED)
+        k_kforce_b<true><<<bp.total[BK_ATOMS], TPB, 0, st>>>(bp.rep, bp.off[BK_ATOMS], nr);
+    else
+        k_kforce_b<false><<<bp.total[BK_ATOMS], TPB, 0, st>>>(bp.rep, bp.off[BK_ATOMS], nr);
+}
+
+void launch_vv_batch(const BatchPlan& bp, int drift, cudaStream_t st)
+{
+    k_vv_b<<<bp.total[BK_ATOMS], TPB, 0, st>>>(bp.rep, bp.off[BK_ATOMS], bp.nrep, drift);
+}
+
+void launch_ke_trace_batch(const BatchPlan& bp, cudaStream_t st)
+{
+    k_ke_b<<<bp.total[BK_Q], TPB, 0, st>>>(bp.rep, bp.off[BK_Q], bp.nrep);
+    k_trace_b<<<bp.nrep, TPB, 0, st>>>(bp.rep, bp.ctl);
 }
 
 // ---------------------------------------------------------------------------

@@ -30,6 +30,7 @@
 // path -- and per-block partial sums of the real-space energies, the virial
 // and the net force in a fixed order.
 #include <math.h>
+#include <string.h>
 
 #include "rbe_internal.cuh"
 
@@ -53,6 +54,7 @@ struct RblArgs {
     RbeConsts c;
     RblGeom g;
     int core_cap, shell_cap;
+    int nslots;                          // blocks (slots) of the replica's grid
     int debug, dbg_cap;
     // adjoint mode
     const double* __restrict__ vs;       // [3n] upstream gradient, sorted
@@ -212,8 +214,12 @@ __device__ __forceinline__ void classify(const float4* __restrict__ src, int beg
     }
 }
 
+// One slot of the pair kernel: the units slot, slot + nslots, ... of one
+// system, with the slot's energy/virial/net-force partial written to
+// part[slot].  Both the single-system kernel (slot = block) and the batched
+// persistent kernel (slots taken from a work queue) run this body.
 template <bool MIXED, bool SMALL, bool ADJ>
-__global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
+__device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const RbeConsts& c = a.c;
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
     const int units_per_row = (nc + G - 1) / G;
     const long nunits = (long)nc * nc * units_per_row;
 
-    for (long unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+    for (long unit = slot; unit < nunits; unit += nslots) {
         const int ux = (int)(unit % units_per_row);
         const int uy = (int)((unit / units_per_row) % nc);
         const int uz = (int)(unit / ((long)units_per_row * nc));
@@ -772,11 +778,48 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
     if (threadIdx.x < RBE_NPART_RBL) {
         double s = 0.0;
         for (int w = 0; w < WARPS; ++w) s += red[w][threadIdx.x];
-        a.part[blockIdx.x * RBE_NPART_RBL + threadIdx.x] = s;
+        a.part[(size_t)slot * RBE_NPART_RBL + threadIdx.x] = s;
     }
     if (ADJ)
         for (int t = threadIdx.x; t < 4 * nt2; t += blockDim.x)
-            a.part_lj[(size_t)blockIdx.x * 4 * nt2 + t] = s_glj[t];
+            a.part_lj[(size_t)slot * 4 * nt2 + t] = s_glj[t];
+}
+
+template <bool MIXED, bool SMALL, bool ADJ>
+__global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
+{
+    rbl_body<MIXED, SMALL, ADJ>(a, blockIdx.x, gridDim.x);
+}
+
+// Persistent pair kernel over many systems: each block repeatedly takes the
+// next (replica, slot) task from a queue ordered by decreasing estimated
+// cost, copies that replica's arguments to shared memory and runs the slot.
+// A slot's result does not depend on which block runs it, so the partials,
+// and every force and energy, equal those of the single-system launch.
+static_assert(sizeof(RblArgs) % 8 == 0, "RblArgs copy");
+template <bool MIXED>
+__global__ void __launch_bounds__(WARPS * 32, 2) k_rbl_batch(const RblArgs* __restrict__ args,
+                                                             const int2* __restrict__ tasks, int ntasks,
+                                                             BatchCtl* __restrict__ ctl)
+{
+    __shared__ __align__(16) RblArgs s_a;
+    __shared__ int s_task;
+    for (;;) {
+        __syncthreads();                       // the previous task is done with s_a
+        if (threadIdx.x == 0) s_task = atomicAdd(&ctl->rbl_next, 1);
+        __syncthreads();
+        const int t = s_task;
+        if (t >= ntasks) break;
+        const int2 tk = tasks[t];
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(args + tk.x);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s_a);
+        for (int k = threadIdx.x; k < (int)(sizeof(RblArgs) / 8); k += blockDim.x) dst[k] = src[k];
+        __syncthreads();
+        if (threadIdx.x == 0) s_a.step = ctl->step;
+        __syncthreads();
+        if (s_a.g.small) rbl_body<MIXED, true, false>(s_a, tk.y, s_a.nslots);
+        else rbl_body<MIXED, false, false>(s_a, tk.y, s_a.nslots);
+    }
 }
 
 template <bool MIXED, bool SMALL, bool ADJ>
@@ -805,11 +848,14 @@ int rbl_smem_bytes(const rbe_ctx* ctx)
     return (int)smem_layout(ctx->rbl, nt2, ctx->c.p, ctx->core_cap, ctx->shell_cap).total;
 }
 
-void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st, bool adjoint)
+size_t rbl_args_bytes() { return sizeof(RblArgs); }
+
+void rbl_fill_args(const rbe_ctx* ctx, int n, void* out)
 {
-    RblArgs a;
+    RblArgs& a = *static_cast<RblArgs*>(out);
+    memset(&a, 0, sizeof(a));
     a.n = n;
-    a.step = step;
+    a.step = 0;
     a.s4 = ctx->s4; a.f4 = ctx->f4; a.p4 = ctx->p4; a.tm = ctx->tm; a.perm = ctx->perm;
     a.cell_start = ctx->cell_start;
     a.lj = ctx->lj; a.F_real = ctx->F_real; a.part = ctx->part_rbl; a.status = ctx->status;
@@ -819,6 +865,20 @@ void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st, bool adjoin
     a.debug = ctx->debug; a.dbg_cap = ctx->dbg_cap_core;
     a.dbg_ncore = ctx->dbg_ncore; a.dbg_nshell = ctx->dbg_nshell; a.dbg_core = ctx->dbg_core; a.dbg_batch = ctx->dbg_batch;
     a.vs = ctx->vs; a.vbar = ctx->totals + 16; a.gq_own = ctx->gq_own; a.gq_tr = ctx->gq_tr; a.part_lj = ctx->part_lj;
+    a.nslots = ctx->grid_rbl;
+}
+
+long rbl_units(const rbe_ctx* ctx)
+{
+    const int nc = ctx->c.n_cell, G = ctx->rbl.G;
+    return (long)nc * nc * ((nc + G - 1) / G);
+}
+
+void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st, bool adjoint)
+{
+    RblArgs a;
+    rbl_fill_args(ctx, n, &a);
+    a.step = step;
     if (adjoint) a.debug = 0;
     int smem = rbl_smem_bytes(ctx);
     prof_begin(ctx, RBE_K_RBL, st);
@@ -842,4 +902,26 @@ int rbl_blocks_per_sm(const rbe_ctx* ctx)
     if (ctx->precision == RBE_MIXED) nb = small ? occupancy_t<true, true>(smem) : occupancy_t<true, false>(smem);
     else nb = small ? occupancy_t<false, true>(smem) : occupancy_t<false, false>(smem);
     return nb > 0 ? nb : 1;
+}
+
+int rbl_max_blocks_per_sm(int precision, int smem)
+{
+    int nb = 0;
+    if (precision == RBE_MIXED) {
+        cudaFuncSetAttribute(k_rbl_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbl_batch<true>, WARPS * 32, smem);
+    } else {
+        cudaFuncSetAttribute(k_rbl_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbl_batch<false>, WARPS * 32, smem);
+    }
+    return nb;
+}
+
+void launch_rbl_batch(const BatchPlan& bp, cudaStream_t st)
+{
+    const RblArgs* args = static_cast<const RblArgs*>(bp.rbl_args);
+    if (bp.precision == RBE_MIXED)
+        k_rbl_batch<true><<<bp.rbl_grid, WARPS * 32, bp.rbl_smem, st>>>(args, bp.tasks, bp.ntasks, bp.ctl);
+    else
+        k_rbl_batch<false><<<bp.rbl_grid, WARPS * 32, bp.rbl_smem, st>>>(args, bp.tasks, bp.ntasks, bp.ctl);
 }

@@ -164,7 +164,8 @@ void rbl_geometry(rbe_ctx* ctx, int n)
     g.nrows = naxis * naxis;
     // shared memory per block: two resident blocks per SM
     const int target = 110 * 1024;
-    int G = (int)lrint(48.0 / (apc > 1e-9 ? apc : 1e-9));
+    const double apu = ctx->tune_apu > 0 ? (double)ctx->tune_apu : 48.0;
+    int G = (int)lrint(apu / (apc > 1e-9 ? apc : 1e-9));
     G = G < 1 ? 1 : (G > nc ? nc : G);
     for (;; --G) {
         g.G = G;
@@ -258,9 +259,14 @@ int ensure(rbe_ctx* ctx, int n)
         // grids (fixed for a given n and device, so every reduction order is fixed)
         int nsm = ctx->n_sm;
         ctx->grid_q = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+        // pair kernel slots: a persistent grid of blocks_per_sm x SMs slots
+        // (units round-robin), or ceil(units / tune_ups) slots when tuned;
+        // never more slots than units
         int bps = rbl_blocks_per_sm(ctx);
-        int g = (n + RBE_WARPS_RBL - 1) / RBE_WARPS_RBL;
-        ctx->grid_rbl = g < bps * nsm ? g : bps * nsm;
+        long units = rbl_units(ctx);
+        long g = ctx->tune_ups > 0 ? (units + ctx->tune_ups - 1) / ctx->tune_ups : (long)bps * nsm;
+        if (g > units) g = units;
+        ctx->grid_rbl = (int)(g < 1 ? 1 : g);
         int gr = (n + 255) / 256;
         ctx->grid_rho = gr < 2 * nsm ? gr : 2 * nsm;
         ctx->last_n = n;
@@ -305,6 +311,18 @@ bool is_device_ptr(const void* p)
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
+
+}  // namespace
+
+int ctx_prepare(rbe_ctx* ctx, int n)
+{
+    if (n < 1) return set_err(ctx, RBE_EINVAL, "n >= 1 is required");
+    if (ctx->n_wmol > 0 && 3 * ctx->n_wmol > n)
+        return set_err(ctx, RBE_EINVAL, "water bonds cover %d atoms but n = %d", 3 * ctx->n_wmol, n);
+    return ensure(ctx, n);
+}
+
+namespace {
 
 int forces_device(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const double* q, const int32_t* type,
                   const int32_t* mol, double* F, cudaStream_t st)
@@ -465,6 +483,15 @@ int rbe_set_capacity(rbe_ctx* ctx, int core_cap, int shell_cap)
     if (!ctx || core_cap < 0 || shell_cap < 0) return RBE_EINVAL;
     ctx->user_core_cap = core_cap;
     ctx->user_shell_cap = shell_cap;
+    ctx->last_n = -1;
+    return RBE_OK;
+}
+
+int rbe_set_rbl_tiling(rbe_ctx* ctx, int atoms_per_unit, int units_per_slot)
+{
+    if (!ctx || atoms_per_unit < 0 || units_per_slot < 0 || atoms_per_unit > 4096) return RBE_EINVAL;
+    ctx->tune_apu = atoms_per_unit;
+    ctx->tune_ups = units_per_slot;
     ctx->last_n = -1;
     return RBE_OK;
 }

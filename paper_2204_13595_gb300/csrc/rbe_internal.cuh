@@ -135,10 +135,101 @@ struct rbe_ctx {
     int64_t prof_n[RBE_NKERNELS];
     int last_launches;
     int n_sm, last_n, last_precision;
+    int tune_apu;        // target atoms per RBL work unit (0: 48)
+    int tune_ups;        // RBL units per slot (0: persistent grid of blocks_per_sm x SMs slots)
     RblGeom rbl;
     size_t cap_atoms[20];
     size_t cap_adj[8];
 };
+
+// ---------------------------------------------------------------------------
+// Batched execution: many independent systems ("replicas") stepped together,
+// every stage one launch over all replicas.  Each replica keeps its own
+// rbe_ctx (buffers, constants, grids); the batched kernels find their replica
+// from per-stage block offsets and read its view from a device array.
+// ---------------------------------------------------------------------------
+struct RepDev {
+    int n, nmol, n_bonded_atoms;
+    long ncells;
+    int grid_q, grid_rho, grid_rbl, grid_bond, rho_chunk;
+    double kb, r0, kth, th0;
+    double dt, accel;
+    RbeConsts c;
+    // caller arrays (device, caller order)
+    double* pos;
+    double* vel;
+    const double* mass;
+    const double* q;
+    const int32_t* type;
+    const int32_t* mol;
+    double* F;
+    // context buffers
+    int* cell_count;
+    int* cell_start;
+    int* cell_of;
+    int* slot;
+    int* perm;
+    uint4* s4;
+    float4* f4;
+    double4_32a* p4;
+    int2* tm;
+    double* part_q;
+    double* part_rbl;
+    double* part_bond;
+    double* ke_part;
+    const uint64_t* kT;
+    int4* km;
+    double4_32a* kv;
+    double2* rho_part;
+    double2* rho;
+    double* totals;
+    double* F_real;
+    double* F_bond;
+    int* status;
+};
+
+// Device control block of a batch: the MD step the batched kernels use, the
+// energy trace and the head of the pair kernel's work queue.
+struct BatchCtl {
+    unsigned long long step, step0;
+    double* trace;         // [nrep][nsteps][2] or null
+    int nsteps;
+    int rbl_next;
+};
+
+// Stages of a batched step, each with its own per-replica block counts.
+enum { BK_CELLS = 0, BK_ATOMS, BK_Q, BK_KS, BK_RHO, BK_BOND, BK_REP, BK_COUNT };
+
+struct BatchPlan {
+    int nrep;
+    int precision;
+    const RepDev* rep;               // [nrep] device
+    const int* off[BK_COUNT];        // [nrep + 1] device, exclusive prefix sums of block counts
+    int total[BK_COUNT];             // blocks of each batched launch
+    BatchCtl* ctl;                   // device
+    int rho_threads;                 // threads of the batched rho kernel (max over replicas)
+    // persistent pair kernel
+    const void* rbl_args;            // [nrep] device, RblArgs (k_rbl.cu)
+    const int2* tasks;               // [ntasks] device, (replica, slot) by decreasing cost
+    int ntasks;
+    int rbl_grid, rbl_smem;
+};
+
+// Replica that owns block b of a batched launch whose per-replica block counts
+// have the exclusive prefix sums off[0..nrep] (off[0] = 0 <= b < off[nrep]),
+// b's index within that replica's grid and the size of that grid.
+__device__ __forceinline__ int rep_of_block(const int* __restrict__ off, int nrep, int b, int& local, int& count)
+{
+    int lo = 0, hi = nrep;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    local = b - off[lo];
+    count = off[lo + 1] - off[lo];
+    return lo;
+}
 
 // ---------------------------------------------------------------------------
 // device helpers
@@ -216,4 +307,20 @@ void launch_vv_kick_drift(rbe_ctx* ctx, int n, double* pos, double* vel, const d
 void launch_ke_trace(rbe_ctx* ctx, int n, const double* vel, const double* mass, double accel,
                      double* trace_slot, cudaStream_t st);
 int rbl_smem_bytes(const rbe_ctx* ctx);
+// validation and device set-up of one context for n atoms (rbe_api.cu)
+int ctx_prepare(rbe_ctx* ctx, int n);
+// batched stages (one launch each over all replicas of a plan)
+void launch_cells_batch(const BatchPlan& bp, cudaStream_t st);
+void launch_kspace_pre_batch(const BatchPlan& bp, cudaStream_t st);
+void launch_kspace_post_batch(const BatchPlan& bp, cudaStream_t st);
+void launch_vv_batch(const BatchPlan& bp, int drift, cudaStream_t st);
+void launch_ke_trace_batch(const BatchPlan& bp, cudaStream_t st);
+// op 0: set step = step0 (and the trace); 1: advance one step; 2: reset the work queue only
+void launch_ctl_batch(const BatchPlan& bp, int op, unsigned long long step0, double* trace, int nsteps,
+                      cudaStream_t st);
+void launch_rbl_batch(const BatchPlan& bp, cudaStream_t st);
+size_t rbl_args_bytes();
+void rbl_fill_args(const rbe_ctx* ctx, int n, void* out);
+int rbl_max_blocks_per_sm(int precision, int smem);
+long rbl_units(const rbe_ctx* ctx);
 int rbl_blocks_per_sm(const rbe_ctx* ctx);

@@ -24,7 +24,9 @@ KERNELS = ["quantize", "scan", "scatter", "sort", "gather", "ksample", "rho", "r
 EXPORTS = ["rbe_create", "rbe_set_coulomb", "rbe_set_lj", "rbe_set_precision", "rbe_set_water_bonds",
            "rbe_set_capacity", "rbe_forces", "rbe_step", "rbe_sync_status", "rbe_set_debug", "rbe_get_lists",
            "rbe_get_kspace", "rbe_get_info", "rbe_set_profiling", "rbe_get_profile", "rbe_last_error",
-           "rbe_destroy", "rbe_rho_noalloc", "rbe_adjoint"]
+           "rbe_destroy", "rbe_rho_noalloc", "rbe_adjoint", "rbe_set_rbl_tiling", "rbe_batch_create",
+           "rbe_batch_bind", "rbe_batch_forces", "rbe_batch_step", "rbe_batch_autotune", "rbe_batch_info",
+           "rbe_batch_sync_status", "rbe_batch_last_error", "rbe_batch_destroy"]
 ELIMIT = -8
 NOALLOC_BLOCKS, NOALLOC_PMAX = 256, 512
 
@@ -61,6 +63,18 @@ def load(path: str = LIB_PATH):
     L.rbe_destroy.restype = None
     L.rbe_rho_noalloc.argtypes = [i, vp, vp, d, i, vp, vp, vp]
     L.rbe_adjoint.argtypes = [vp, u64, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rbe_set_rbl_tiling.argtypes = [vp, i, i]
+    L.rbe_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
+    L.rbe_batch_bind.argtypes = [vp, ctypes.POINTER(i)] + [ctypes.POINTER(vp)] * 7 + [ctypes.POINTER(d)] * 2
+    L.rbe_batch_forces.argtypes = [vp, u64, vp, vp]
+    L.rbe_batch_step.argtypes = [vp, u64, i, vp, vp]
+    L.rbe_batch_autotune.argtypes = [vp, u64, ctypes.POINTER(d), i, vp]
+    L.rbe_batch_info.argtypes = [vp, ctypes.POINTER(d), i]
+    L.rbe_batch_sync_status.argtypes = [vp, vp, vp]
+    L.rbe_batch_last_error.argtypes = [vp]
+    L.rbe_batch_last_error.restype = ctypes.c_char_p
+    L.rbe_batch_destroy.argtypes = [vp]
+    L.rbe_batch_destroy.restype = None
     return L
 
 
@@ -140,6 +154,9 @@ class Context:
     def set_capacity(self, core, shell):
         self._check(self.L.rbe_set_capacity(self.h, core, shell))
 
+    def set_rbl_tiling(self, atoms_per_unit=0, units_per_slot=0):
+        self._check(self.L.rbe_set_rbl_tiling(self.h, int(atoms_per_unit), int(units_per_slot)))
+
     def set_debug(self, on, cap_core=0):
         self._check(self.L.rbe_set_debug(self.h, int(on), cap_core))
 
@@ -210,6 +227,84 @@ class Context:
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             self.L.rbe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """rbe_batch_*: many contexts (replicas) stepped together, one launch per
+    stage over all replicas, one MD step replayed as a CUDA graph.  The
+    contexts must outlive the batch."""
+
+    def __init__(self, contexts):
+        self.L = lib()
+        self.ctxs = list(contexts)
+        arr = (ctypes.c_void_p * len(self.ctxs))(*[c.h.value for c in self.ctxs])
+        h = ctypes.c_void_p()
+        rc = self.L.rbe_batch_create(ctypes.byref(h), len(self.ctxs), arr)
+        if rc != OK or not h.value:
+            raise RbeError(rc, "rbe_batch_create rejected the contexts")
+        self.h = h
+        self.nrep = len(self.ctxs)
+        self._keep = None
+
+    def _check(self, rc):
+        if rc != OK:
+            raise RbeError(rc, self.L.rbe_batch_last_error(self.h).decode(errors="replace"))
+        return rc
+
+    def bind(self, pos, q, typ, mol, F, vel=None, mass=None, dt=None, accel=None):
+        """Per-replica lists of device tensors (typ, mol, vel, mass entries may
+        be None); dt and accel per-replica lists of floats (or None)."""
+        R = self.nrep
+        VP = ctypes.c_void_p * R
+
+        def arr(xs):
+            return VP(*[_ptr(x) if xs is not None else None for x in (xs if xs is not None else [None] * R)])
+        n = (ctypes.c_int * R)(*[int(p.shape[0]) for p in pos])
+        dts = (ctypes.c_double * R)(*[float(x) for x in dt]) if dt is not None else None
+        acs = (ctypes.c_double * R)(*[float(x) for x in accel]) if accel is not None else None
+        args = [n, arr(pos), arr(q), arr(typ), arr(mol), arr(F), arr(vel), arr(mass)]
+        self._keep = (pos, q, typ, mol, F, vel, mass)
+        return self._check(self.L.rbe_batch_bind(self.h, *args, dts, acs))
+
+    def forces(self, step, energy=False, stream=None):
+        """Forces of every replica at `step` into the bound F; with energy=True
+        returns the [nrep, NE] energies (waits)."""
+        E = np.zeros((self.nrep, NE)) if energy else None
+        self._check(self.L.rbe_batch_forces(self.h, step, _ptr(E), _stream(stream)))
+        return E
+
+    def step(self, step0, nsteps, trace=None, stream=None):
+        return self._check(self.L.rbe_batch_step(self.h, step0, nsteps, _ptr(trace), _stream(stream)))
+
+    def autotune(self, step=0, stream=None):
+        out = (ctypes.c_double * 64)()
+        self._check(self.L.rbe_batch_autotune(self.h, step, out, 64, _stream(stream)))
+        nf = int(self.info()["families"])
+        fams = [dict(atoms_per_unit=int(out[3 * f]), units_per_slot=int(out[3 * f + 1]), ms=out[3 * f + 2])
+                for f in range(nf)]
+        return dict(families=fams, untuned_ms=out[3 * nf])
+
+    def info(self):
+        out = (ctypes.c_double * 7)()
+        self._check(self.L.rbe_batch_info(self.h, out, 7))
+        keys = ["replicas", "atoms", "tasks", "rbl_blocks", "rbl_smem", "launches_per_step", "families"]
+        return {k: out[i] for i, k in enumerate(keys)}
+
+    def sync_status(self, stream=None):
+        st = np.zeros(self.nrep, np.int32)
+        first = self.L.rbe_batch_sync_status(self.h, _ptr(st), _stream(stream))
+        return first, st
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.rbe_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -23,6 +23,7 @@ import math
 from dataclasses import dataclass, field
 
 import numpy as np
+from scipy.spatial import cKDTree
 
 WATER_DENSITY = 0.0334          # molecules per A^3
 K_E_WATER = 1389.35458          # kJ mol^-1 A e^-2
@@ -88,41 +89,65 @@ def _maxwell(rng, mass, kT, accel):
     return v - p
 
 
-def _rsa(rng, n, L, dmin):
-    """Random sequential insertion of n points in a periodic cube, min distance dmin."""
-    nc = max(1, int(L // dmin))
+def _rsa(rng, n, L, dmin, chunk=2048):
+    """Random sequential insertion of n points in a periodic cube, min distance dmin.
+
+    Candidates are uniform points drawn three coordinates at a time from rng;
+    each is accepted when it is at least dmin (minimum image) from every point
+    accepted before it.  Candidates are drawn in chunks and tested against the
+    accepted set through a grid of cells of edge < dmin/sqrt(3) (at most one
+    point per cell), then in order against the chunk's earlier acceptances; on
+    return rng has consumed exactly the candidates up to the n-th acceptance,
+    as a one-at-a-time insertion would."""
+    state = rng.bit_generator.state
+    nc = int(math.floor(L * math.sqrt(3.0) / dmin)) + 1
     w = L / nc
-    cells: dict = {}
+    reach = int(math.ceil(dmin / w))
+    rr = np.arange(-reach, reach + 1)
+    offs = np.stack(np.meshgrid(rr, rr, rr, indexing="ij"), -1).reshape(-1, 3)
+    grid = np.full(nc ** 3, -1, dtype=np.int64)
     out = np.zeros((n, 3))
     k = 0
-    tries = 0
+    used = 0
+    d2min = dmin * dmin
     while k < n:
-        tries += 1
-        if tries > 200 * n + 10000:
+        if used > 200 * n + 10000:
             raise RuntimeError("random sequential insertion did not converge")
-        x = rng.random(3) * L
-        c = (x // w).astype(int) % nc
-        ok = True
-        for dx in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dz in (-1, 0, 1):
-                    key = ((c[0] + dx) % nc, (c[1] + dy) % nc, (c[2] + dz) % nc)
-                    for j in cells.get(key, ()):
-                        d = out[j] - x
-                        d -= L * np.round(d / L)
-                        if d @ d < dmin * dmin:
-                            ok = False
-                            break
-                    if not ok:
-                        break
-                if not ok:
-                    break
-            if not ok:
-                break
-        if ok:
-            out[k] = x
-            cells.setdefault((c[0], c[1], c[2]), []).append(k)
-            k += 1
+        X = rng.random((chunk, 3)) * L
+        c = np.floor(X / w).astype(np.int64) % nc
+        nb = (c[:, None, :] + offs[None, :, :]) % nc
+        occ = grid[nb[..., 0] + nc * (nb[..., 1] + nc * nb[..., 2])]
+        ti, si = np.nonzero(occ >= 0)
+        d = out[occ[ti, si]] - X[ti]
+        d -= L * np.round(d / L)
+        clash = np.zeros(chunk, dtype=bool)
+        clash[ti[(d * d).sum(-1) < d2min]] = True
+        # in order against the chunk's earlier acceptances: only candidates
+        # within dmin of an earlier candidate need the sequential test
+        acc = ~clash
+        cand = np.nonzero(acc)[0]
+        if cand.size > 1:
+            pairs = cKDTree(X[cand], boxsize=L).query_pairs(dmin, output_type="ndarray")
+            if pairs.size:
+                i, j = cand[pairs[:, 0]], cand[pairs[:, 1]]
+                e = X[i] - X[j]
+                e -= L * np.round(e / L)
+                near = (e * e).sum(-1) < d2min
+                i, j = np.minimum(i, j)[near], np.maximum(i, j)[near]
+                order = np.argsort(j, kind="stable")
+                for a, b in zip(i[order], j[order]):
+                    if acc[a]:
+                        acc[b] = False
+        take = np.nonzero(acc)[0][: n - k]
+        if take.size:
+            ci = c[take]
+            grid[ci[:, 0] + nc * (ci[:, 1] + nc * ci[:, 2])] = np.arange(k, k + take.size)
+            out[k:k + take.size] = X[take]
+            k += take.size
+        used += int(take[-1]) + 1 if k == n else chunk
+    # leave rng where a one-candidate-at-a-time insertion would have left it
+    rng.bit_generator.state = state
+    rng.random((used, 3))
     return out
 
 
@@ -180,6 +205,27 @@ def water(n_mol: int = 30000, seed: int = 2, r_c: float = 5.0, r_s: float = 10.0
     return System("water", L, pos, q, typ, mol, mass, vel, alpha_for(r_s), r_c, r_s, p, P,
                   K_E_WATER, (0.650, 0.0), (3.166, 1.0), ACCEL_WATER, dt, seed,
                   n_water_mol=n_mol, bonds=(KB_OH, R_OH, KTH_HOH, THETA_HOH))
+
+
+def batch_replicas(nrep: int = 64, n_min: int = 1000, n_max: int = 50000, seed0: int = 0) -> list:
+    """A suite of independent systems of uneven size for batched stepping:
+    replica r (seed seed0 + r) has about N atoms with log N uniform in
+    [log n_min, log n_max] (drawn from a generator seeded with seed0); even
+    seeds are 1:1 electrolytes (N even, P = 100, density 0.25 sigma^-3 as in
+    the 2,000-ion box of side 20 sigma), odd seeds water boxes (N a multiple
+    of 3, P = 200).  Each replica has its own box, alpha and cutoffs."""
+    rng = np.random.default_rng(seed0 + 7919)
+    out = []
+    for r in range(nrep):
+        seed = seed0 + r
+        N = float(np.exp(rng.uniform(math.log(n_min), math.log(n_max))))
+        if seed % 2 == 0:
+            n = max(2, int(round(N / 2)) * 2)
+            L = (n / 0.25) ** (1.0 / 3.0)
+            out.append(electrolyte(n=n, L=L, seed=seed, P=100))
+        else:
+            out.append(water(n_mol=max(1, int(round(N / 3))), seed=seed, P=200))
+    return out
 
 
 def nacl_crystal(cells: int = 2, r0: float = 1.0):

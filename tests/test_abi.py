@@ -64,3 +64,36 @@ def test_parameter_tables_match_oracle_definitions(L):
         M, H, T = oracle.k_table(s.alpha, s.L)
         assert info[2] == M and info[3] == oracle.S(s.alpha, s.L)
         L.rbe_destroy(h)
+
+
+def test_binding_argument_counts_match_header(L):
+    """Every ctypes prototype set by the binding has as many arguments as the
+    header's declaration (a mismatch would pass garbage through the ABI)."""
+    src = open(os.path.join(ROOT, "include", "rbe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = dict(re.findall(r"\b(rbe_[a-z_]+)\s*\(([^;{)]*)\)\s*;", src))
+    assert len(protos) >= 25
+    for name, params in protos.items():
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        fn = getattr(L, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+
+
+def test_batch_create_validates_contexts(L):
+    hb = ctypes.c_void_p()
+    assert L.rbe_batch_create(ctypes.byref(hb), 0, None) == -1
+    h = ctypes.c_void_p()
+    assert L.rbe_create(ctypes.byref(h), 20.0, 0.3, 2.5, 5.0, 10, 100, 1) == 0
+    arr = (ctypes.c_void_p * 2)(h.value, h.value)
+    assert L.rbe_batch_create(ctypes.byref(hb), 2, arr) == -1       # the same context twice
+    arr1 = (ctypes.c_void_p * 1)(h.value)
+    assert L.rbe_batch_create(ctypes.byref(hb), 1, arr1) == 0
+    info = (ctypes.c_double * 7)()
+    assert L.rbe_batch_info(hb, info, 7) == 0 and info[0] == 1
+    assert L.rbe_batch_forces(hb, 0, None, None) == -1                 # not bound
+    L.rbe_batch_destroy(hb)
+    assert L.rbe_set_rbl_tiling(h, -1, 0) == -1
+    assert L.rbe_set_rbl_tiling(h, 32, 2) == 0
+    L.rbe_destroy(h)
