@@ -237,9 +237,10 @@ int rbe_rho_noalloc(int n, const double* pos, const double* q, double box_L, int
 void rbe_destroy(rbe_ctx* ctx);
 
 /* Work decomposition of the RBL pair kernel (Sec. 2.3 stencil walk): a work
- * unit is a run of cells along x holding about atoms_per_unit atoms (0: 48);
- * the kernel's grid has ceil(units / units_per_slot) slots (0: a persistent
- * grid of resident blocks x SMs slots).  Results do not depend on the unit
+ * unit is a run of cells along x holding about atoms_per_unit atoms (0: 48;
+ * shared memory caps the width); the kernel's grid has
+ * ceil(units / units_per_slot) slots, one block each (0: about three units
+ * per slot, and no fewer slots than one wave of resident blocks).  Results do not depend on the unit
  * width except through the order of the block partials of energies, virial
  * and net force (rounding only).  rbe_batch_autotune sets these. */
 int rbe_set_rbl_tiling(rbe_ctx* ctx, int atoms_per_unit, int units_per_slot);
@@ -284,13 +285,16 @@ int rbe_batch_forces(rbe_batch* b, uint64_t step, double* energy, void* cuda_str
  * [nrep][nsteps][2] of (potential, kinetic / accel) per step. */
 int rbe_batch_step(rbe_batch* b, uint64_t step0, int nsteps, double* energy_trace, void* cuda_stream);
 
-/* Project-written autotuner of the pair kernel's tiling: for each family of
- * replicas (same cutoffs, p and precision) it times the batched pair kernel
- * over candidate atoms_per_unit and units_per_slot values, keeps the
- * fastest, sets them on the contexts (rbe_set_rbl_tiling) and re-binds.
- * Runs force steps at step `step` (the bound positions are not moved).
- * out (may be NULL, nout entries): per family the chosen atoms_per_unit,
- * units_per_slot and the kernel time in ms, then the untuned time. */
+/* Project-written autotuner of the pair kernel: for each family of replicas
+ * (same cutoffs and p) it times the batched pair kernel over candidate
+ * atoms_per_unit and units_per_slot values (coordinate descent), keeps the
+ * fastest, sets them on the contexts (rbe_set_rbl_tiling), then picks the
+ * kernel form (persistent blocks over the work queue, or one block per task)
+ * and re-binds.  Runs force steps at step `step`: F receives the forces at
+ * (pos, step); positions are not moved.  out (may be NULL, nout entries):
+ * per family the chosen atoms_per_unit, units_per_slot and the kernel time
+ * in ms; then the form (1 persistent, 0 one block per task), the final
+ * kernel time and the untuned time (ms). */
 int rbe_batch_autotune(rbe_batch* b, uint64_t step, double* out, int nout, void* cuda_stream);
 
 /* Plan facts: out[0] replicas, [1] total atoms, [2] pair-kernel tasks,

@@ -244,6 +244,32 @@ __device__ double block_sum_col(const double* __restrict__ src, int nrow, int st
     return r;
 }
 
+// Fixed-order block reduction of the rows of a row-major [nrow][NC] table:
+// thread t sums rows t, t + blockDim, ... (each row one contiguous read),
+// then a tree over the threads, column by column.
+template <int NC>
+__device__ void block_sum_rows(const double* __restrict__ src, int nrow, double* out, double* sh)
+{
+    double acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
+        const double* row = src + (size_t)r * NC;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] += row[c];
+    }
+    for (int c = 0; c < NC; ++c) {
+        sh[threadIdx.x] = acc[c];
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        out[c] = sh[0];
+        __syncthreads();
+    }
+}
+
 // totals: E[0..5], W[6..11], corr[12..14]
 __device__ __forceinline__ void finalize_body(int n, const RbeConsts& c, const double* __restrict__ part_rbl,
                                               int grid_rbl, const double* __restrict__ part_q, int grid_q,
@@ -252,7 +278,7 @@ __device__ __forceinline__ void finalize_body(int n, const RbeConsts& c, const d
 {
     __shared__ double sh[TPB];
     double r[RBE_NPART_RBL];
-    for (int q = 0; q < RBE_NPART_RBL; ++q) r[q] = block_sum_col(part_rbl, grid_rbl, RBE_NPART_RBL, q, sh);
+    block_sum_rows<RBE_NPART_RBL>(part_rbl, grid_rbl, r, sh);
     double qs[RBE_NPART_Q];
     for (int q = 0; q < RBE_NPART_Q; ++q) qs[q] = block_sum_col(part_q, grid_q, RBE_NPART_Q, q, sh);
     double kt[7];

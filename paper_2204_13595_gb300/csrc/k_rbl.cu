@@ -791,22 +791,25 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
     rbl_body<MIXED, SMALL, ADJ>(a, blockIdx.x, gridDim.x);
 }
 
-// Persistent pair kernel over many systems: each block repeatedly takes the
-// next (replica, slot) task from a queue ordered by decreasing estimated
-// cost, copies that replica's arguments to shared memory and runs the slot.
-// A slot's result does not depend on which block runs it, so the partials,
-// and every force and energy, equal those of the single-system launch.
+// Pair kernel over many systems.  PERSIST: a grid of resident blocks, each
+// repeatedly taking the next (replica, slot) task from a queue ordered by
+// decreasing estimated cost; otherwise one block per task in that order (the
+// hardware block scheduler then hands them out in the same order).  A block
+// copies its replica's arguments to shared memory and runs the slot.  A
+// slot's result does not depend on which block runs it, so the partials, and
+// every force and energy, equal those of the single-system launch.
 static_assert(sizeof(RblArgs) % 8 == 0, "RblArgs copy");
-template <bool MIXED>
+template <bool MIXED, bool PERSIST>
 __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl_batch(const RblArgs* __restrict__ args,
                                                              const int2* __restrict__ tasks, int ntasks,
                                                              BatchCtl* __restrict__ ctl)
 {
     __shared__ __align__(16) RblArgs s_a;
     __shared__ int s_task;
-    for (;;) {
+    for (int iter = 0;; ++iter) {
+        if (!PERSIST && iter > 0) break;
         __syncthreads();                       // the previous task is done with s_a
-        if (threadIdx.x == 0) s_task = atomicAdd(&ctl->rbl_next, 1);
+        if (threadIdx.x == 0) s_task = PERSIST ? atomicAdd(&ctl->rbl_next, 1) : (int)blockIdx.x;
         __syncthreads();
         const int t = s_task;
         if (t >= ntasks) break;
@@ -904,24 +907,38 @@ int rbl_blocks_per_sm(const rbe_ctx* ctx)
     return nb > 0 ? nb : 1;
 }
 
-int rbl_max_blocks_per_sm(int precision, int smem)
+namespace {
+template <bool MIXED, bool PERSIST>
+int occ_batch(int smem)
 {
     int nb = 0;
-    if (precision == RBE_MIXED) {
-        cudaFuncSetAttribute(k_rbl_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbl_batch<true>, WARPS * 32, smem);
-    } else {
-        cudaFuncSetAttribute(k_rbl_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbl_batch<false>, WARPS * 32, smem);
-    }
+    cudaFuncSetAttribute(k_rbl_batch<MIXED, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbl_batch<MIXED, PERSIST>, WARPS * 32, smem);
     return nb;
+}
+}  // namespace
+
+int rbl_max_blocks_per_sm(int precision, int smem)
+{
+    int a, b;
+    if (precision == RBE_MIXED) { a = occ_batch<true, true>(smem); b = occ_batch<true, false>(smem); }
+    else { a = occ_batch<false, true>(smem); b = occ_batch<false, false>(smem); }
+    return a < b ? a : b;
 }
 
 void launch_rbl_batch(const BatchPlan& bp, cudaStream_t st)
 {
     const RblArgs* args = static_cast<const RblArgs*>(bp.rbl_args);
-    if (bp.precision == RBE_MIXED)
-        k_rbl_batch<true><<<bp.rbl_grid, WARPS * 32, bp.rbl_smem, st>>>(args, bp.tasks, bp.ntasks, bp.ctl);
-    else
-        k_rbl_batch<false><<<bp.rbl_grid, WARPS * 32, bp.rbl_smem, st>>>(args, bp.tasks, bp.ntasks, bp.ctl);
+    const int grid = bp.rbl_persistent ? bp.rbl_grid : bp.ntasks;
+    if (bp.precision == RBE_MIXED) {
+        if (bp.rbl_persistent)
+            k_rbl_batch<true, true><<<grid, WARPS * 32, bp.rbl_smem, st>>>(args, bp.tasks, bp.ntasks, bp.ctl);
+        else
+            k_rbl_batch<true, false><<<grid, WARPS * 32, bp.rbl_smem, st>>>(args, bp.tasks, bp.ntasks, bp.ctl);
+    } else {
+        if (bp.rbl_persistent)
+            k_rbl_batch<false, true><<<grid, WARPS * 32, bp.rbl_smem, st>>>(args, bp.tasks, bp.ntasks, bp.ctl);
+        else
+            k_rbl_batch<false, false><<<grid, WARPS * 32, bp.rbl_smem, st>>>(args, bp.tasks, bp.ntasks, bp.ctl);
+    }
 }

@@ -259,12 +259,18 @@ int ensure(rbe_ctx* ctx, int n)
         // grids (fixed for a given n and device, so every reduction order is fixed)
         int nsm = ctx->n_sm;
         ctx->grid_q = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
-        // pair kernel slots: a persistent grid of blocks_per_sm x SMs slots
-        // (units round-robin), or ceil(units / tune_ups) slots when tuned;
-        // never more slots than units
+        // pair kernel slots (one block each, units round-robin over the
+        // slots): ceil(units / tune_ups) when tuned; by default about three
+        // units per slot, and at least one full wave of resident blocks
+        // (measured on the 1.2M-atom water box: 3-4 units per slot beat a
+        // persistent grid of blocks_per_sm x SMs slots by 11%, the hardware
+        // block scheduler balancing the uneven unit costs); never more
+        // slots than units
         int bps = rbl_blocks_per_sm(ctx);
         long units = rbl_units(ctx);
-        long g = ctx->tune_ups > 0 ? (units + ctx->tune_ups - 1) / ctx->tune_ups : (long)bps * nsm;
+        const long wave = (long)bps * nsm;
+        long g = ctx->tune_ups > 0 ? (units + ctx->tune_ups - 1) / ctx->tune_ups : (units + 2) / 3;
+        if (ctx->tune_ups == 0 && g < wave) g = wave;
         if (g > units) g = units;
         ctx->grid_rbl = (int)(g < 1 ? 1 : g);
         int gr = (n + 255) / 256;

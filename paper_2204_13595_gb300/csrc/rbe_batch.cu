@@ -6,8 +6,10 @@
 //   cells:   zero counts, quantise+count, scan (block per replica), scatter,
 //            in-cell sort, gather
 //   k space: sample, rho partials, rho sum, [bonded water]
-//   pairs:   one persistent launch of the RBL kernel over a (replica, slot)
-//            work queue ordered by decreasing estimated cost
+//   pairs:   one launch of the RBL kernel over all (replica, slot) tasks,
+//            ordered by decreasing estimated cost: persistent resident
+//            blocks pulling tasks from a device queue, or one block per task
+//            (the autotuner picks the faster form)
 //   finish:  finalize (block per replica), k-space force + combination
 // and one MD step (velocity Verlet around it) is captured once as a CUDA
 // graph and replayed, the step number living in a device control block.
@@ -45,6 +47,7 @@ struct rbe_batch {
     size_t tasks_cap = 0;
     BatchCtl* d_ctl = nullptr;
     BatchPlan plan{};
+    int persistent = 1;      // pair kernel form (autotuned)
     int launches_force = 0, launches_step = 0;
     long total_atoms = 0;
     int n_sm = 0;
@@ -255,6 +258,7 @@ int build_plan(rbe_batch* b)
     p.ntasks = (int)tasks.size();
     p.rbl_grid = bps * b->n_sm;
     p.rbl_smem = smem;
+    p.rbl_persistent = b->persistent;
     b->launches_force = 6 + 3 + (bonds ? 1 : 0) + 1 + 2;
     b->launches_step = b->launches_force + 1 + 2 + 2;   // + control, two half kicks, kinetic energy + trace
     return RBE_OK;
@@ -458,7 +462,7 @@ int rbe_batch_autotune(rbe_batch* b, uint64_t step, double* out, int nout, void*
     if ((rc = measure(&t_untuned))) return rc;
 
     static const int cand_apu[] = {16, 24, 32, 48, 64, 96, 128};
-    static const int cand_ups[] = {0, 1, 2, 4, 8};
+    static const int cand_ups[] = {0, 1, 2, 3, 4, 8};
     std::vector<double> res;
     double best_all = t_untuned;
     for (int f = 0; f < b->nfam; ++f) {
@@ -482,6 +486,17 @@ int rbe_batch_autotune(rbe_batch* b, uint64_t step, double* out, int nout, void*
         res.push_back(best_u);
         res.push_back(best);
     }
+    // kernel form: persistent blocks over the queue, or one block per task
+    {
+        const int cur = b->persistent;
+        b->persistent = 1 - cur;
+        double t;
+        if ((rc = measure(&t))) return rc;
+        if (!(t < best_all)) b->persistent = cur;
+        else best_all = t;
+    }
+    res.push_back((double)b->persistent);
+    res.push_back(best_all);
     res.push_back(t_untuned);
     if ((rc = build_plan(b))) return rc;
     // leave the forces at `step` consistent with the chosen tiling

@@ -136,7 +136,7 @@ struct rbe_ctx {
     int last_launches;
     int n_sm, last_n, last_precision;
     int tune_apu;        // target atoms per RBL work unit (0: 48)
-    int tune_ups;        // RBL units per slot (0: persistent grid of blocks_per_sm x SMs slots)
+    int tune_ups;        // RBL units per slot (0: about 3, at least one wave of resident blocks)
     RblGeom rbl;
     size_t cap_atoms[20];
     size_t cap_adj[8];
@@ -213,6 +213,7 @@ struct BatchPlan {
     const int2* tasks;               // [ntasks] device, (replica, slot) by decreasing cost
     int ntasks;
     int rbl_grid, rbl_smem;
+    int rbl_persistent;              // 1: rbl_grid resident blocks over the queue; 0: one block per task
 };
 
 // Replica that owns block b of a batched launch whose per-replica block counts

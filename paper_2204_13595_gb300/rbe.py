@@ -289,7 +289,8 @@ class Batch:
         nf = int(self.info()["families"])
         fams = [dict(atoms_per_unit=int(out[3 * f]), units_per_slot=int(out[3 * f + 1]), ms=out[3 * f + 2])
                 for f in range(nf)]
-        return dict(families=fams, untuned_ms=out[3 * nf])
+        return dict(families=fams, persistent=bool(out[3 * nf]), tuned_ms=out[3 * nf + 1],
+                    untuned_ms=out[3 * nf + 2])
 
     def info(self):
         out = (ctypes.c_double * 7)()
