@@ -70,11 +70,20 @@ class Params(ctypes.Structure):
         ("shift_lj", ctypes.c_int),
         ("eps", ctypes.c_double * MAXT),
         ("sigma", ctypes.c_double * MAXT),
+        ("shell_mode", ctypes.c_int),
+        ("lj_rc_factor", ctypes.c_double),
+        ("kpool", ctypes.c_int),
+        ("kpool_burn", ctypes.c_int),
     ]
 
 
-def make_params(L, alpha, r_c, r_s, p, P, seed, k_e=1.0, eps=(0.0,), sigma=(1.0,), shift_lj=0):
+def make_params(L, alpha, r_c, r_s, p, P, seed, k_e=1.0, eps=(0.0,), sigma=(1.0,), shift_lj=0, shell_mode=0,
+                lj_rc_factor=0.0, kpool=0, kpool_burn=0):
+    """Parameters of the estimator; shell_mode, lj_rc_factor, kpool and
+    kpool_burn select the variants of reading R9 (defaults: the base method)."""
     pr = Params()
+    pr.shell_mode, pr.lj_rc_factor = int(shell_mode), float(lj_rc_factor)
+    pr.kpool, pr.kpool_burn = int(kpool), int(kpool_burn)
     pr.L, pr.alpha, pr.r_c, pr.r_s, pr.k_e = float(L), float(alpha), float(r_c), float(r_s), float(k_e)
     pr.p, pr.P, pr.seed = int(p), int(P), int(seed)
     pr.ntypes = len(eps)
@@ -110,6 +119,10 @@ def lib():
             L.orc_k_table.argtypes = [d, d, ctypes.c_int, _P(u64)]
             L.orc_k_table.restype = d
             L.orc_sample_k.argtypes = [u64, u64, ctypes.c_int, d, d, _P(i32)]
+            L.orc_mh_tables.argtypes = [d, d, ctypes.c_int, _P(d), _P(d), _P(u64)]
+            L.orc_kpool.argtypes = [u64, d, d, ctypes.c_int, ctypes.c_int, _P(i32)]
+            L.orc_kpool.restype = d
+            L.orc_sample_k_params.argtypes = [_P(Params), u64, _P(i32)]
             L.orc_S.argtypes = [d, d]
             L.orc_S.restype = d
             L.orc_floyd.argtypes = [u64, ctypes.c_int, _P(u64), _P(u64)]
@@ -174,6 +187,31 @@ def k_table(alpha, L):
     T = np.zeros(2 * M + 1, dtype=np.uint64)
     H = lib().orc_k_table(alpha, L, M, _ptr(T, ctypes.c_uint64))
     return M, H, T
+
+
+def mh_tables(alpha, L):
+    """Target w_m, proposal q_m and the proposal's inverse-CDF thresholds of the
+    Metropolis-Hastings pool (reading R9), |m| <= M."""
+    M = lib().orc_kmax(alpha, L)
+    w, q = np.zeros(2 * M + 1), np.zeros(2 * M + 1)
+    Tq = np.zeros(2 * M + 1, dtype=np.uint64)
+    lib().orc_mh_tables(alpha, L, M, _ptr(w, ctypes.c_double), _ptr(q, ctypes.c_double),
+                        _ptr(Tq, ctypes.c_uint64))
+    return M, w, q, Tq
+
+
+def kpool(seed, alpha, L, K, burn):
+    """The pool [K, 3] and the chains' acceptance rate."""
+    pool = np.zeros((K, 3), dtype=np.int32)
+    acc = lib().orc_kpool(seed, alpha, L, K, burn, _ptr(pool, ctypes.c_int32))
+    return pool, acc
+
+
+def sample_k_params(pr, step):
+    """The P wave-vector integers of a step under the parameters' sampling mode."""
+    m = np.zeros((pr.P, 3), dtype=np.int32)
+    lib().orc_sample_k_params(ctypes.byref(pr), step, _ptr(m, ctypes.c_int32))
+    return m
 
 
 def sample_k(seed, step, P, alpha, L):

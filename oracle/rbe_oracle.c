@@ -43,6 +43,17 @@
  *  R7  Same-molecule (excluded) pairs keep their membership in C(i)/S(i) but
  *      their pair term is the Ewald exclusion correction
  *      -k_e q_i q_j erf(sqrt(alpha) r)/r instead of erfc + LJ.
+ *  R9  Variants (Algorithm 1 and Sec. 2.3 leave these open): shell_mode 1
+ *      draws the p slots of B(i) independently and uniformly with
+ *      replacement (same words, ordinal floor(u N_S / 2^64)), weight N_S/p;
+ *      lj_rc_factor f > 0 truncates the LJ term of pair (a, b) at
+ *      min(f sigma_ab, r_s), shifted there when shift_lj is set (f = 2^(1/6)
+ *      with the shift is the WCA soft sphere of the paper's electrolytes,
+ *      Sec. 3.1); kpool K > 0 replaces the fresh draws of R4 by the pool of
+ *      Algorithm 1: K samples of a Metropolis-Hastings chain per axis
+ *      (proposal round(x), x ~ N(0, alpha L^2 / (2 pi^2)), Sec. 2.2), and
+ *      sample l of a step is pool entry floor(u K / 2^64), u word 0 of the
+ *      block at counter (l, 0, step, 5).
  *  R8  Energy estimator: E_real = 1/2 sum_i [sum_C u_ij + w_i sum_B u_ij];
  *      E_k = (S/P) sum_l (2 pi k_e / (V k_l^2)) |rho_l|^2;
  *      E_self = -k_e sqrt(alpha/pi) sum q^2  (Eq. (2.3) terms, reweighted).
@@ -73,6 +84,10 @@ typedef struct orc_params {
     int shift_lj;    /* 1: LJ energy shifted to zero at r_s               */
     double eps[ORC_MAXT];    /* per-type LJ epsilon                       */
     double sigma[ORC_MAXT];  /* per-type LJ sigma                         */
+    int shell_mode;          /* R9: 0 without replacement, 1 with         */
+    double lj_rc_factor;     /* R9: 0 LJ to r_s, f > 0 cut at f sigma_ab  */
+    int kpool;               /* R9: 0 fresh draws, K > 0 MH pool of K     */
+    int kpool_burn;          /* R9: burn-in iterations of the MH chains   */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -246,6 +261,90 @@ int orc_sample_k(uint64_t seed, uint64_t step, int P, double alpha, double L, in
     return worst;
 }
 
+/* Metropolis-Hastings pool of k samples (R9; Algorithm 1, pool step; Sec. 2.2).
+ * Per axis, target w_m = exp(-pi^2 m^2 / (alpha L^2)) and proposal
+ * q_m = P(round(X) = m), X ~ N(0, s^2), s^2 = alpha L^2 / (2 pi^2), both on
+ * |m| <= M (the truncation of R4) and normalised there.  Proposals are drawn
+ * by inverse CDF on 64-bit thresholds of q (as R4 draws w); the move from m
+ * to m* is accepted when u < (w_m* q_m) / (w_m q_m*), u = (word >> 11) 2^-53.
+ * Iteration t of axis a uses the block at counter (t, a, 0, 4): word 0 the
+ * proposal, word 1 the acceptance.  The chains start at 0; after `burn`
+ * iterations every iteration emits (m_x, m_y, m_z) unless it is (0,0,0),
+ * until K samples are collected. */
+void orc_mh_tables(double alpha, double L, int M, double* w, double* q, uint64_t* Tq)
+{
+    double aL2 = alpha * L * L;
+    double c = ORC_PI * ORC_PI / aL2;
+    double s = sqrt(aL2 / (2.0 * ORC_PI * ORC_PI));
+    double sq2 = s * sqrt(2.0);
+    double Q = 0.0;
+    for (int m = -M; m <= M; ++m) {
+        w[m + M] = exp(-c * (double)m * (double)m);
+        /* P(m - 1/2 <= X < m + 1/2) through complementary error functions of |m| */
+        double am = fabs((double)m);
+        double lo = (am - 0.5) / sq2, hi = (am + 0.5) / sq2;
+        double qm = (m == 0) ? erf(0.5 / sq2) : 0.5 * (erfc(lo) - erfc(hi));
+        q[m + M] = qm;
+        Q += qm;
+    }
+    double acc = 0.0;
+    for (int m = -M; m <= M; ++m) {
+        acc += q[m + M];
+        double v = (acc / Q) * 18446744073709551616.0;
+        Tq[m + M] = (v >= 18446744073709551616.0) ? UINT64_MAX : (uint64_t)v;
+    }
+}
+
+/* Fills pool[3K]; returns the accepted fraction over all axes and iterations. */
+double orc_kpool(uint64_t seed, double alpha, double L, int K, int burn, int32_t* pool)
+{
+    int M = orc_kmax(alpha, L);
+    double* w = (double*)malloc(sizeof(double) * (size_t)(2 * M + 1));
+    double* q = (double*)malloc(sizeof(double) * (size_t)(2 * M + 1));
+    uint64_t* Tq = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(2 * M + 1));
+    orc_mh_tables(alpha, L, M, w, q, Tq);
+    int m[3] = {0, 0, 0};
+    long acc = 0, tries = 0;
+    int k = 0;
+    for (uint64_t t = 0; k < K; ++t) {
+        for (int a = 0; a < 3; ++a) {
+            uint64_t blk[4];
+            rng_block(seed, t, (uint64_t)a, 0, 4, blk);
+            int mp = inv_cdf(blk[0], Tq, M);
+            double u = (double)(blk[1] >> 11) * 1.1102230246251565e-16;
+            double r = (w[mp + M] * q[m[a] + M]) / (w[m[a] + M] * q[mp + M]);
+            ++tries;
+            if (u < r) { m[a] = mp; ++acc; }
+        }
+        if (t < (uint64_t)burn) continue;
+        if (m[0] == 0 && m[1] == 0 && m[2] == 0) continue;
+        pool[3 * k + 0] = m[0]; pool[3 * k + 1] = m[1]; pool[3 * k + 2] = m[2];
+        ++k;
+    }
+    free(w); free(q); free(Tq);
+    return (double)acc / (double)tries;
+}
+
+/* The P samples of a step under the parameters' sampling mode (R4 or R9). */
+static void sample_k_mode(const orc_params* pr, uint64_t step, int32_t* m)
+{
+    if (pr->kpool <= 0) {
+        orc_sample_k(pr->seed, step, pr->P, pr->alpha, pr->L, m);
+        return;
+    }
+    int32_t* pool = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)pr->kpool);
+    orc_kpool(pr->seed, pr->alpha, pr->L, pr->kpool, pr->kpool_burn, pool);
+    for (int l = 0; l < pr->P; ++l) {
+        uint64_t blk[4];
+        rng_block(pr->seed, (uint64_t)l, 0, step, 5, blk);
+        uint64_t e = uniform_below(blk[0], (uint64_t)pr->kpool);
+        for (int a = 0; a < 3; ++a) m[3 * l + a] = pool[3 * e + a];
+    }
+    free(pool);
+}
+
+void orc_sample_k_params(const orc_params* pr, uint64_t step, int32_t* m) { sample_k_mode(pr, step, m); }
+
 /* S = H^3 - 1 (Eq. (2.6)) with H by direct sum (Eq. (2.7), left side). */
 double orc_S(double alpha, double L)
 {
@@ -361,7 +460,7 @@ typedef struct {
 
 /* Classify candidates (canonical order) into C(i) and S(i), then draw B(i). */
 static void classify_and_sample(const orc_grid* g, int i, const int32_t* cand, int ncand,
-                                int p, uint64_t seed, uint64_t step, atom_lists* al,
+                                int p, int shell_mode, uint64_t seed, uint64_t step, atom_lists* al,
                                 uint64_t* words, uint64_t* ord)
 {
     const uint32_t* si = g->s + 3 * i;
@@ -379,7 +478,12 @@ static void classify_and_sample(const orc_grid* g, int i, const int32_t* cand, i
         al->n_batch = al->n_shell;
     } else {
         shell_words(seed, step, (uint64_t)i, p, words);
-        orc_floyd((uint64_t)al->n_shell, p, words, ord);
+        if (shell_mode == 1) {
+            /* R9: p independent uniform ordinals (with replacement) */
+            for (int k = 0; k < p; ++k) ord[k] = uniform_below(words[k], (uint64_t)al->n_shell);
+        } else {
+            orc_floyd((uint64_t)al->n_shell, p, words, ord);
+        }
         for (int k = 0; k < p; ++k) al->batch[k] = al->shell[ord[k]];
         al->n_batch = p;
     }
@@ -397,6 +501,8 @@ typedef struct {
     double eps_ij[ORC_MAXT * ORC_MAXT];
     double sig_ij[ORC_MAXT * ORC_MAXT];
     double lj_shift[ORC_MAXT * ORC_MAXT];
+    double lj_rc2[ORC_MAXT * ORC_MAXT];   /* squared LJ cutoff (R9)           */
+    int lj_cut[ORC_MAXT * ORC_MAXT];      /* 1: cut at f sigma_ab < r_s (R9)  */
     int ntypes;
 } pair_consts;
 
@@ -414,7 +520,16 @@ static void make_pair_consts(const orc_params* pr, pair_consts* pc)
             double s = 0.5 * (pr->sigma[a] + pr->sigma[b]);    /* Lorentz   */
             pc->eps_ij[a * ORC_MAXT + b] = e;
             pc->sig_ij[a * ORC_MAXT + b] = s;
-            double sr6 = pow(s / pr->r_s, 6.0);
+            /* R9: LJ cutoff min(f sigma_ab, r_s); the shift is U_LJ there */
+            double rc = pr->r_s;
+            int cut = 0;
+            if (pr->lj_rc_factor > 0.0 && pr->lj_rc_factor * s < pr->r_s) {
+                rc = pr->lj_rc_factor * s;
+                cut = 1;
+            }
+            pc->lj_rc2[a * ORC_MAXT + b] = rc * rc;
+            pc->lj_cut[a * ORC_MAXT + b] = cut;
+            double sr6 = pow(s / rc, 6.0);
             pc->lj_shift[a * ORC_MAXT + b] = 4.0 * e * (sr6 * sr6 - sr6);
         }
 }
@@ -443,7 +558,8 @@ static void pair_term(const pair_consts* pc, double qi, double qj, int ti, int t
         s = -qq * (ec / r2 + gauss / r) / r;
         u[0] = qq * ec / r;
         double e = pc->eps_ij[ti * ORC_MAXT + tj];
-        if (e != 0.0) {
+        int in_lj = !pc->lj_cut[ti * ORC_MAXT + tj] || r2 < pc->lj_rc2[ti * ORC_MAXT + tj];
+        if (e != 0.0 && in_lj) {
             double sg = pc->sig_ij[ti * ORC_MAXT + tj];
             double sr2 = sg * sg / r2;
             double sr6 = sr2 * sr2 * sr2;
@@ -563,7 +679,7 @@ int orc_lists(int n, const double* pos, const orc_params* pr, uint64_t step, int
                 candidates_cells(&g, i, gs.reach, &c);
                 cl = cand; ncand = c.count;
             }
-            classify_and_sample(&g, i, cl, ncand, pr->p, pr->seed, step, &al, words, ord);
+            classify_and_sample(&g, i, cl, ncand, pr->p, pr->shell_mode, pr->seed, step, &al, words, ord);
             n_core[i] = al.n_core; n_shell[i] = al.n_shell; n_batch[i] = al.n_batch;
             if (al.overlap) local_status |= 2;
             if (core) {
@@ -696,7 +812,7 @@ int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* typ
         for (int i = 0; i < n; ++i) {
             cand_list c = {0, cand};
             candidates_cells(&g, i, gs.reach, &c);
-            classify_and_sample(&g, i, cand, c.count, pr->p, pr->seed, step, &al, words, ord);
+            classify_and_sample(&g, i, cand, c.count, pr->p, pr->shell_mode, pr->seed, step, &al, words, ord);
             if (al.overlap) local_status |= 2;
             double w_shell = (al.n_shell <= pr->p) ? 1.0 : (double)al.n_shell / (double)pr->p;
             double f[3] = {0, 0, 0}, u[3] = {0, 0, 0}, wv[6] = {0, 0, 0, 0, 0, 0}, fa[3] = {0, 0, 0};
@@ -752,7 +868,7 @@ int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* typ
     double* rho = (double*)malloc(sizeof(double) * 2 * (size_t)pr->P);
     double* Flong = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     double* Flabs = (double*)malloc(sizeof(double) * 3 * (size_t)n);
-    orc_sample_k(pr->seed, step, pr->P, pr->alpha, pr->L, m);
+    sample_k_mode(pr, step, m);
     orc_rho(n, pos, q, pr->L, pr->P, m, rho);
     double Ek, Wk[6];
     rbe_fourier(n, pos, q, pr, m, rho, Flong, Flabs, &Ek, Wk);
@@ -1083,7 +1199,7 @@ int orc_rbe_adjoint(int n, const double* pos, const double* q, const int32_t* ty
         for (int i = 0; i < n; ++i) {
             cand_list c = {0, cand};
             candidates_cells(&g, i, gs.reach, &c);
-            classify_and_sample(&g, i, cand, c.count, pr->p, pr->seed, step, &al, words, ord);
+            classify_and_sample(&g, i, cand, c.count, pr->p, pr->shell_mode, pr->seed, step, &al, words, ord);
             double w_shell = (al.n_shell <= pr->p) ? 1.0 : (double)al.n_shell / (double)pr->p;
             double vt[3] = {0, 0, 0};
             if (gF) for (int a = 0; a < 3; ++a) vt[a] = gF[3 * i + a] - vbar[a];
@@ -1127,7 +1243,8 @@ int orc_rbe_adjoint(int n, const double* pos, const double* q, const int32_t* ty
                         local_status |= 1;
                     }
                     /* LJ pair parameters */
-                    if (!excl) {
+                    int tti = type[i] * ORC_MAXT + type[j];
+                    if (!excl && (!pc.lj_cut[tti] || r2 < pc.lj_rc2[tti])) {
                         int ti = type[i], tj = type[j];
                         double e = pc.eps_ij[ti * ORC_MAXT + tj], sg = pc.sig_ij[ti * ORC_MAXT + tj];
                         double sr = sg / r, sr6 = pow(sr, 6.0), sr12 = sr6 * sr6;
@@ -1135,9 +1252,12 @@ int orc_rbe_adjoint(int n, const double* pos, const double* q, const int32_t* ty
                         double du_de = 4.0 * (sr12 - sr6);
                         double du_ds = 4.0 * e * (12.0 * sr12 - 6.0 * sr6) / sg;
                         if (pc.shift_lj) {
-                            double ss = sg / pc.r_s, ss6 = pow(ss, 6.0), ss12 = ss6 * ss6;
+                            /* shift 4 e ((sg/rc)^12 - (sg/rc)^6): with rc = f sg
+                             * (R9) it does not depend on sg */
+                            double rc = pc.lj_cut[tti] ? sqrt(pc.lj_rc2[tti]) : pc.r_s;
+                            double ss = sg / rc, ss6 = pow(ss, 6.0), ss12 = ss6 * ss6;
                             du_de -= 4.0 * (ss12 - ss6);
-                            du_ds -= 4.0 * e * (12.0 * ss12 - 6.0 * ss6) / sg;
+                            if (!pc.lj_cut[tti]) du_ds -= 4.0 * e * (12.0 * ss12 - 6.0 * ss6) / sg;
                         }
                         double dh_de = -(48.0 * sr12 - 24.0 * sr6) / r2;
                         double dh_ds = -e * (576.0 * sr12 - 144.0 * sr6) / (r2 * sg);
@@ -1158,7 +1278,7 @@ int orc_rbe_adjoint(int n, const double* pos, const double* q, const int32_t* ty
     int32_t* m = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)pr->P);
     double* rho = (double*)malloc(sizeof(double) * 2 * (size_t)pr->P);
     double* tau = (double*)calloc(2 * (size_t)pr->P, sizeof(double));
-    orc_sample_k(pr->seed, step, pr->P, pr->alpha, pr->L, m);
+    sample_k_mode(pr, step, m);
     orc_rho(n, pos, q, pr->L, pr->P, m, rho);
     double L = pr->L, V = L * L * L;
     double S = orc_S(pr->alpha, L);
