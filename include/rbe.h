@@ -236,6 +236,34 @@ int rbe_rho_noalloc(int n, const double* pos, const double* q, double box_L, int
  * idle). */
 void rbe_destroy(rbe_ctx* ctx);
 
+/* Variants of the method (the paper leaves them open; defaults = base method).
+ *
+ * Shell batch (Algorithm 1, shell selection step): RBE_SHELL_FLOYD draws the
+ * min(p, N_S) atoms of B(i) without replacement (Floyd's algorithm over the
+ * shell ordinals); RBE_SHELL_REPLACE draws, when N_S > p, p independent
+ * uniform ordinals (slot k: floor(u_k N_S / 2^64), u_k the slot's Philox
+ * word), weight N_S/p, repeats allowed. */
+#define RBE_SHELL_FLOYD   0
+#define RBE_SHELL_REPLACE 1
+int rbe_set_shell_sampling(rbe_ctx* ctx, int mode);
+
+/* LJ cutoff per pair type: factor f > 0 truncates the LJ term of pair (a, b)
+ * at min(f sigma_ab, r_s), shifted to zero there when rbe_set_lj's
+ * shift_energy is set; f = 2^(1/6) with the shift is the WCA soft sphere of
+ * the paper's primitive-model electrolytes (Sec. 3.1, "shifted-truncated
+ * LJ").  f = 0 (default): LJ to r_s.  Pairs beyond the cutoff keep their
+ * Coulomb term. */
+int rbe_set_lj_cutoff(rbe_ctx* ctx, double factor);
+
+/* k-sample pool (Algorithm 1, pool step; Sec. 2.2): size K > 0 builds, once,
+ * a pool of K wave vectors from one Metropolis-Hastings chain per axis
+ * (target the discrete Gaussian of Eq. (2.8); proposal round(x),
+ * x ~ N(0, alpha L^2 / (2 pi^2)); chain iteration t of axis a uses Philox
+ * block (t, a, 0, 4); burn_in iterations discarded; k = 0 skipped), and each
+ * step's sample l is pool entry floor(u K / 2^64), u word 0 of block
+ * (l, 0, step, 5).  K = 0 (default): fresh exact draws every step. */
+int rbe_set_kpool(rbe_ctx* ctx, int size, int burn_in);
+
 /* Work decomposition of the RBL pair kernel (Sec. 2.3 stencil walk): a work
  * unit is a run of cells along x holding about atoms_per_unit atoms (0: 48;
  * shared memory caps the width); the kernel's grid has

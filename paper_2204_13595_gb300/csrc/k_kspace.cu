@@ -43,13 +43,23 @@ __device__ __forceinline__ int inv_cdf(uint64_t u, const uint64_t* __restrict__ 
 // explicitly (bx, nbx) so that the single-system kernels and the batched ones
 // (one launch over many replicas, at the end of this file) share them.
 __device__ __forceinline__ void sample_body(int bx, int nbx, const RbeConsts& c, uint64_t step,
-                                            const uint64_t* __restrict__ T, int4* __restrict__ km,
-                                            double4_32a* __restrict__ kv, int* __restrict__ status)
+                                            const uint64_t* __restrict__ T, const int4* __restrict__ pool,
+                                            int4* __restrict__ km, double4_32a* __restrict__ kv,
+                                            int* __restrict__ status)
 {
     const double twopi_L = 2.0 * 3.14159265358979323846 / c.L;
     for (int l = bx * TPB + threadIdx.x; l < c.P; l += nbx * TPB) {
         int mx = 1, my = 0, mz = 0;
         bool ok = false;
+        if (c.kpool > 0) {
+            // Algorithm 1: sample l of the step is pool entry floor(u K / 2^64),
+            // u word 0 of the block at counter (l, 0, step, 5)
+            uint64_t w[4];
+            philox4x64_10((uint64_t)l, 0ull, step, 5ull, c.seed, 0ull, w);
+            const int4 e = pool[uniform_below(w[0], (uint32_t)c.kpool)];
+            mx = e.x; my = e.y; mz = e.z;
+            ok = true;
+        }
         for (uint64_t t = 0; t < 1024 && !ok; ++t) {
             uint64_t w[4];
             philox4x64_10((uint64_t)l, t, step, 2ull, c.seed, 0ull, w);
@@ -65,10 +75,48 @@ __device__ __forceinline__ void sample_body(int bx, int nbx, const RbeConsts& c,
 }
 
 __global__ void __launch_bounds__(TPB) k_sample(RbeConsts c, uint64_t step, const uint64_t* __restrict__ T,
-                                                int4* __restrict__ km, double4_32a* __restrict__ kv,
-                                                int* __restrict__ status)
+                                                const int4* __restrict__ pool, int4* __restrict__ km,
+                                                double4_32a* __restrict__ kv, int* __restrict__ status)
 {
-    sample_body(blockIdx.x, gridDim.x, c, step, T, km, kv, status);
+    sample_body(blockIdx.x, gridDim.x, c, step, T, pool, km, kv, status);
+}
+
+// Metropolis-Hastings pool of k samples (Algorithm 1, pool step; Sec. 2.2):
+// per axis an independence chain with target w_m (the discrete Gaussian of
+// Eq. (2.8)) and proposal q_m = P(round(X) = m), X ~ N(0, alpha L^2/(2 pi^2)),
+// both tabulated on the host for |m| <= M; the proposal is drawn by inverse CDF
+// on the thresholds Tq, the move m -> m* accepted when
+// u < (w_m* q_m) / (w_m q_m*), u = (word >> 11) 2^-53.  Iteration t of axis a
+// uses the block at counter (t, a, 0, 4) (word 0 proposal, word 1 acceptance).
+// The chains start at 0; after `burn` iterations each iteration emits
+// (m_x, m_y, m_z) unless it is 0, until K samples.  One thread: a Markov
+// chain is sequential, and the pool is built once per context.
+__global__ void k_kpool_build(uint64_t seed, int M, int K, int burn, const double* __restrict__ w,
+                              const double* __restrict__ q, const uint64_t* __restrict__ Tq, int4* __restrict__ pool,
+                              int* __restrict__ status)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int m[3] = {0, 0, 0};
+    int k = 0;
+    // bounded: far more iterations than K non-zero samples can need
+    const uint64_t tmax = (uint64_t)burn + 64ull * (uint64_t)K + 4096ull;
+    for (uint64_t t = 0; k < K; ++t) {
+        if (t >= tmax) {
+            latch_status(status, RBE_ST_KSAMPLE);
+            break;
+        }
+        for (int a = 0; a < 3; ++a) {
+            uint64_t blk[4];
+            philox4x64_10(t, (uint64_t)a, 0ull, 4ull, seed, 0ull, blk);
+            const int mp = inv_cdf(blk[0], Tq, M);
+            const double u = __dmul_rn((double)(blk[1] >> 11), 1.1102230246251565e-16);
+            const double r = __ddiv_rn(__dmul_rn(w[mp + M], q[m[a] + M]), __dmul_rn(w[m[a] + M], q[mp + M]));
+            if (u < r) m[a] = mp;
+        }
+        if (t < (uint64_t)burn) continue;
+        if (m[0] == 0 && m[1] == 0 && m[2] == 0) continue;
+        pool[k++] = make_int4(m[0], m[1], m[2], 0);
+    }
 }
 
 // rho partial sums: block b owns atoms [b*chunk, min(n,(b+1)*chunk)).
@@ -485,7 +533,7 @@ __global__ void __launch_bounds__(TPB) k_sample_b(const RepDev* __restrict__ R, 
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    sample_body(bx, nbx, d.c, ctl->step, d.kT, d.km, d.kv, d.status);
+    sample_body(bx, nbx, d.c, ctl->step, d.kT, d.kpool, d.km, d.kv, d.status);
 }
 
 template <bool MIXED>
@@ -557,8 +605,14 @@ void launch_ksample(rbe_ctx* ctx, uint64_t step, cudaStream_t st)
 {
     prof_begin(ctx, RBE_K_KSAMPLE, st);
     int g = (ctx->c.P + TPB - 1) / TPB;
-    k_sample<<<g, TPB, 0, st>>>(ctx->c, step, ctx->kT, ctx->km, ctx->kv, ctx->status);
+    k_sample<<<g, TPB, 0, st>>>(ctx->c, step, ctx->kT, ctx->kpool_buf, ctx->km, ctx->kv, ctx->status);
     prof_end(ctx, RBE_K_KSAMPLE, st);
+}
+
+void launch_kpool_build(rbe_ctx* ctx, const double* w, const double* q, const uint64_t* Tq, int M, cudaStream_t st)
+{
+    k_kpool_build<<<1, 32, 0, st>>>(ctx->c.seed, M, ctx->c.kpool, ctx->kpool_burn, w, q, Tq, ctx->kpool_buf,
+                                    ctx->status);
 }
 
 void launch_rho(rbe_ctx* ctx, int n, cudaStream_t st)

@@ -101,7 +101,7 @@ __host__ __device__ inline SmemLayout smem_layout(const RblGeom& g, int nt2, int
     L.cellpos = o;
     o = up16(o + sizeof(int) * (size_t)g.nrows * (size_t)(g.cells_per_row + 1));
     L.lj = o;
-    o = up16(o + sizeof(double) * 11 * (size_t)nt2);
+    o = up16(o + sizeof(double) * 12 * (size_t)nt2);
     L.warps = o;
     L.wbytes = up16(sizeof(uint64_t) * (size_t)p_pad * L.ga + sizeof(int) * (size_t)(core_cap + shell_cap + p_pad));
     L.total = o + L.wbytes * WARPS;
@@ -131,13 +131,6 @@ __device__ __forceinline__ unsigned long long d2_exact(uint4 a, uint4 b)
            (unsigned long long)((long long)dz * dz);
 }
 
-// floor(u * n / 2^64) for n < 2^32: a uniform integer in [0, n) from a 64-bit word.
-__device__ __forceinline__ uint32_t uniform_below(uint64_t u, uint32_t n)
-{
-    uint64_t lo = (uint64_t)(uint32_t)u * n;
-    uint64_t hi = (uint64_t)(uint32_t)(u >> 32) * n;
-    return (uint32_t)((hi + (lo >> 32)) >> 32);
-}
 
 // Classification of one canonical segment [beg, end) of the source array:
 // FP32 distance with exact integer decision inside the rounding bands.
@@ -247,7 +240,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     double* s_sig = s_eps + nt2;
     double* s_dsde = s_sig + nt2;
     double* s_dsds = s_dsde + nt2;
-    double* s_glj = s_dsds + nt2;           // adjoint: [4][nt2] block accumulators
+    double* s_rc2 = s_dsds + nt2;           // squared LJ cutoff per pair type
+    double* s_glj = s_rc2 + nt2;            // adjoint: [4][nt2] block accumulators
     uint64_t* words = reinterpret_cast<uint64_t*>(smem + lay.warps + lay.wbytes * wib);   // [ga][p_pad]
     int* core_buf = reinterpret_cast<int*>(words + (size_t)p_pad * lay.ga);
     int* shell_buf = core_buf + a.core_cap;
@@ -260,6 +254,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
         s_c12[t] = a.lj->c12[ti * RBE_MAXT + tj];
         s_c6[t] = a.lj->c6[ti * RBE_MAXT + tj];
         s_sh[t] = a.lj->shift[ti * RBE_MAXT + tj];
+        s_rc2[t] = a.lj->rc2[ti * RBE_MAXT + tj];
         if (ADJ) {
             s_eps[t] = a.lj->eps[ti * RBE_MAXT + tj];
             s_sig[t] = a.lj->sig[ti * RBE_MAXT + tj];
@@ -506,7 +501,10 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
             const bool sample = nshell > p;
             const int nb = sample ? p : nshell;
             const uint64_t* wa = words + (size_t)aslot * p_pad;
-            if (sample) {
+            if (sample && c.shell_mode == 1) {
+                // with replacement: slot k is ordinal floor(u_k N_S / 2^64)
+                for (int k = lane; k < p; k += 32) sel[k] = (int)uniform_below(wa[k], (uint32_t)nshell);
+            } else if (sample) {
                 if (p <= 32) {
                     // slot k on lane k; the insertions resolved in slot order
                     const uint32_t jk = (uint32_t)(nshell - p + lane);
@@ -598,8 +596,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     gL += w * ke * qj * h * vd;
                     atomicAdd(&a.gq_tr[2 * (size_t)j], 0.5 * w * ke * qi * phi);
                     atomicAdd(&a.gq_tr[2 * (size_t)j + 1], w * ke * qi * h * vd);
-                    if (!ex) {
-                        const int tt = ti.x * c.ntypes + tj.x;
+                    const int tt = ti.x * c.ntypes + tj.x;
+                    if (!ex && r2 < s_rc2[tt]) {
                         const double e = s_eps[tt], sg = s_sig[tt];
                         if (e != 0.0) {
                             const double ir2 = 1.0 / r2;
@@ -652,11 +650,12 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     const float ucoul = qq * ec * rinv;
                     float s = -qq * (ec * rinv + gauss) * rinv * rinv;
                     const int tt = ti.x * c.ntypes + tj.x;
-                    const float c12 = ex ? 0.f : (float)s_c12[tt], c6 = ex ? 0.f : (float)s_c6[tt];
+                    const bool nolj = ex || !(r2 < (float)s_rc2[tt]);
+                    const float c12 = nolj ? 0.f : (float)s_c12[tt], c6 = nolj ? 0.f : (float)s_c6[tt];
                     const float ir2 = rinv * rinv;
                     const float ir6 = ir2 * ir2 * ir2;
                     s -= (12.f * c12 * ir6 - 6.f * c6) * ir6 * ir2;
-                    const float ulj = (c12 * ir6 - c6) * ir6 - (ex ? 0.f : (float)s_sh[tt]);
+                    const float ulj = (c12 * ir6 - c6) * ir6 - (nolj ? 0.f : (float)s_sh[tt]);
                     const float gx = w * s * dx, gy = w * s * dy, gz = w * s * dz;
                     ff[0] += gx; ff[1] += gy; ff[2] += gz;
                     facc_e[0] += ex ? 0.f : w * ucoul;
@@ -717,11 +716,12 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     const double ucoul = qq * ec * rinv;
                     double s = -qq * (ec * rinv + gauss) * rinv * rinv;
                     const int tt = ti.x * c.ntypes + tj.x;
-                    const double c12 = ex ? 0.0 : s_c12[tt], c6 = ex ? 0.0 : s_c6[tt];
+                    const bool nolj = ex || !(r2 < s_rc2[tt]);
+                    const double c12 = nolj ? 0.0 : s_c12[tt], c6 = nolj ? 0.0 : s_c6[tt];
                     const double ir2 = rinv * rinv;
                     const double ir6 = ir2 * ir2 * ir2;
                     s -= (12.0 * c12 * ir6 - 6.0 * c6) * ir6 * ir2;
-                    const double ulj = (c12 * ir6 - c6) * ir6 - (ex ? 0.0 : s_sh[tt]);
+                    const double ulj = (c12 * ir6 - c6) * ir6 - (nolj ? 0.0 : s_sh[tt]);
                     const double gx = w * s * dx, gy = w * s * dy, gz = w * s * dz;
                     fi[0] += gx; fi[1] += gy; fi[2] += gz;
                     acc_e[0] += ex ? 0.0 : w * ucoul;

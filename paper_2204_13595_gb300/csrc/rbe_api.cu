@@ -75,6 +75,33 @@ double k_thresholds(double alpha, double L, int M, uint64_t* T)
     return H;
 }
 
+// Tables of the Metropolis-Hastings k pool (Algorithm 1, pool step; Sec. 2.2
+// sampling text): target w_m = exp(-pi^2 m^2/(alpha L^2)) and proposal
+// q_m = P(round(X) = m), X ~ N(0, s^2), s^2 = alpha L^2/(2 pi^2), on |m| <= M,
+// with the 64-bit inverse-CDF thresholds of q (normalised on |m| <= M).
+void mh_tables(double alpha, double L, int M, double* w, double* q, uint64_t* Tq)
+{
+    const double aL2 = alpha * L * L;
+    const double c = PI * PI / aL2;
+    const double sd = sqrt(aL2 / (2.0 * PI * PI));
+    const double sq2 = sd * sqrt(2.0);
+    double Q = 0.0;
+    for (int m = -M; m <= M; ++m) {
+        w[m + M] = exp(-c * (double)m * (double)m);
+        const double am = fabs((double)m);
+        const double lo = (am - 0.5) / sq2, hi = (am + 0.5) / sq2;
+        const double qm = (m == 0) ? erf(0.5 / sq2) : 0.5 * (erfc(lo) - erfc(hi));
+        q[m + M] = qm;
+        Q += qm;
+    }
+    double acc = 0.0;
+    for (int m = -M; m <= M; ++m) {
+        acc += q[m + M];
+        const double v = (acc / Q) * 18446744073709551616.0;
+        Tq[m + M] = (v >= 18446744073709551616.0) ? UINT64_MAX : (uint64_t)v;
+    }
+}
+
 uint64_t radius2_fixed(double r, double L)
 {
     double invL = 1.0 / L;
@@ -95,7 +122,7 @@ void refresh_consts(rbe_ctx* ctx)
 
 void free_dev(rbe_ctx* ctx)
 {
-    void* ptrs[] = {ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
+    void* ptrs[] = {ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
                     ctx->F_real, ctx->F_bond, ctx->part_rbl, ctx->part_q, ctx->part_bond, ctx->kT, ctx->km, ctx->kv,
                     ctx->rho_part, ctx->rho, ctx->totals, ctx->status, ctx->lj, ctx->dbg_ncore, ctx->dbg_nshell,
                     ctx->dbg_core, ctx->dbg_batch, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
@@ -111,7 +138,7 @@ void free_dev(rbe_ctx* ctx)
     ctx->dbg_nshell = nullptr; ctx->dbg_core = nullptr; ctx->dbg_batch = nullptr; ctx->h_pos = nullptr;
     ctx->h_q = nullptr; ctx->h_type = nullptr; ctx->h_mol = nullptr; ctx->h_F = nullptr; ctx->ke_part = nullptr;
     ctx->vs = nullptr; ctx->gq_own = nullptr; ctx->gq_tr = nullptr; ctx->part_lj = nullptr; ctx->part_v = nullptr;
-    ctx->tau_part = nullptr; ctx->tau = nullptr;
+    ctx->tau_part = nullptr; ctx->tau = nullptr; ctx->kpool_buf = nullptr; ctx->kpool_dirty = 1;
     ctx->n_cap = 0; ctx->dbg_n_cap = 0; ctx->h_cap = 0;
     for (int k = 0; k < 20; ++k) ctx->cap_atoms[k] = 0;
     for (int k = 0; k < 8; ++k) ctx->cap_adj[k] = 0;
@@ -240,15 +267,47 @@ int ensure(rbe_ctx* ctx, int n)
                 double s6 = s * s * s * s * s * s;
                 h.c12[a * RBE_MAXT + b] = 4.0 * e * s6 * s6;
                 h.c6[a * RBE_MAXT + b] = 4.0 * e * s6;
-                double sr6 = pow(s / ctx->c.r_s, 6.0);
+                // LJ cutoff of the pair: min(f sigma_ab, r_s) (f = 2^(1/6) with
+                // the shift: the WCA soft sphere); beyond r_s no pair is summed
+                double rc = ctx->c.r_s;
+                bool cut = false;
+                if (ctx->lj_rc_factor > 0.0 && ctx->lj_rc_factor * s < ctx->c.r_s) {
+                    rc = ctx->lj_rc_factor * s;
+                    cut = true;
+                }
+                h.rc2[a * RBE_MAXT + b] = cut ? rc * rc : 1.0e300;
+                double sr6 = pow(s / rc, 6.0);
                 h.shift[a * RBE_MAXT + b] = ctx->c.shift_lj ? 4.0 * e * (sr6 * sr6 - sr6) : 0.0;
                 h.eps[a * RBE_MAXT + b] = e;
                 h.sig[a * RBE_MAXT + b] = s;
                 h.dshift_de[a * RBE_MAXT + b] = ctx->c.shift_lj ? 4.0 * (sr6 * sr6 - sr6) : 0.0;
-                h.dshift_ds[a * RBE_MAXT + b] = ctx->c.shift_lj ? 4.0 * e * (12.0 * sr6 * sr6 - 6.0 * sr6) / s : 0.0;
+                // with rc = f sigma the shift does not depend on sigma
+                h.dshift_ds[a * RBE_MAXT + b] =
+                    (ctx->c.shift_lj && !cut) ? 4.0 * e * (12.0 * sr6 * sr6 - 6.0 * sr6) / s : 0.0;
             }
         CUDA_TRY(ctx, cudaMemcpy(ctx->lj, &h, sizeof(h), cudaMemcpyHostToDevice));
         ctx->lj_dirty = 0;
+    }
+    if (ctx->c.kpool > 0 && (ctx->kpool_dirty || !ctx->kpool_buf)) {
+        // k pool: tables on the host, the chains on the device (set-up, once)
+        const int M = ctx->c.M;
+        std::vector<double> w(2 * M + 1), q(2 * M + 1);
+        std::vector<uint64_t> Tq(2 * M + 1);
+        mh_tables(ctx->c.alpha, ctx->c.L, M, w.data(), q.data(), Tq.data());
+        double *dw = nullptr, *dq = nullptr;
+        uint64_t* dT = nullptr;
+        if ((rc = dev_alloc(ctx, &ctx->kpool_buf, (size_t)ctx->c.kpool))) return rc;
+        if ((rc = dev_alloc(ctx, &dw, w.size()))) return rc;
+        if ((rc = dev_alloc(ctx, &dq, q.size()))) { cudaFree(dw); return rc; }
+        if ((rc = dev_alloc(ctx, &dT, Tq.size()))) { cudaFree(dw); cudaFree(dq); return rc; }
+        cudaMemcpy(dw, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(dq, q.data(), sizeof(double) * q.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(dT, Tq.data(), sizeof(uint64_t) * Tq.size(), cudaMemcpyHostToDevice);
+        launch_kpool_build(ctx, dw, dq, dT, M, 0);
+        cudaError_t e = cudaDeviceSynchronize();
+        cudaFree(dw); cudaFree(dq); cudaFree(dT);
+        if (e != cudaSuccess) return set_err(ctx, RBE_ECUDA, "k pool build failed: %s", cudaGetErrorString(e));
+        ctx->kpool_dirty = 0;
     }
     if (n != ctx->last_n || ctx->precision != ctx->last_precision) {
         auto_caps(ctx, n);
@@ -490,6 +549,30 @@ int rbe_set_capacity(rbe_ctx* ctx, int core_cap, int shell_cap)
     ctx->user_core_cap = core_cap;
     ctx->user_shell_cap = shell_cap;
     ctx->last_n = -1;
+    return RBE_OK;
+}
+
+int rbe_set_shell_sampling(rbe_ctx* ctx, int mode)
+{
+    if (!ctx || (mode != RBE_SHELL_FLOYD && mode != RBE_SHELL_REPLACE)) return RBE_EINVAL;
+    ctx->c.shell_mode = mode;
+    return RBE_OK;
+}
+
+int rbe_set_lj_cutoff(rbe_ctx* ctx, double factor)
+{
+    if (!ctx || !(factor >= 0.0) || !isfinite(factor)) return RBE_EINVAL;
+    ctx->lj_rc_factor = factor;
+    ctx->lj_dirty = 1;
+    return RBE_OK;
+}
+
+int rbe_set_kpool(rbe_ctx* ctx, int size, int burn_in)
+{
+    if (!ctx || size < 0 || burn_in < 0) return RBE_EINVAL;
+    ctx->c.kpool = size;
+    ctx->kpool_burn = burn_in;
+    ctx->kpool_dirty = 1;
     return RBE_OK;
 }
 

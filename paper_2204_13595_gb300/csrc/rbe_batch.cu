@@ -180,6 +180,7 @@ int build_plan(rbe_batch* b)
         d.part_q = ctx->part_q; d.part_rbl = ctx->part_rbl; d.part_bond = ctx->part_bond; d.ke_part = ctx->ke_part;
         d.kT = ctx->kT; d.km = ctx->km; d.kv = ctx->kv; d.rho_part = ctx->rho_part; d.rho = ctx->rho;
         d.totals = ctx->totals; d.F_real = ctx->F_real; d.F_bond = ctx->F_bond; d.status = ctx->status;
+        d.kpool = ctx->kpool_buf;
         rbl_fill_args(ctx, n, b->rbl_args.data() + ab * r);
 
         cnt[BK_CELLS][r] = ceil_div(ctx->ncells + 1, 256);

@@ -43,6 +43,8 @@ struct RbeConsts {
     int M;                // k truncation
     int ntypes;
     int shift_lj;
+    int shell_mode;       // 0: batch without replacement (Floyd), 1: with replacement
+    int kpool;            // 0: fresh k draws each step, K > 0: draws from a pool of K
 };
 
 // Geometry of the RBL kernel's work units and of its FP32 classification
@@ -69,6 +71,7 @@ struct RbeLJ {
     double sig[RBE_MAXT * RBE_MAXT];
     double dshift_de[RBE_MAXT * RBE_MAXT];
     double dshift_ds[RBE_MAXT * RBE_MAXT];
+    double rc2[RBE_MAXT * RBE_MAXT];      // squared LJ cutoff of the pair (huge: no cut below r_s)
 };
 
 struct rbe_ctx {
@@ -79,6 +82,10 @@ struct rbe_ctx {
     int core_cap, shell_cap;
     int profiling;
     double eps[RBE_MAXT], sigma[RBE_MAXT];
+    double lj_rc_factor;  // LJ of pair (a, b) cut at min(f sigma_ab, r_s) when f > 0
+    int kpool_burn;       // burn-in of the k pool's Metropolis-Hastings chains
+    int kpool_dirty;
+    int4* kpool_buf;      // [kpool] pool of k samples (device)
     // water bonds
     int n_wmol;
     double kb, r0, kth, th0;
@@ -186,6 +193,7 @@ struct RepDev {
     double* F_real;
     double* F_bond;
     int* status;
+    const int4* kpool;
 };
 
 // Device control block of a batch: the MD step the batched kernels use, the
@@ -280,6 +288,14 @@ __device__ __forceinline__ T warp_sum(T v)
 
 __device__ __forceinline__ void latch_status(int* status, int bit) { atomicOr(status, bit); }
 
+// floor(u * n / 2^64) for n < 2^32: a uniform integer in [0, n) from a 64-bit word.
+__device__ __forceinline__ uint32_t uniform_below(uint64_t u, uint32_t n)
+{
+    uint64_t lo = (uint64_t)(uint32_t)u * n;
+    uint64_t hi = (uint64_t)(uint32_t)(u >> 32) * n;
+    return (uint32_t)((hi + (lo >> 32)) >> 32);
+}
+
 // ---------------------------------------------------------------------------
 // kernel launchers (each returns the number of kernels enqueued)
 // ---------------------------------------------------------------------------
@@ -299,6 +315,8 @@ void launch_adj_prep(rbe_ctx* ctx, int n, const double* gF, cudaStream_t st);
 void launch_adj_final(rbe_ctx* ctx, int n, double* dEdq, double* dLdq, cudaStream_t st);
 // Fourier part and finalisation (k_kspace.cu)
 void launch_ksample(rbe_ctx* ctx, uint64_t step, cudaStream_t st);
+// Metropolis-Hastings pool of k samples from host-made tables (k_kspace.cu)
+void launch_kpool_build(rbe_ctx* ctx, const double* w, const double* q, const uint64_t* Tq, int M, cudaStream_t st);
 void launch_rho(rbe_ctx* ctx, int n, cudaStream_t st);
 void launch_bonded(rbe_ctx* ctx, int n, const double* pos, cudaStream_t st);
 void launch_finalize(rbe_ctx* ctx, int n, cudaStream_t st);

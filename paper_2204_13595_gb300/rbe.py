@@ -26,7 +26,10 @@ EXPORTS = ["rbe_create", "rbe_set_coulomb", "rbe_set_lj", "rbe_set_precision", "
            "rbe_get_kspace", "rbe_get_info", "rbe_set_profiling", "rbe_get_profile", "rbe_last_error",
            "rbe_destroy", "rbe_rho_noalloc", "rbe_adjoint", "rbe_set_rbl_tiling", "rbe_batch_create",
            "rbe_batch_bind", "rbe_batch_forces", "rbe_batch_step", "rbe_batch_autotune", "rbe_batch_info",
-           "rbe_batch_sync_status", "rbe_batch_last_error", "rbe_batch_destroy"]
+           "rbe_batch_sync_status", "rbe_batch_last_error", "rbe_batch_destroy", "rbe_set_shell_sampling",
+           "rbe_set_lj_cutoff", "rbe_set_kpool"]
+SHELL_FLOYD, SHELL_REPLACE = 0, 1
+WCA_FACTOR = 2.0 ** (1.0 / 6.0)
 ELIMIT = -8
 NOALLOC_BLOCKS, NOALLOC_PMAX = 256, 512
 
@@ -64,6 +67,9 @@ def load(path: str = LIB_PATH):
     L.rbe_rho_noalloc.argtypes = [i, vp, vp, d, i, vp, vp, vp]
     L.rbe_adjoint.argtypes = [vp, u64, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.rbe_set_rbl_tiling.argtypes = [vp, i, i]
+    L.rbe_set_shell_sampling.argtypes = [vp, i]
+    L.rbe_set_lj_cutoff.argtypes = [vp, d]
+    L.rbe_set_kpool.argtypes = [vp, i, i]
     L.rbe_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
     L.rbe_batch_bind.argtypes = [vp, ctypes.POINTER(i)] + [ctypes.POINTER(vp)] * 7 + [ctypes.POINTER(d)] * 2
     L.rbe_batch_forces.argtypes = [vp, u64, vp, vp]
@@ -153,6 +159,15 @@ class Context:
 
     def set_capacity(self, core, shell):
         self._check(self.L.rbe_set_capacity(self.h, core, shell))
+
+    def set_shell_sampling(self, mode):
+        self._check(self.L.rbe_set_shell_sampling(self.h, int(mode)))
+
+    def set_lj_cutoff(self, factor):
+        self._check(self.L.rbe_set_lj_cutoff(self.h, float(factor)))
+
+    def set_kpool(self, size, burn_in=0):
+        self._check(self.L.rbe_set_kpool(self.h, int(size), int(burn_in)))
 
     def set_rbl_tiling(self, atoms_per_unit=0, units_per_slot=0):
         self._check(self.L.rbe_set_rbl_tiling(self.h, int(atoms_per_unit), int(units_per_slot)))
