@@ -264,6 +264,18 @@ int rbe_set_lj_cutoff(rbe_ctx* ctx, double factor);
  * (l, 0, step, 5).  K = 0 (default): fresh exact draws every step. */
 int rbe_set_kpool(rbe_ctx* ctx, int size, int burn_in);
 
+/* Langevin thermostat for rbe_step and rbe_batch_step (Sec. 3.1 runs its
+ * electrolytes with a Langevin thermostat of relaxation time tau inside
+ * velocity Verlet).  With tau > 0, every force evaluation at step s adds
+ *   F^L_i = -(m_i / (accel tau)) v_i + sqrt(24 m_i kT / (accel tau dt)) (u - 1/2)
+ * per component, v_i the velocity after the first half kick and u uniform in
+ * [0, 1) from word a of the Philox block at counter (i, 0, s, 3) (i the
+ * caller's atom index): friction plus a uniform random force of variance
+ * 2 m kT / (accel tau dt); the next step's first half kick uses the same F^L.
+ * kT is in the caller's energy units.  tau <= 0 (default) turns it off (NVE).
+ * F returned by rbe_step stays the conservative force. */
+int rbe_set_langevin(rbe_ctx* ctx, double kT, double tau);
+
 /* Work decomposition of the RBL pair kernel (Sec. 2.3 stencil walk): a work
  * unit is a run of cells along x holding about atoms_per_unit atoms (0: 48;
  * shared memory caps the width); the kernel's grid has

@@ -74,14 +74,18 @@ class Params(ctypes.Structure):
         ("lj_rc_factor", ctypes.c_double),
         ("kpool", ctypes.c_int),
         ("kpool_burn", ctypes.c_int),
+        ("lang_kT", ctypes.c_double),
+        ("lang_tau", ctypes.c_double),
     ]
 
 
 def make_params(L, alpha, r_c, r_s, p, P, seed, k_e=1.0, eps=(0.0,), sigma=(1.0,), shift_lj=0, shell_mode=0,
-                lj_rc_factor=0.0, kpool=0, kpool_burn=0):
+                lj_rc_factor=0.0, kpool=0, kpool_burn=0, lang_kT=0.0, lang_tau=0.0):
     """Parameters of the estimator; shell_mode, lj_rc_factor, kpool and
-    kpool_burn select the variants of reading R9 (defaults: the base method)."""
+    kpool_burn select the variants of reading R9, lang_kT and lang_tau the
+    Langevin thermostat of R10 used by vv_run (defaults: the base method)."""
     pr = Params()
+    pr.lang_kT, pr.lang_tau = float(lang_kT), float(lang_tau)
     pr.shell_mode, pr.lj_rc_factor = int(shell_mode), float(lj_rc_factor)
     pr.kpool, pr.kpool_burn = int(kpool), int(kpool_burn)
     pr.L, pr.alpha, pr.r_c, pr.r_s, pr.k_e = float(L), float(alpha), float(r_c), float(r_s), float(k_e)

@@ -54,6 +54,15 @@
  *      (proposal round(x), x ~ N(0, alpha L^2 / (2 pi^2)), Sec. 2.2), and
  *      sample l of a step is pool entry floor(u K / 2^64), u word 0 of the
  *      block at counter (l, 0, step, 5).
+ *  R10 Langevin thermostat (Sec. 3.1 runs the electrolytes with a Langevin
+ *      thermostat of relaxation time tau inside velocity Verlet; the form is
+ *      not given): with force-to-acceleration factor accel, each force
+ *      evaluation at step s adds F^L_i = -(m_i / (accel tau)) v_i
+ *      + sqrt(24 m_i kT / (accel tau dt)) (u - 1/2) per component, v_i the
+ *      velocity at that moment (after the first half kick), u = (w >> 11)
+ *      2^-53 from word a of the Philox block at counter (i, 0, s, 3): a
+ *      uniform random force of the variance 2 m kT / (accel tau dt) of the
+ *      Euler-Maruyama step; the first half kick of the next step uses it too.
  *  R8  Energy estimator: E_real = 1/2 sum_i [sum_C u_ij + w_i sum_B u_ij];
  *      E_k = (S/P) sum_l (2 pi k_e / (V k_l^2)) |rho_l|^2;
  *      E_self = -k_e sqrt(alpha/pi) sum q^2  (Eq. (2.3) terms, reweighted).
@@ -88,6 +97,8 @@ typedef struct orc_params {
     double lj_rc_factor;     /* R9: 0 LJ to r_s, f > 0 cut at f sigma_ab  */
     int kpool;               /* R9: 0 fresh draws, K > 0 MH pool of K     */
     int kpool_burn;          /* R9: burn-in iterations of the MH chains   */
+    double lang_kT;          /* R10: thermostat kT (energy units)         */
+    double lang_tau;         /* R10: relaxation time; <= 0 thermostat off */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -1114,6 +1125,28 @@ double orc_water_bonded(int nmol, int first, const double* pos, double L, double
  * F holds the forces at (pos, step0) on entry and at the final positions on
  * exit.  etrace[2*k] = potential (sum of E[0..5]), etrace[2*k+1] = kinetic
  * after step k.  Water bonds are applied when nmol_w > 0 (atoms 0..3*nmol_w-1). */
+/* Langevin force of R10 at step s from the current velocities (FL = 0 when
+ * the thermostat is off). */
+static void langevin_force(int n, const double* vel, const double* mass, const orc_params* pr, uint64_t s,
+                           double dt, double accel, double* FL)
+{
+    if (!(pr->lang_tau > 0.0)) {
+        for (int i = 0; i < 3 * n; ++i) FL[i] = 0.0;
+        return;
+    }
+    double c1 = accel * pr->lang_tau;                   /* m / c1: friction coefficient */
+    double c2 = 24.0 * pr->lang_kT / (c1 * dt);         /* sqrt(m c2): noise amplitude  */
+    for (int i = 0; i < n; ++i) {
+        uint64_t w[4];
+        rng_block(pr->seed, (uint64_t)i, 0, s, 3, w);
+        double amp = sqrt(mass[i] * c2);
+        for (int a = 0; a < 3; ++a) {
+            double u = (double)(w[a] >> 11) * 1.1102230246251565e-16;
+            FL[3 * i + a] = -(mass[i] / c1) * vel[3 * i + a] + amp * (u - 0.5);
+        }
+    }
+}
+
 int orc_vv_run(int n, double* pos, double* vel, const double* mass, const double* q,
                const int32_t* type, const int32_t* mol, const orc_params* pr,
                uint64_t step0, int nsteps, double dt, double accel,
@@ -1122,16 +1155,21 @@ int orc_vv_run(int n, double* pos, double* vel, const double* mass, const double
 {
     double E[6], W[6];
     int status = 0;
+    double* FL = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    langevin_force(n, vel, mass, pr, step0, dt, accel, FL);
     for (int k = 0; k < nsteps; ++k) {
         for (int i = 0; i < n; ++i)
-            for (int a = 0; a < 3; ++a) vel[3 * i + a] += 0.5 * dt * accel * F[3 * i + a] / mass[i];
+            for (int a = 0; a < 3; ++a)
+                vel[3 * i + a] += 0.5 * dt * accel * (F[3 * i + a] + FL[3 * i + a]) / mass[i];
         for (int i = 0; i < n; ++i)
             for (int a = 0; a < 3; ++a) pos[3 * i + a] += dt * vel[3 * i + a];
         status |= orc_rbe_forces(n, pos, q, type, mol, pr, step0 + (uint64_t)k + 1, F, NULL, NULL, E, W,
                                  NULL, NULL, NULL, NULL);
         if (nmol_w > 0) E[5] = orc_water_bonded(nmol_w, 0, pos, pr->L, kb, r0, kth, th0, F);
+        langevin_force(n, vel, mass, pr, step0 + (uint64_t)k + 1, dt, accel, FL);
         for (int i = 0; i < n; ++i)
-            for (int a = 0; a < 3; ++a) vel[3 * i + a] += 0.5 * dt * accel * F[3 * i + a] / mass[i];
+            for (int a = 0; a < 3; ++a)
+                vel[3 * i + a] += 0.5 * dt * accel * (F[3 * i + a] + FL[3 * i + a]) / mass[i];
         if (etrace) {
             double ke = 0.0;
             for (int i = 0; i < n; ++i)
@@ -1140,6 +1178,7 @@ int orc_vv_run(int n, double* pos, double* vel, const double* mass, const double
             etrace[2 * k + 1] = ke / accel;
         }
     }
+    free(FL);
     return status;
 }
 

@@ -449,25 +449,59 @@ __global__ void __launch_bounds__(TPB) k_kforce(int n, RbeConsts c, const uint4*
     kforce_body<MIXED>(blockIdx.x, n, c, s4, p4, perm, km, kv, rho, F_real, totals, F_bond, n_bonded_atoms, F);
 }
 
+// Half kick v += (dt/2) accel (F + F^L) / m (F^L the Langevin force, or none)
+// and, with drift, x += dt v.
 __device__ __forceinline__ void vv_body(int bx, int n, double* __restrict__ pos, double* __restrict__ vel,
-                                        const double* __restrict__ mass, const double* __restrict__ F, double hdta,
-                                        double dt, int drift)
+                                        const double* __restrict__ mass, const double* __restrict__ F,
+                                        const double* __restrict__ FL, double hdta, double dt, int drift)
 {
     int i = bx * TPB + threadIdx.x;
     if (i >= n) return;
     double m = mass[i];
     for (int a = 0; a < 3; ++a) {
-        double v = __dadd_rn(vel[3 * i + a], __ddiv_rn(__dmul_rn(hdta, F[3 * i + a]), m));
+        const double f = FL ? __dadd_rn(F[3 * i + a], FL[3 * i + a]) : F[3 * i + a];
+        double v = __dadd_rn(vel[3 * i + a], __ddiv_rn(__dmul_rn(hdta, f), m));
         vel[3 * i + a] = v;
         if (drift) pos[3 * i + a] = __dadd_rn(pos[3 * i + a], __dmul_rn(dt, v));
     }
 }
 
 __global__ void __launch_bounds__(TPB) k_vv(int n, double* __restrict__ pos, double* __restrict__ vel,
-                                            const double* __restrict__ mass, const double* __restrict__ F, double hdta,
-                                            double dt, int drift)
+                                            const double* __restrict__ mass, const double* __restrict__ F,
+                                            const double* __restrict__ FL, double hdta, double dt, int drift)
 {
-    vv_body(blockIdx.x, n, pos, vel, mass, F, hdta, dt, drift);
+    vv_body(blockIdx.x, n, pos, vel, mass, F, FL, hdta, dt, drift);
+}
+
+// Langevin thermostat (Sec. 3.1 runs its electrolytes with one, relaxation
+// time tau, inside velocity Verlet): at the force evaluation of step s,
+//   F^L_i = -(m_i / c1) v_i + sqrt(m_i c2) (u - 1/2),  c1 = accel tau,
+//   c2 = 24 kT / (c1 dt),
+// a uniform random force of variance 2 m kT / (accel tau dt) per component
+// (the Euler-Maruyama impulse), u = (w >> 11) 2^-53 from word a of the Philox
+// block at counter (i, 0, s, 3), i the caller's atom index.
+__device__ __forceinline__ void langevin_body(int bx, int n, const double* __restrict__ vel,
+                                              const double* __restrict__ mass, uint64_t seed, uint64_t s, double c1,
+                                              double c2, double* __restrict__ FL)
+{
+    const int i = bx * TPB + threadIdx.x;
+    if (i >= n) return;
+    uint64_t w[4];
+    philox4x64_10((uint64_t)i, 0ull, s, 3ull, seed, 0ull, w);
+    const double m = mass[i];
+    const double amp = __dsqrt_rn(__dmul_rn(m, c2));
+    const double fr = __ddiv_rn(m, c1);
+    for (int a = 0; a < 3; ++a) {
+        const double u = __dmul_rn((double)(w[a] >> 11), 1.1102230246251565e-16);
+        FL[3 * i + a] = __dadd_rn(__dmul_rn(-fr, vel[3 * i + a]), __dmul_rn(amp, __dsub_rn(u, 0.5)));
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_langevin(int n, const double* __restrict__ vel,
+                                                  const double* __restrict__ mass, uint64_t seed, uint64_t s,
+                                                  double c1, double c2, double* __restrict__ FL)
+{
+    langevin_body(blockIdx.x, n, vel, mass, seed, s, c1, c2, FL);
 }
 
 __device__ __forceinline__ void ke_body(int bx, int nbx, int n, const double* __restrict__ vel,
@@ -579,7 +613,16 @@ __global__ void __launch_bounds__(TPB) k_vv_b(const RepDev* __restrict__ R, cons
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    vv_body(bx, d.n, d.pos, d.vel, d.mass, d.F, 0.5 * d.dt * d.accel, d.dt, drift);
+    vv_body(bx, d.n, d.pos, d.vel, d.mass, d.F, d.FL, 0.5 * d.dt * d.accel, d.dt, drift);
+}
+
+__global__ void __launch_bounds__(TPB) k_langevin_b(const RepDev* __restrict__ R, const int* __restrict__ off,
+                                                    int nrep, const BatchCtl* __restrict__ ctl)
+{
+    int bx, nbx;
+    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
+    if (!d.FL) return;
+    langevin_body(bx, d.n, d.vel, d.mass, d.c.seed, ctl->step, d.lang_c1, d.lang_c2, d.FL);
 }
 
 __global__ void __launch_bounds__(TPB) k_ke_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
@@ -663,11 +706,21 @@ void launch_kforce(rbe_ctx* ctx, int n, double* F, cudaStream_t st)
     prof_end(ctx, RBE_K_KFORCE, st);
 }
 
-void launch_vv_kick_drift(rbe_ctx* ctx, int n, double* pos, double* vel, const double* mass, const double* F, double dt,
-                          double accel, int drift, cudaStream_t st)
+void launch_vv_kick_drift(rbe_ctx* ctx, int n, double* pos, double* vel, const double* mass, const double* F,
+                          const double* FL, double dt, double accel, int drift, cudaStream_t st)
 {
     prof_begin(ctx, RBE_K_VV, st);
-    k_vv<<<(n + TPB - 1) / TPB, TPB, 0, st>>>(n, pos, vel, mass, F, 0.5 * dt * accel, dt, drift);
+    k_vv<<<(n + TPB - 1) / TPB, TPB, 0, st>>>(n, pos, vel, mass, F, FL, 0.5 * dt * accel, dt, drift);
+    prof_end(ctx, RBE_K_VV, st);
+}
+
+void launch_langevin(rbe_ctx* ctx, int n, const double* vel, const double* mass, uint64_t s, double dt, double accel,
+                     cudaStream_t st)
+{
+    const double c1 = accel * ctx->lang_tau;
+    const double c2 = 24.0 * ctx->lang_kT / (c1 * dt);
+    prof_begin(ctx, RBE_K_VV, st);
+    k_langevin<<<(n + TPB - 1) / TPB, TPB, 0, st>>>(n, vel, mass, ctx->c.seed, s, c1, c2, ctx->F_lang);
     prof_end(ctx, RBE_K_VV, st);
 }
 
@@ -713,6 +766,11 @@ void launch_kspace_post_batch(const BatchPlan& bp, cudaStream_t st)
 void launch_vv_batch(const BatchPlan& bp, int drift, cudaStream_t st)
 {
     k_vv_b<<<bp.total[BK_ATOMS], TPB, 0, st>>>(bp.rep, bp.off[BK_ATOMS], bp.nrep, drift);
+}
+
+void launch_langevin_batch(const BatchPlan& bp, cudaStream_t st)
+{
+    k_langevin_b<<<bp.total[BK_ATOMS], TPB, 0, st>>>(bp.rep, bp.off[BK_ATOMS], bp.nrep, bp.ctl);
 }
 
 void launch_ke_trace_batch(const BatchPlan& bp, cudaStream_t st)

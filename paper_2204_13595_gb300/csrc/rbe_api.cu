@@ -122,7 +122,7 @@ void refresh_consts(rbe_ctx* ctx)
 
 void free_dev(rbe_ctx* ctx)
 {
-    void* ptrs[] = {ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
+    void* ptrs[] = {ctx->F_lang, ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
                     ctx->F_real, ctx->F_bond, ctx->part_rbl, ctx->part_q, ctx->part_bond, ctx->kT, ctx->km, ctx->kv,
                     ctx->rho_part, ctx->rho, ctx->totals, ctx->status, ctx->lj, ctx->dbg_ncore, ctx->dbg_nshell,
                     ctx->dbg_core, ctx->dbg_batch, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
@@ -139,6 +139,7 @@ void free_dev(rbe_ctx* ctx)
     ctx->h_q = nullptr; ctx->h_type = nullptr; ctx->h_mol = nullptr; ctx->h_F = nullptr; ctx->ke_part = nullptr;
     ctx->vs = nullptr; ctx->gq_own = nullptr; ctx->gq_tr = nullptr; ctx->part_lj = nullptr; ctx->part_v = nullptr;
     ctx->tau_part = nullptr; ctx->tau = nullptr; ctx->kpool_buf = nullptr; ctx->kpool_dirty = 1;
+    ctx->F_lang = nullptr; ctx->F_lang_cap = 0;
     ctx->n_cap = 0; ctx->dbg_n_cap = 0; ctx->h_cap = 0;
     for (int k = 0; k < 20; ++k) ctx->cap_atoms[k] = 0;
     for (int k = 0; k < 8; ++k) ctx->cap_adj[k] = 0;
@@ -387,6 +388,8 @@ int ctx_prepare(rbe_ctx* ctx, int n)
     return ensure(ctx, n);
 }
 
+int ctx_grow_lang(rbe_ctx* ctx, int n) { return grow(ctx, &ctx->F_lang, &ctx->F_lang_cap, 3 * (size_t)n); }
+
 namespace {
 
 int forces_device(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const double* q, const int32_t* type,
@@ -576,6 +579,14 @@ int rbe_set_kpool(rbe_ctx* ctx, int size, int burn_in)
     return RBE_OK;
 }
 
+int rbe_set_langevin(rbe_ctx* ctx, double kT, double tau)
+{
+    if (!ctx || !isfinite(kT) || !isfinite(tau) || kT < 0.0) return RBE_EINVAL;
+    ctx->lang_kT = kT;
+    ctx->lang_tau = tau > 0.0 ? tau : 0.0;
+    return RBE_OK;
+}
+
 int rbe_set_rbl_tiling(rbe_ctx* ctx, int atoms_per_unit, int units_per_slot)
 {
     if (!ctx || atoms_per_unit < 0 || units_per_slot < 0 || atoms_per_unit > 4096) return RBE_EINVAL;
@@ -656,11 +667,20 @@ int rbe_step(rbe_ctx* ctx, uint64_t step0, int nsteps, double dt, double accel, 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int rc = ensure(ctx, n);
     if (rc) return rc;
+    // Langevin thermostat: F^L from the entry velocities at step0, then after
+    // every force evaluation from the half-kicked velocities
+    const bool lang = ctx->lang_tau > 0.0;
+    if (lang) {
+        if ((rc = grow(ctx, &ctx->F_lang, &ctx->F_lang_cap, 3 * (size_t)n))) return rc;
+        launch_langevin(ctx, n, vel, mass, step0, dt, accel, st);
+    }
+    const double* FL = lang ? ctx->F_lang : nullptr;
     for (int k = 0; k < nsteps; ++k) {
-        launch_vv_kick_drift(ctx, n, pos, vel, mass, F, dt, accel, 1, st);
+        launch_vv_kick_drift(ctx, n, pos, vel, mass, F, FL, dt, accel, 1, st);
         rc = forces_device(ctx, step0 + (uint64_t)k + 1, n, pos, q, type, mol, F, st);
         if (rc) return rc;
-        launch_vv_kick_drift(ctx, n, pos, vel, mass, F, dt, accel, 0, st);
+        if (lang) launch_langevin(ctx, n, vel, mass, step0 + (uint64_t)k + 1, dt, accel, st);
+        launch_vv_kick_drift(ctx, n, pos, vel, mass, F, FL, dt, accel, 0, st);
         if (energy_trace) launch_ke_trace(ctx, n, vel, mass, accel, energy_trace + 2 * (size_t)k, st);
     }
     cudaError_t e = cudaGetLastError();

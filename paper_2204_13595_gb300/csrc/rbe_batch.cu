@@ -48,6 +48,7 @@ struct rbe_batch {
     BatchCtl* d_ctl = nullptr;
     BatchPlan plan{};
     int persistent = 1;      // pair kernel form (autotuned)
+    bool lang = false;       // some replica runs the Langevin thermostat
     int launches_force = 0, launches_step = 0;
     long total_atoms = 0;
     int n_sm = 0;
@@ -152,7 +153,7 @@ int build_plan(rbe_batch* b)
     for (int k = 0; k < BK_COUNT; ++k) cnt[k].assign(nr, 0);
     int rho_threads = 32, smem = 0;
     b->total_atoms = 0;
-    bool bonds = false;
+    bool bonds = false, lang = false;
     struct Task { double cost; int r, s; };
     std::vector<Task> tasks;
     for (int r = 0; r < nr; ++r) {
@@ -181,6 +182,16 @@ int build_plan(rbe_batch* b)
         d.kT = ctx->kT; d.km = ctx->km; d.kv = ctx->kv; d.rho_part = ctx->rho_part; d.rho = ctx->rho;
         d.totals = ctx->totals; d.F_real = ctx->F_real; d.F_bond = ctx->F_bond; d.status = ctx->status;
         d.kpool = ctx->kpool_buf;
+        d.FL = nullptr;
+        d.lang_c1 = d.lang_c2 = 0.0;
+        if (ctx->lang_tau > 0.0 && b->can_step) {
+            int rc = ctx_grow_lang(ctx, n);
+            if (rc) return berr(b, rc, "replica %d: %s", r, ctx->err);
+            d.FL = ctx->F_lang;
+            d.lang_c1 = d.accel * ctx->lang_tau;
+            d.lang_c2 = 24.0 * ctx->lang_kT / (d.lang_c1 * d.dt);
+            lang = true;
+        }
         rbl_fill_args(ctx, n, b->rbl_args.data() + ab * r);
 
         cnt[BK_CELLS][r] = ceil_div(ctx->ncells + 1, 256);
@@ -261,7 +272,9 @@ int build_plan(rbe_batch* b)
     p.rbl_smem = smem;
     p.rbl_persistent = b->persistent;
     b->launches_force = 6 + 3 + (bonds ? 1 : 0) + 1 + 2;
-    b->launches_step = b->launches_force + 1 + 2 + 2;   // + control, two half kicks, kinetic energy + trace
+    // + control, two half kicks, kinetic energy + trace, Langevin force
+    b->launches_step = b->launches_force + 1 + 2 + 2 + (lang ? 1 : 0);
+    b->lang = lang;
     return RBE_OK;
 }
 
@@ -289,6 +302,7 @@ int ensure_graph(rbe_batch* b)
     launch_vv_batch(p, 1, b->cap_stream);
     launch_ctl_batch(p, 1, 0, nullptr, 0, b->cap_stream);
     enqueue_forces(p, b->cap_stream);
+    if (b->lang) launch_langevin_batch(p, b->cap_stream);
     launch_vv_batch(p, 0, b->cap_stream);
     launch_ke_trace_batch(p, b->cap_stream);
     cudaGraph_t g = nullptr;
@@ -430,6 +444,7 @@ int rbe_batch_step(rbe_batch* b, uint64_t step0, int nsteps, double* energy_trac
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     launch_ctl_batch(b->plan, 0, step0, energy_trace, nsteps, st);
+    if (b->lang) launch_langevin_batch(b->plan, st);     // F^L at entry (step0)
     for (int k = 0; k < nsteps; ++k) BATCH_TRY(b, cudaGraphLaunch(b->exec, st));
     return launch_status(b);
 }

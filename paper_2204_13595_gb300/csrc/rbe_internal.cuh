@@ -86,6 +86,9 @@ struct rbe_ctx {
     int kpool_burn;       // burn-in of the k pool's Metropolis-Hastings chains
     int kpool_dirty;
     int4* kpool_buf;      // [kpool] pool of k samples (device)
+    double lang_kT, lang_tau;   // Langevin thermostat (tau <= 0: off)
+    double* F_lang;       // [3n] Langevin force, caller order
+    size_t F_lang_cap;
     // water bonds
     int n_wmol;
     double kb, r0, kth, th0;
@@ -194,6 +197,8 @@ struct RepDev {
     double* F_bond;
     int* status;
     const int4* kpool;
+    double* FL;               // Langevin force [3n] (null: thermostat off)
+    double lang_c1, lang_c2;  // accel tau, 24 kT / (accel tau dt)
 };
 
 // Device control block of a batch: the MD step the batched kernels use, the
@@ -322,12 +327,17 @@ void launch_bonded(rbe_ctx* ctx, int n, const double* pos, cudaStream_t st);
 void launch_finalize(rbe_ctx* ctx, int n, cudaStream_t st);
 void launch_kforce(rbe_ctx* ctx, int n, double* F, cudaStream_t st);
 void launch_vv_kick_drift(rbe_ctx* ctx, int n, double* pos, double* vel, const double* mass,
-                          const double* F, double dt, double accel, int drift, cudaStream_t st);
+                          const double* F, const double* FL, double dt, double accel, int drift, cudaStream_t st);
+void launch_langevin(rbe_ctx* ctx, int n, const double* vel, const double* mass, uint64_t s, double dt,
+                     double accel, cudaStream_t st);
+void launch_langevin_batch(const BatchPlan& bp, cudaStream_t st);
 void launch_ke_trace(rbe_ctx* ctx, int n, const double* vel, const double* mass, double accel,
                      double* trace_slot, cudaStream_t st);
 int rbl_smem_bytes(const rbe_ctx* ctx);
 // validation and device set-up of one context for n atoms (rbe_api.cu)
 int ctx_prepare(rbe_ctx* ctx, int n);
+// Langevin force buffer of a context for n atoms (rbe_api.cu)
+int ctx_grow_lang(rbe_ctx* ctx, int n);
 // batched stages (one launch each over all replicas of a plan)
 void launch_cells_batch(const BatchPlan& bp, cudaStream_t st);
 void launch_kspace_pre_batch(const BatchPlan& bp, cudaStream_t st);

@@ -27,7 +27,7 @@ EXPORTS = ["rbe_create", "rbe_set_coulomb", "rbe_set_lj", "rbe_set_precision", "
            "rbe_destroy", "rbe_rho_noalloc", "rbe_adjoint", "rbe_set_rbl_tiling", "rbe_batch_create",
            "rbe_batch_bind", "rbe_batch_forces", "rbe_batch_step", "rbe_batch_autotune", "rbe_batch_info",
            "rbe_batch_sync_status", "rbe_batch_last_error", "rbe_batch_destroy", "rbe_set_shell_sampling",
-           "rbe_set_lj_cutoff", "rbe_set_kpool"]
+           "rbe_set_lj_cutoff", "rbe_set_kpool", "rbe_set_langevin"]
 SHELL_FLOYD, SHELL_REPLACE = 0, 1
 WCA_FACTOR = 2.0 ** (1.0 / 6.0)
 ELIMIT = -8
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH):
     L.rbe_set_shell_sampling.argtypes = [vp, i]
     L.rbe_set_lj_cutoff.argtypes = [vp, d]
     L.rbe_set_kpool.argtypes = [vp, i, i]
+    L.rbe_set_langevin.argtypes = [vp, d, d]
     L.rbe_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
     L.rbe_batch_bind.argtypes = [vp, ctypes.POINTER(i)] + [ctypes.POINTER(vp)] * 7 + [ctypes.POINTER(d)] * 2
     L.rbe_batch_forces.argtypes = [vp, u64, vp, vp]
@@ -168,6 +169,10 @@ class Context:
 
     def set_kpool(self, size, burn_in=0):
         self._check(self.L.rbe_set_kpool(self.h, int(size), int(burn_in)))
+
+    def set_langevin(self, kT, tau):
+        """Langevin thermostat of rbe_step (tau <= 0: off)."""
+        self._check(self.L.rbe_set_langevin(self.h, float(kT), float(tau)))
 
     def set_rbl_tiling(self, atoms_per_unit=0, units_per_slot=0):
         self._check(self.L.rbe_set_rbl_tiling(self.h, int(atoms_per_unit), int(units_per_slot)))

@@ -48,3 +48,56 @@ def test_velocity_verlet_energy_and_reversibility(orc):
                       water=(1, kb, r0, kth, th0))
     assert np.abs(back["pos"] - pos).max() < 1e-9
     assert np.abs(back["vel"] + vel).max() < 1e-9
+
+
+def _free_particles(n, L, m, seed):
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, 3)) * L
+    return pos, np.zeros(n), np.zeros(n, dtype=np.int32), np.full(n, m)
+
+
+def test_langevin_zero_temperature_decay(orc):
+    """kT = 0, no interactions: the scheme of R10 gives w_0 = (1 - a) v_0 and
+    w_k = (1 - 2a) w_{k-1} for the half-step velocities, so
+    v_n = (1 - a)^2 (1 - 2a)^(n - 1) v_0 with a = dt / (2 tau)."""
+    n, L, dt, tau, accel = 64, 40.0, 0.01, 0.25, 0.7
+    pos, q, typ, mass = _free_particles(n, L, 2.5, 1)
+    vel = np.random.default_rng(2).normal(size=(n, 3))
+    pr = orc.make_params(L, 0.05, 3.0, 6.0, 10, 1, 5, eps=(0.0,), sigma=(1.0,), lang_kT=0.0, lang_tau=tau)
+    F0 = np.zeros((n, 3))
+    a = dt / (2 * tau)
+    for nsteps in (1, 5, 30):
+        out = orc.vv_run(pos, vel, mass, q, typ, None, pr, 0, nsteps, dt, accel, F0)
+        pred = (1 - a) ** 2 * (1 - 2 * a) ** (nsteps - 1) * vel
+        assert np.allclose(out["vel"], pred, rtol=1e-12, atol=0)
+
+
+def test_langevin_velocity_variance_closed_form(orc):
+    """Free particles from rest under R10: with eta of variance
+    s2 = 2 accel kT / (m tau dt), Var w_0 = dt^2 s2 / 4,
+    Var w_k = (1 - 2a)^2 Var w_{k-1} + dt^2 s2, and
+    Var v_n = (1 - a)^2 Var w_{n-1} + dt^2 s2 / 4, which tends to accel kT / m
+    (equipartition).  Checked per mass class at a transient and a late step."""
+    n, L, dt, tau, accel, kT = 20000, 400.0, 0.01, 0.05, 1.0, 1.7
+    pos, q, typ, _ = _free_particles(n, L, 1.0, 3)
+    mass = np.where(np.arange(n) % 2 == 0, 1.0, 4.0)
+    vel = np.zeros((n, 3))
+    pr = orc.make_params(L, 0.05, 3.0, 6.0, 10, 1, 9, eps=(0.0,), sigma=(1.0,), lang_kT=kT, lang_tau=tau)
+    a = dt / (2 * tau)
+    for nsteps in (3, 40):
+        out = orc.vv_run(pos, vel, mass, q, typ, None, pr, 0, nsteps, dt, accel, np.zeros((n, 3)))
+        for m in (1.0, 4.0):
+            s2 = 2 * accel * kT / (m * tau * dt)
+            vw = dt * dt * s2 / 4
+            for _ in range(nsteps - 1):
+                vw = (1 - 2 * a) ** 2 * vw + dt * dt * s2
+            pred = (1 - a) ** 2 * vw + dt * dt * s2 / 4
+            v = out["vel"][mass == m]
+            emp = float((v * v).mean())
+            rel_sd = math.sqrt(2.0 / v.size)
+            assert abs(emp / pred - 1) < 5 * rel_sd, (nsteps, m, emp, pred)
+            assert abs(float(v.mean())) < 5 * math.sqrt(pred / v.size)
+        if nsteps == 40:
+            for m in (1.0, 4.0):
+                v = out["vel"][mass == m]
+                assert float((v * v).mean()) == pytest.approx(accel * kT / m, rel=5 * math.sqrt(2.0 / v.size))
