@@ -82,8 +82,8 @@ class Params(ctypes.Structure):
 def make_params(L, alpha, r_c, r_s, p, P, seed, k_e=1.0, eps=(0.0,), sigma=(1.0,), shift_lj=0, shell_mode=0,
                 lj_rc_factor=0.0, kpool=0, kpool_burn=0, lang_kT=0.0, lang_tau=0.0):
     """Parameters of the estimator; shell_mode, lj_rc_factor, kpool and
-    kpool_burn select the variants of reading R9, lang_kT and lang_tau the
-    Langevin thermostat of R10 used by vv_run (defaults: the base method)."""
+    kpool_burn select the variants of reading R13, lang_kT and lang_tau the
+    Langevin thermostat of R14 used by vv_run (defaults: the base method)."""
     pr = Params()
     pr.lang_kT, pr.lang_tau = float(lang_kT), float(lang_tau)
     pr.shell_mode, pr.lj_rc_factor = int(shell_mode), float(lj_rc_factor)
@@ -195,7 +195,7 @@ def k_table(alpha, L):
 
 def mh_tables(alpha, L):
     """Target w_m, proposal q_m and the proposal's inverse-CDF thresholds of the
-    Metropolis-Hastings pool (reading R9), |m| <= M."""
+    Metropolis-Hastings pool (reading R13), |m| <= M."""
     M = lib().orc_kmax(alpha, L)
     w, q = np.zeros(2 * M + 1), np.zeros(2 * M + 1)
     Tq = np.zeros(2 * M + 1, dtype=np.uint64)

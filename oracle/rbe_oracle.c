@@ -43,7 +43,7 @@
  *  R7  Same-molecule (excluded) pairs keep their membership in C(i)/S(i) but
  *      their pair term is the Ewald exclusion correction
  *      -k_e q_i q_j erf(sqrt(alpha) r)/r instead of erfc + LJ.
- *  R9  Variants (Algorithm 1 and Sec. 2.3 leave these open): shell_mode 1
+ *  R13 Variants (Algorithm 1 and Sec. 2.3 leave these open): shell_mode 1
  *      draws the p slots of B(i) independently and uniformly with
  *      replacement (same words, ordinal floor(u N_S / 2^64)), weight N_S/p;
  *      lj_rc_factor f > 0 truncates the LJ term of pair (a, b) at
@@ -54,7 +54,7 @@
  *      (proposal round(x), x ~ N(0, alpha L^2 / (2 pi^2)), Sec. 2.2), and
  *      sample l of a step is pool entry floor(u K / 2^64), u word 0 of the
  *      block at counter (l, 0, step, 5).
- *  R10 Langevin thermostat (Sec. 3.1 runs the electrolytes with a Langevin
+ *  R14 Langevin thermostat (Sec. 3.1 runs the electrolytes with a Langevin
  *      thermostat of relaxation time tau inside velocity Verlet; the form is
  *      not given): with force-to-acceleration factor accel, each force
  *      evaluation at step s adds F^L_i = -(m_i / (accel tau)) v_i
@@ -93,12 +93,12 @@ typedef struct orc_params {
     int shift_lj;    /* 1: LJ energy shifted to zero at r_s               */
     double eps[ORC_MAXT];    /* per-type LJ epsilon                       */
     double sigma[ORC_MAXT];  /* per-type LJ sigma                         */
-    int shell_mode;          /* R9: 0 without replacement, 1 with         */
-    double lj_rc_factor;     /* R9: 0 LJ to r_s, f > 0 cut at f sigma_ab  */
-    int kpool;               /* R9: 0 fresh draws, K > 0 MH pool of K     */
-    int kpool_burn;          /* R9: burn-in iterations of the MH chains   */
-    double lang_kT;          /* R10: thermostat kT (energy units)         */
-    double lang_tau;         /* R10: relaxation time; <= 0 thermostat off */
+    int shell_mode;          /* R13: 0 without replacement, 1 with         */
+    double lj_rc_factor;     /* R13: 0 LJ to r_s, f > 0 cut at f sigma_ab  */
+    int kpool;               /* R13: 0 fresh draws, K > 0 MH pool of K     */
+    int kpool_burn;          /* R13: burn-in iterations of the MH chains   */
+    double lang_kT;          /* R14: thermostat kT (energy units)         */
+    double lang_tau;         /* R14: relaxation time; <= 0 thermostat off */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -272,7 +272,7 @@ int orc_sample_k(uint64_t seed, uint64_t step, int P, double alpha, double L, in
     return worst;
 }
 
-/* Metropolis-Hastings pool of k samples (R9; Algorithm 1, pool step; Sec. 2.2).
+/* Metropolis-Hastings pool of k samples (R13; Algorithm 1, pool step; Sec. 2.2).
  * Per axis, target w_m = exp(-pi^2 m^2 / (alpha L^2)) and proposal
  * q_m = P(round(X) = m), X ~ N(0, s^2), s^2 = alpha L^2 / (2 pi^2), both on
  * |m| <= M (the truncation of R4) and normalised there.  Proposals are drawn
@@ -336,7 +336,7 @@ double orc_kpool(uint64_t seed, double alpha, double L, int K, int burn, int32_t
     return (double)acc / (double)tries;
 }
 
-/* The P samples of a step under the parameters' sampling mode (R4 or R9). */
+/* The P samples of a step under the parameters' sampling mode (R4 or R13). */
 static void sample_k_mode(const orc_params* pr, uint64_t step, int32_t* m)
 {
     if (pr->kpool <= 0) {
@@ -490,7 +490,7 @@ static void classify_and_sample(const orc_grid* g, int i, const int32_t* cand, i
     } else {
         shell_words(seed, step, (uint64_t)i, p, words);
         if (shell_mode == 1) {
-            /* R9: p independent uniform ordinals (with replacement) */
+            /* R13: p independent uniform ordinals (with replacement) */
             for (int k = 0; k < p; ++k) ord[k] = uniform_below(words[k], (uint64_t)al->n_shell);
         } else {
             orc_floyd((uint64_t)al->n_shell, p, words, ord);
@@ -512,8 +512,8 @@ typedef struct {
     double eps_ij[ORC_MAXT * ORC_MAXT];
     double sig_ij[ORC_MAXT * ORC_MAXT];
     double lj_shift[ORC_MAXT * ORC_MAXT];
-    double lj_rc2[ORC_MAXT * ORC_MAXT];   /* squared LJ cutoff (R9)           */
-    int lj_cut[ORC_MAXT * ORC_MAXT];      /* 1: cut at f sigma_ab < r_s (R9)  */
+    double lj_rc2[ORC_MAXT * ORC_MAXT];   /* squared LJ cutoff (R13)           */
+    int lj_cut[ORC_MAXT * ORC_MAXT];      /* 1: cut at f sigma_ab < r_s (R13)  */
     int ntypes;
 } pair_consts;
 
@@ -531,7 +531,7 @@ static void make_pair_consts(const orc_params* pr, pair_consts* pc)
             double s = 0.5 * (pr->sigma[a] + pr->sigma[b]);    /* Lorentz   */
             pc->eps_ij[a * ORC_MAXT + b] = e;
             pc->sig_ij[a * ORC_MAXT + b] = s;
-            /* R9: LJ cutoff min(f sigma_ab, r_s); the shift is U_LJ there */
+            /* R13: LJ cutoff min(f sigma_ab, r_s); the shift is U_LJ there */
             double rc = pr->r_s;
             int cut = 0;
             if (pr->lj_rc_factor > 0.0 && pr->lj_rc_factor * s < pr->r_s) {
@@ -1125,7 +1125,7 @@ double orc_water_bonded(int nmol, int first, const double* pos, double L, double
  * F holds the forces at (pos, step0) on entry and at the final positions on
  * exit.  etrace[2*k] = potential (sum of E[0..5]), etrace[2*k+1] = kinetic
  * after step k.  Water bonds are applied when nmol_w > 0 (atoms 0..3*nmol_w-1). */
-/* Langevin force of R10 at step s from the current velocities (FL = 0 when
+/* Langevin force of R14 at step s from the current velocities (FL = 0 when
  * the thermostat is off). */
 static void langevin_force(int n, const double* vel, const double* mass, const orc_params* pr, uint64_t s,
                            double dt, double accel, double* FL)
@@ -1292,7 +1292,7 @@ int orc_rbe_adjoint(int n, const double* pos, const double* q, const int32_t* ty
                         double du_ds = 4.0 * e * (12.0 * sr12 - 6.0 * sr6) / sg;
                         if (pc.shift_lj) {
                             /* shift 4 e ((sg/rc)^12 - (sg/rc)^6): with rc = f sg
-                             * (R9) it does not depend on sg */
+                             * (R13) it does not depend on sg */
                             double rc = pc.lj_cut[tti] ? sqrt(pc.lj_rc2[tti]) : pc.r_s;
                             double ss = sg / rc, ss6 = pow(ss, 6.0), ss12 = ss6 * ss6;
                             du_de -= 4.0 * (ss12 - ss6);

@@ -1,4 +1,4 @@
-"""Langevin thermostat (reading R10) on the GPU: the zero-temperature closed
+"""Langevin thermostat (reading R14) on the GPU: the zero-temperature closed
 form, trajectory parity with the oracle, batched = looped bit for bit, and
 physical checks on the paper's 1:1 primitive-model electrolyte (Sec. 3.1:
 5,120 ions at 0.01 sigma^-3, L = 80 sigma, WCA soft spheres, r_eta = 5 sigma,

@@ -1,4 +1,4 @@
-"""Parity of the method variants on the GPU with the oracle (reading R9):
+"""Parity of the method variants on the GPU with the oracle (reading R13):
 shell batches with replacement, the per-pair LJ cutoff (WCA soft spheres)
 and the Metropolis-Hastings k pool.  Same bars as the base method: lists,
 batches and k samples bit-exact; FP64 forces within 1e-11 of each

@@ -57,7 +57,7 @@ def _free_particles(n, L, m, seed):
 
 
 def test_langevin_zero_temperature_decay(orc):
-    """kT = 0, no interactions: the scheme of R10 gives w_0 = (1 - a) v_0 and
+    """kT = 0, no interactions: the scheme of R14 gives w_0 = (1 - a) v_0 and
     w_k = (1 - 2a) w_{k-1} for the half-step velocities, so
     v_n = (1 - a)^2 (1 - 2a)^(n - 1) v_0 with a = dt / (2 tau)."""
     n, L, dt, tau, accel = 64, 40.0, 0.01, 0.25, 0.7
@@ -73,7 +73,7 @@ def test_langevin_zero_temperature_decay(orc):
 
 
 def test_langevin_velocity_variance_closed_form(orc):
-    """Free particles from rest under R10: with eta of variance
+    """Free particles from rest under R14: with eta of variance
     s2 = 2 accel kT / (m tau dt), Var w_0 = dt^2 s2 / 4,
     Var w_k = (1 - 2a)^2 Var w_{k-1} + dt^2 s2, and
     Var v_n = (1 - a)^2 Var w_{n-1} + dt^2 s2 / 4, which tends to accel kT / m

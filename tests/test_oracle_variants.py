@@ -1,4 +1,4 @@
-"""Pins of the oracle's method variants (reading R9): shell batches drawn with
+"""Pins of the oracle's method variants (reading R13): shell batches drawn with
 replacement, the LJ term truncated per pair type (the WCA soft sphere of the
 paper's electrolytes, Sec. 3.1) and the Metropolis-Hastings pool of k samples
 (Algorithm 1, pool step; Sec. 2.2).  CPU only."""
