@@ -54,8 +54,8 @@ SM_MAX_MHZ = 2070.0
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    from paper_2204_13595_gb300 import replicas
+    ws, rank, _ = replicas.world()
     return ws, rank
 
 
@@ -245,7 +245,7 @@ def run_ours(args):
     import torch
 
     from paper_2204_13595_gb300 import build as b
-    from paper_2204_13595_gb300 import rbe, systems
+    from paper_2204_13595_gb300 import rbe, replicas, systems
 
     ws, rank = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -254,7 +254,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     b.build()
-    s = systems.water(N_MOL, seed=SEED + rank)
+    s = systems.water(N_MOL, seed=replicas.rank_seed(SEED, rank))
     dev = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device="cuda")
     pos, q, typ, mol = dev(s.pos), dev(s.q), dev(s.type, torch.int32), dev(s.mol, torch.int32)
     F = torch.empty_like(pos)
@@ -276,8 +276,7 @@ def run_ours(args):
             ctx.profile(reset=True)
             ctx.set_profiling(True)
         total = 0.0
-        if ws > 1:
-            torch.distributed.barrier()
+        replicas.barrier(ws)
         torch.cuda.synchronize()
         for k in range(steps):
             flush.fill_(float(k))
@@ -289,8 +288,7 @@ def run_ours(args):
             e1.synchronize()
             total += e0.elapsed_time(e1)
         torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
+        replicas.barrier(ws)
         prof = None
         if profile:
             prof = ctx.profile(reset=True)
@@ -298,11 +296,7 @@ def run_ours(args):
         launches = int(ctx.info()["launches"])
         if ctx.sync_status() != 0:
             raise RuntimeError("device status error during the timed steps")
-        ms = total / steps
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = replicas.max_over_ranks(total / steps, ws, device="cuda")
         return ms, prof, launches
 
     # fixed-error check: mixed vs FP64 on identical draws (outside timing)
@@ -328,10 +322,11 @@ def run_ours(args):
     hW = torch.empty(rbe.NW, dtype=torch.float64).pin_memory()
     for w in range(args.warmup):
         mixed.forces(w, hp, hq, ht, hm, hF, hE, hW)
+    replicas.barrier(ws)
     t0 = time.perf_counter()
     for k in range(args.steps):
         mixed.forces(args.warmup + k, hp, hq, ht, hm, hF, hE, hW)
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = replicas.max_over_ranks((time.perf_counter() - t0) / args.steps, ws, device="cuda")
     h2d = hp.numel() * 8 + hq.numel() * 8 + ht.numel() * 4 + hm.numel() * 4
     d2h = hF.numel() * 8 + hE.numel() * 8 + hW.numel() * 8
 
@@ -357,7 +352,7 @@ def run_ours(args):
     cpu_s = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
-    value = ws * 1e3 / ms_mixed
+    value = replicas.throughput(ws, 1, ms_mixed)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -374,7 +369,7 @@ def run_ours(args):
         "kernel_share": kshare,
         "cpu_baseline": {"value": 1.0 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "one full FP64 oracle force evaluation of the same 1.2M-atom system"},
-        "e2e": {"value": ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": replicas.throughput(ws, 1, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks, "gpu_launches": launches * args.steps,
         "batch": batch,
     }

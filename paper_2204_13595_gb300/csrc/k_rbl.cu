@@ -159,7 +159,8 @@ __device__ __forceinline__ void dist_class(const float4 pj, bool valid, float xi
 // Classification of one canonical segment [beg, end) of the source array:
 // FP32 distance with exact integer decision inside the rounding bands.  Two
 // chunks of 32 candidates are processed per iteration (their loads and
-// arithmetic are independent) and appended in order.
+// arithmetic are independent) and appended in order; a tail of at most 32
+// candidates takes a one-chunk iteration.
 template <bool SMALL>
 __device__ __forceinline__ void classify(const float4* __restrict__ src, int beg, int end, int goff, float xie,
                                          float yie, float zie, const RblArgs& a, int i, uint4 si, int lane,
@@ -168,13 +169,14 @@ __device__ __forceinline__ void classify(const float4* __restrict__ src, int beg
 {
     const RblGeom& g = a.g;
     const unsigned FULL = 0xffffffffu;
-    for (int bb = beg; bb < end; bb += 64) {
+    int bb = beg;
+    for (; end - bb > 32; bb += 64) {
         const int sa = bb + lane, sb = bb + 32 + lane;
-        const bool va = sa < end, vb = sb < end;
-        const float4 pa = src[va ? sa : beg];
+        const bool vb = sb < end;
+        const float4 pa = src[sa];
         const float4 pb = src[vb ? sb : beg];
         bool ca, sha, ma, cb, shb, mb;
-        dist_class<SMALL>(pa, va, xie, yie, zie, g, Lf, invLf, ca, sha, ma);
+        dist_class<SMALL>(pa, true, xie, yie, zie, g, Lf, invLf, ca, sha, ma);
         dist_class<SMALL>(pb, vb, xie, yie, zie, g, Lf, invLf, cb, shb, mb);
         const int ga = sa + goff, gb = sb + goff;
         if (__any_sync(FULL, ma || mb)) {
@@ -205,12 +207,31 @@ __device__ __forceinline__ void classify(const float4* __restrict__ src, int beg
         ncore += nca + __popc(cmb);
         nshell += nsa + __popc(smb);
     }
+    if (bb < end) {
+        const int sa = bb + lane;
+        const bool va = sa < end;
+        const float4 pa = src[va ? sa : beg];
+        bool ca, sha, ma;
+        dist_class<SMALL>(pa, va, xie, yie, zie, g, Lf, invLf, ca, sha, ma);
+        const int ga = sa + goff;
+        if (__any_sync(FULL, ma)) {
+            if (ma) {
+                unsigned long long d2 = d2_exact(si, a.s4[ga]);
+                bool other = ga != i;
+                ca = other && d2 <= a.c.Rc2;
+                sha = other && d2 > a.c.Rc2 && d2 <= a.c.Rs2;
+                overlap |= other && d2 == 0ull;
+            }
+        }
+        const unsigned cma = __ballot_sync(FULL, ca), sma = __ballot_sync(FULL, sha);
+        const int cpa = ncore + __popc(cma & lt_mask), spa = nshell + __popc(sma & lt_mask);
+        if (ca && cpa < a.core_cap) core_buf[cpa] = ga;
+        if (sha && spa < a.shell_cap) shell_buf[spa] = ga;
+        ncore += __popc(cma);
+        nshell += __popc(sma);
+    }
 }
 
-// One slot of the pair kernel: the units slot, slot + nslots, ... of one
-// system, with the slot's energy/virial/net-force partial written to
-// part[slot].  Both the single-system kernel (slot = block) and the batched
-// persistent kernel (slots taken from a work queue) run this body.
 template <bool MIXED, bool SMALL, bool ADJ>
 __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
 {
