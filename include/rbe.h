@@ -23,8 +23,8 @@
  * List membership is decided on 32-bit fixed-point fractional coordinates
  * s = floor(frac(x/L) 2^32) with exact integer squared distances, so lists and
  * batches are reproducible bit for bit.  Shell ordinals index S(i) in the
- * canonical order: ascending (cell, atom index) on the grid of floor(L/r_c)
- * cells per axis (the cell grid of Sec. 2.3).
+ * canonical order: ascending (cell, fixed-point x code s_x, atom index) on the
+ * grid of floor(L/r_c) cells per axis (the cell grid of Sec. 2.3).
  *
  * Conventions for every entry point:
  *   - return 0 (RBE_OK) or a negative RBE_E* code; no exception or abort

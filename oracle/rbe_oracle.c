@@ -24,9 +24,9 @@
  *      This makes list membership reproducible bit for bit.
  *  R3  The shell batch B(i) is drawn uniformly without replacement by Floyd's
  *      algorithm (Bentley & Floyd, CACM 1987) over ordinals [0, N_S); ordinals
- *      index S(i) in canonical order: ascending (cell index, atom id) on the
- *      grid of n_cell = floor(L/r_c) cells per axis (Sec. 2.3 uses cells of
- *      edge r_eta).  If N_S <= p the batch is all of S(i) with weight 1
+ *      index S(i) in canonical order: ascending (cell index, fixed-point x
+ *      code s_x, atom id) on the grid of n_cell = floor(L/r_c) cells per axis
+ *      (Sec. 2.3 uses cells of edge r_eta).  If N_S <= p the batch is all of S(i) with weight 1
  *      (Algorithm 1, shell selection step).
  *  R4  The k sampler draws each axis independently from the discrete Gaussian
  *      w_m = exp(-pi^2 m^2 / (alpha L^2)) by exact inverse CDF on 64-bit
@@ -629,11 +629,27 @@ static void build_grid(int n, const double* pos, const orc_params* pr, grid_stor
     }
     for (long c = 0; c < ncells; ++c) gs->cell_start[c + 1] += gs->cell_start[c];
     int32_t* fill = (int32_t*)calloc((size_t)ncells, sizeof(int32_t));
-    for (int i = 0; i < n; ++i) { /* ascending id inside each cell */
+    for (int i = 0; i < n; ++i) {
         int c = gs->cell[i];
         gs->cell_atoms[gs->cell_start[c] + fill[c]++] = i;
     }
     free(fill);
+    /* R3: inside a cell, ascending (s_x, atom id) (insertion sort; ids are
+     * already ascending, so equal s_x keep id order) */
+    for (long c = 0; c < ncells; ++c) {
+        int32_t* a = gs->cell_atoms + gs->cell_start[c];
+        int cnt = gs->cell_start[c + 1] - gs->cell_start[c];
+        for (int k = 1; k < cnt; ++k) {
+            int32_t v = a[k];
+            uint32_t key = gs->s[3 * v];
+            int t = k - 1;
+            while (t >= 0 && (gs->s[3 * a[t]] > key || (gs->s[3 * a[t]] == key && a[t] > v))) {
+                a[t + 1] = a[t];
+                --t;
+            }
+            a[t + 1] = v;
+        }
+    }
 }
 
 static void free_grid(grid_storage* gs)
@@ -641,7 +657,7 @@ static void free_grid(grid_storage* gs)
     free(gs->s); free(gs->cell); free(gs->cell_start); free(gs->cell_atoms);
 }
 
-/* Canonical order of all atoms: ascending (cell, id). */
+/* Canonical order of all atoms: ascending (cell, s_x, id) (R3). */
 static void canonical_order(const grid_storage* gs, int n, int32_t* order)
 {
     int nc = gs->n_cell;

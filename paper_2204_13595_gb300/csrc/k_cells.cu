@@ -19,8 +19,8 @@ constexpr int TPB = 256;
 __device__ __forceinline__ void quantize_count_body(int bx, int nbx, int n, const double* __restrict__ pos,
                                                     const double* __restrict__ q, const RbeConsts& c,
                                                     int* __restrict__ cell_count, int* __restrict__ cell_of,
-                                                    int* __restrict__ slot, double* __restrict__ part_q,
-                                                    int* __restrict__ status)
+                                                    int* __restrict__ slot, uint32_t* __restrict__ sx_of,
+                                                    double* __restrict__ part_q, int* __restrict__ status)
 {
     double sq2 = 0.0, sq = 0.0, sabs = 0.0;
     for (int i = bx * TPB + threadIdx.x; i < n; i += nbx * TPB) {
@@ -38,6 +38,7 @@ __device__ __forceinline__ void quantize_count_body(int bx, int nbx, int n, cons
         uint32_t cx = cell_of_fixed(sx, c.n_cell), cy = cell_of_fixed(sy, c.n_cell), cz = cell_of_fixed(sz, c.n_cell);
         int cell = (int)(cx + (uint32_t)c.n_cell * (cy + (uint32_t)c.n_cell * cz));
         cell_of[i] = cell;
+        sx_of[i] = sx;
         slot[i] = atomicAdd(&cell_count[cell], 1);
         sq2 += qi * qi;
         sq += qi;
@@ -58,10 +59,10 @@ __device__ __forceinline__ void quantize_count_body(int bx, int nbx, int n, cons
 __global__ void __launch_bounds__(TPB) k_quantize_count(int n, const double* __restrict__ pos,
                                                         const double* __restrict__ q, RbeConsts c,
                                                         int* __restrict__ cell_count, int* __restrict__ cell_of,
-                                                        int* __restrict__ slot, double* __restrict__ part_q,
-                                                        int* __restrict__ status)
+                                                        int* __restrict__ slot, uint32_t* __restrict__ sx_of,
+                                                        double* __restrict__ part_q, int* __restrict__ status)
 {
-    quantize_count_body(blockIdx.x, gridDim.x, n, pos, q, c, cell_count, cell_of, slot, part_q, status);
+    quantize_count_body(blockIdx.x, gridDim.x, n, pos, q, c, cell_count, cell_of, slot, sx_of, part_q, status);
 }
 
 // Exclusive scan of cell_count[0..m) into start[0..m] (single block).
@@ -129,23 +130,35 @@ __global__ void __launch_bounds__(TPB) k_scatter(int n, const int* __restrict__ 
     scatter_body(blockIdx.x, n, cell_of, slot, start, perm);
 }
 
-// Canonical in-cell order: ascending caller index (insertion sort, cells are small).
-__device__ __forceinline__ void sort_cells_body(int bx, long m, const int* __restrict__ start, int* __restrict__ perm)
+// Canonical in-cell order: ascending (fixed-point x code, caller index)
+// (insertion sort on the 64-bit key, cells are small).  Sorting by x lets the
+// pair kernel drop, by binary search, the atoms of a stencil row's end cells
+// that lie beyond r_s along x.
+__device__ __forceinline__ void sort_cells_body(int bx, long m, const int* __restrict__ start,
+                                                const uint32_t* __restrict__ sx_of, int* __restrict__ perm)
 {
     long c = (long)bx * TPB + threadIdx.x;
     if (c >= m) return;
     int b = start[c], e = start[c + 1];
     for (int k = b + 1; k < e; ++k) {
-        int v = perm[k];
+        const int v = perm[k];
+        const unsigned long long kv = ((unsigned long long)sx_of[v] << 32) | (unsigned)v;
         int t = k - 1;
-        while (t >= b && perm[t] > v) { perm[t + 1] = perm[t]; --t; }
+        while (t >= b) {
+            const int u = perm[t];
+            const unsigned long long ku = ((unsigned long long)sx_of[u] << 32) | (unsigned)u;
+            if (ku <= kv) break;
+            perm[t + 1] = u;
+            --t;
+        }
         perm[t + 1] = v;
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_sort_cells(long m, const int* __restrict__ start, int* __restrict__ perm)
+__global__ void __launch_bounds__(TPB) k_sort_cells(long m, const int* __restrict__ start,
+                                                    const uint32_t* __restrict__ sx_of, int* __restrict__ perm)
 {
-    sort_cells_body(blockIdx.x, m, start, perm);
+    sort_cells_body(blockIdx.x, m, start, sx_of, perm);
 }
 
 __device__ __forceinline__ void gather_body(int bx, int n, const int* __restrict__ perm, const double* __restrict__ pos,
@@ -205,7 +218,8 @@ __global__ void __launch_bounds__(TPB) k_quantize_count_b(const RepDev* __restri
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    quantize_count_body(bx, nbx, d.n, d.pos, d.q, d.c, d.cell_count, d.cell_of, d.slot, d.part_q, d.status);
+    quantize_count_body(bx, nbx, d.n, d.pos, d.q, d.c, d.cell_count, d.cell_of, d.slot, d.sx_of, d.part_q,
+                        d.status);
 }
 
 __global__ void __launch_bounds__(1024) k_scan_b(const RepDev* __restrict__ R)
@@ -226,7 +240,7 @@ __global__ void __launch_bounds__(TPB) k_sort_cells_b(const RepDev* __restrict__
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    sort_cells_body(bx, d.ncells, d.cell_start, d.perm);
+    sort_cells_body(bx, d.ncells, d.cell_start, d.sx_of, d.perm);
 }
 
 __global__ void __launch_bounds__(TPB) k_gather_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
@@ -243,7 +257,7 @@ void launch_quantize_count(rbe_ctx* ctx, int n, const double* pos, const double*
     cudaMemsetAsync(ctx->cell_count, 0, sizeof(int) * (size_t)(ctx->ncells + 1), st);
     prof_begin(ctx, RBE_K_QUANTIZE, st);
     k_quantize_count<<<ctx->grid_q, TPB, 0, st>>>(n, pos, q, ctx->c, ctx->cell_count, ctx->cell_of, ctx->slot,
-                                                  ctx->part_q, ctx->status);
+                                                  ctx->sx_of, ctx->part_q, ctx->status);
     prof_end(ctx, RBE_K_QUANTIZE, st);
 }
 
@@ -262,7 +276,8 @@ void launch_scatter_sort_gather(rbe_ctx* ctx, int n, const double* pos, const do
     k_scatter<<<g, TPB, 0, st>>>(n, ctx->cell_of, ctx->slot, ctx->cell_start, ctx->perm);
     prof_end(ctx, RBE_K_SCATTER, st);
     prof_begin(ctx, RBE_K_SORT, st);
-    k_sort_cells<<<(unsigned)((ctx->ncells + TPB - 1) / TPB), TPB, 0, st>>>(ctx->ncells, ctx->cell_start, ctx->perm);
+    k_sort_cells<<<(unsigned)((ctx->ncells + TPB - 1) / TPB), TPB, 0, st>>>(ctx->ncells, ctx->cell_start,
+                                                                            ctx->sx_of, ctx->perm);
     prof_end(ctx, RBE_K_SORT, st);
     prof_begin(ctx, RBE_K_GATHER, st);
     k_gather<<<g, TPB, 0, st>>>(n, ctx->perm, pos, q, type, mol, ctx->c, ctx->s4, ctx->f4, ctx->p4, ctx->tm,

@@ -7,10 +7,11 @@
 // cells, R = floor(r_s/w)+1 (Sec. 2.3's stencil reach).  Each warp then owns
 // one atom i of the unit at a time:
 //   1. list construction: the warp walks i's stencil rows in canonical order
-//      (ascending wrapped cell index, then atom index), each row trimmed to
-//      the cells that can hold a point within r_s; every row is one or two
-//      contiguous ranges of the staged arrays with a fixed periodic image
-//      shift.  Candidates are classified into the core C(i) (r <= r_c) and
+//      (ascending wrapped cell index, then fixed-point x, then atom index),
+//      each row cut to the cells that can hold a point within r_s and, by
+//      binary search on the x-sorted end cells, to the atoms within the
+//      row's x half-width; every row is one or two contiguous ranges of the
+//      staged arrays with a fixed periodic image shift.  Candidates are classified into the core C(i) (r <= r_c) and
 //      the shell S(i) (r_c < r <= r_s) by an FP32 distance whose rounding is
 //      bounded on the host; candidates inside that bound of r_c or r_s, and
 //      r ~ 0, are decided by the exact integer squared distance of the 32-bit
@@ -131,6 +132,35 @@ __device__ __forceinline__ unsigned long long d2_exact(uint4 a, uint4 b)
            (unsigned long long)((long long)dz * dz);
 }
 
+
+// Trim the canonical segment [b, e) of a stencil row to the atoms whose x lies
+// within [xref - H, xref + H]: inside a cell atoms are sorted by their
+// fixed-point x code, so the staged FP32 x is non-decreasing there (up to one
+// ulp between atoms of equal code) and the first and last cells of the
+// segment are cut by binary search.  H = hx L is the row's x half-width
+// bound already used to choose the segment's cells (conservative by
+// construction: every member of C or S has |dx| <= r_s < H - 1e-3 A), so no
+// member is dropped and the exact classification is unchanged.
+__device__ __forceinline__ void trim_segment(const float4* __restrict__ src, int& b, int& e, int cnt_lo, int cnt_hi,
+                                             bool one_cell, float xref, float H)
+{
+    const float lo_x = xref - H, hi_x = xref + H;
+    int l = b, r = b + cnt_lo;
+    while (l < r) {
+        const int m = (l + r) >> 1;
+        if (src[m].x < lo_x) l = m + 1;
+        else r = m;
+    }
+    const int nb = l;
+    int l2 = one_cell ? nb : e - cnt_hi, r2 = e;
+    while (l2 < r2) {
+        const int m = (l2 + r2) >> 1;
+        if (src[m].x <= hi_x) l2 = m + 1;
+        else r2 = m;
+    }
+    b = nb;
+    e = l2 < nb ? nb : l2;
+}
 
 // Classification of one canonical segment [beg, end) of the source array:
 // FP32 distance with exact integer decision inside the rounding bands.
@@ -469,12 +499,16 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                             if (ua < 0) { lo1 = 0; hi1 = ub; lo2 = ua; hi2 = -1; }
                             else if (ub >= nc) { lo1 = nc; hi1 = ub; lo2 = ua; hi2 = nc - 1; }
                             else { lo1 = ua; hi1 = ub; }
+                            const float H = hx * Lf;
+                            const float4* srcp = staged ? stage : a.f4;
                             {
                                 const int pc = lo1 >= nc ? 2 : 1;
                                 if (staged) { b1 = base + cp[lo1 - ul]; e1 = base + cp[hi1 - ul + 1]; }
                                 else { b1 = a.cell_start[rbw + wrapc(lo1, nc)]; e1 = b1 + cp[hi1 - ul + 1] - cp[lo1 - ul]; }
                                 o1 = ri.goff[pc];
                                 x1 = fi4.x - (pc == 2 ? Lf : 0.f);
+                                trim_segment(srcp, b1, e1, cp[lo1 - ul + 1] - cp[lo1 - ul], cp[hi1 - ul + 1] - cp[hi1 - ul],
+                                             lo1 == hi1, x1, H);
                             }
                             if (lo2 <= hi2) {
                                 const int pc = lo2 < 0 ? 0 : 1;
@@ -482,6 +516,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                                 else { b2 = a.cell_start[rbw + wrapc(lo2, nc)]; e2 = b2 + cp[hi2 - ul + 1] - cp[lo2 - ul]; }
                                 o2 = ri.goff[pc];
                                 x2 = fi4.x - (pc == 0 ? -Lf : 0.f);
+                                trim_segment(srcp, b2, e2, cp[lo2 - ul + 1] - cp[lo2 - ul], cp[hi2 - ul + 1] - cp[hi2 - ul],
+                                             lo2 == hi2, x2, H);
                             }
                         }
                     }

@@ -2,8 +2,9 @@
 //
 // Data layout in HBM (all device buffers owned by rbe_ctx, sized for n_cap
 // atoms and grown on demand):
-//   sorted order = atoms ordered by (canonical cell, caller index), built by a
-//   counting sort each step (cells of edge L/floor(L/r_c), Sec. 2.3).
+//   sorted order = atoms ordered by (canonical cell, fixed-point x, caller
+//   index), built by a counting sort each step (cells of edge L/floor(L/r_c),
+//   Sec. 2.3).
 //   s4   [n]  uint4   fixed-point (sx, sy, sz) and q as FP32 bits   (16 B/atom)
 //   f4   [n]  float4  FP32 wrapped (x, y, z) and q                 (16 B/atom)
 //   p4   [n]  double4_32a wrapped (x, y, z) and q in FP64              (32 B/atom)
@@ -104,6 +105,7 @@ struct rbe_ctx {
     int* perm;
     int* cell_of;
     int* slot;
+    uint32_t* sx_of;     // [n] fixed-point x code, caller order (in-cell sort key)
     int* cell_count;     // [ncells + 1]
     int* cell_start;     // [ncells + 1]
     double* F_real;      // [3n] sorted (FP32 [3n] on the mixed path)
@@ -148,7 +150,7 @@ struct rbe_ctx {
     int tune_apu;        // target atoms per RBL work unit (0: 48)
     int tune_ups;        // RBL units per slot (0: about 3, at least one wave of resident blocks)
     RblGeom rbl;
-    size_t cap_atoms[20];
+    size_t cap_atoms[24];
     size_t cap_adj[8];
 };
 
@@ -178,6 +180,7 @@ struct RepDev {
     int* cell_start;
     int* cell_of;
     int* slot;
+    uint32_t* sx_of;
     int* perm;
     uint4* s4;
     float4* f4;
