@@ -116,18 +116,103 @@ __global__ void __launch_bounds__(1024) k_scan(long m, const int* __restrict__ c
     scan_body(m, count, start);
 }
 
+// Three-phase exclusive scan of the cell counts for large grids: tile sums,
+// one block scanning the tile sums, then each tile rescanned with its offset.
+// SCAN_TILE cells per block of TPB threads, SCAN_ITEMS consecutive cells per
+// thread.  Integer arithmetic: the result is the same as the one-block scan.
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = TPB * SCAN_ITEMS;
+
+__device__ __forceinline__ int block_excl_scan(int v, int& total)
+{
+    __shared__ int wsum[TPB / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int k = 0; k < TPB / 32; ++k) {
+        const int x = wsum[k];
+        if (k < w) before += x;
+        all += x;
+    }
+    __syncthreads();
+    total = all;
+    return before + incl - v;
+}
+
+__global__ void __launch_bounds__(TPB) k_scan_tiles(long m, const int* __restrict__ count, int* __restrict__ tile_sum)
+{
+    const long base = (long)blockIdx.x * SCAN_TILE + (long)threadIdx.x * SCAN_ITEMS;
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < m) v += count[base + k];
+    int total;
+    block_excl_scan(v, total);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(TPB) k_scan_top(int ntiles, int* __restrict__ tile_sum, long m,
+                                                 int* __restrict__ start)
+{
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int t0 = 0; t0 < ntiles; t0 += TPB) {
+        const int t = t0 + threadIdx.x;
+        const int v = t < ntiles ? tile_sum[t] : 0;
+        int total;
+        const int ex = block_excl_scan(v, total);
+        const int c0 = carry;
+        if (t < ntiles) tile_sum[t] = c0 + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c0 + total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) start[m] = carry;
+}
+
+__global__ void __launch_bounds__(TPB) k_scan_apply(long m, const int* __restrict__ count,
+                                                   const int* __restrict__ tile_off, int* __restrict__ start)
+{
+    const long base = (long)blockIdx.x * SCAN_TILE + (long)threadIdx.x * SCAN_ITEMS;
+    int c[SCAN_ITEMS];
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        c[k] = base + k < m ? count[base + k] : 0;
+        v += c[k];
+    }
+    int total;
+    int run = tile_off[blockIdx.x] + block_excl_scan(v, total);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < m) start[base + k] = run;
+        run += c[k];
+    }
+}
+
+// Scatter into the cell ranges the in-cell sort key (fixed-point x << 32 |
+// caller index) of every atom.
 __device__ __forceinline__ void scatter_body(int bx, int n, const int* __restrict__ cell_of,
-                                             const int* __restrict__ slot, const int* __restrict__ start,
-                                             int* __restrict__ perm)
+                                             const int* __restrict__ slot, const uint32_t* __restrict__ sx_of,
+                                             const int* __restrict__ start, unsigned long long* __restrict__ skey)
 {
     int i = bx * TPB + threadIdx.x;
-    if (i < n) perm[start[cell_of[i]] + slot[i]] = i;
+    if (i < n) skey[start[cell_of[i]] + slot[i]] = ((unsigned long long)sx_of[i] << 32) | (unsigned)i;
 }
 
 __global__ void __launch_bounds__(TPB) k_scatter(int n, const int* __restrict__ cell_of, const int* __restrict__ slot,
-                                                 const int* __restrict__ start, int* __restrict__ perm)
+                                                 const uint32_t* __restrict__ sx_of, const int* __restrict__ start,
+                                                 unsigned long long* __restrict__ skey)
 {
-    scatter_body(blockIdx.x, n, cell_of, slot, start, perm);
+    scatter_body(blockIdx.x, n, cell_of, slot, sx_of, start, skey);
 }
 
 // Canonical in-cell order: ascending (fixed-point x code, caller index)
@@ -135,30 +220,29 @@ __global__ void __launch_bounds__(TPB) k_scatter(int n, const int* __restrict__ 
 // pair kernel drop, by binary search, the atoms of a stencil row's end cells
 // that lie beyond r_s along x.
 __device__ __forceinline__ void sort_cells_body(int bx, long m, const int* __restrict__ start,
-                                                const uint32_t* __restrict__ sx_of, int* __restrict__ perm)
+                                                unsigned long long* __restrict__ skey, int* __restrict__ perm)
 {
     long c = (long)bx * TPB + threadIdx.x;
     if (c >= m) return;
     int b = start[c], e = start[c + 1];
     for (int k = b + 1; k < e; ++k) {
-        const int v = perm[k];
-        const unsigned long long kv = ((unsigned long long)sx_of[v] << 32) | (unsigned)v;
+        const unsigned long long kv = skey[k];
         int t = k - 1;
         while (t >= b) {
-            const int u = perm[t];
-            const unsigned long long ku = ((unsigned long long)sx_of[u] << 32) | (unsigned)u;
+            const unsigned long long ku = skey[t];
             if (ku <= kv) break;
-            perm[t + 1] = u;
+            skey[t + 1] = ku;
             --t;
         }
-        perm[t + 1] = v;
+        skey[t + 1] = kv;
     }
+    for (int k = b; k < e; ++k) perm[k] = (int)(unsigned)(skey[k] & 0xffffffffull);
 }
 
 __global__ void __launch_bounds__(TPB) k_sort_cells(long m, const int* __restrict__ start,
-                                                    const uint32_t* __restrict__ sx_of, int* __restrict__ perm)
+                                                    unsigned long long* __restrict__ skey, int* __restrict__ perm)
 {
-    sort_cells_body(blockIdx.x, m, start, sx_of, perm);
+    sort_cells_body(blockIdx.x, m, start, skey, perm);
 }
 
 __device__ __forceinline__ void gather_body(int bx, int n, const int* __restrict__ perm, const double* __restrict__ pos,
@@ -232,7 +316,7 @@ __global__ void __launch_bounds__(TPB) k_scatter_b(const RepDev* __restrict__ R,
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    scatter_body(bx, d.n, d.cell_of, d.slot, d.cell_start, d.perm);
+    scatter_body(bx, d.n, d.cell_of, d.slot, d.sx_of, d.cell_start, d.skey);
 }
 
 __global__ void __launch_bounds__(TPB) k_sort_cells_b(const RepDev* __restrict__ R, const int* __restrict__ off,
@@ -240,7 +324,7 @@ __global__ void __launch_bounds__(TPB) k_sort_cells_b(const RepDev* __restrict__
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    sort_cells_body(bx, d.ncells, d.cell_start, d.sx_of, d.perm);
+    sort_cells_body(bx, d.ncells, d.cell_start, d.skey, d.perm);
 }
 
 __global__ void __launch_bounds__(TPB) k_gather_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
@@ -264,20 +348,30 @@ void launch_quantize_count(rbe_ctx* ctx, int n, const double* pos, const double*
 void launch_scan(rbe_ctx* ctx, cudaStream_t st)
 {
     prof_begin(ctx, RBE_K_SCAN, st);
-    k_scan<<<1, 1024, 0, st>>>(ctx->ncells, ctx->cell_count, ctx->cell_start);
+    const long m = ctx->ncells;
+    const long ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
+    if (ntiles <= 2 || !ctx->scan_tmp) {
+        k_scan<<<1, 1024, 0, st>>>(m, ctx->cell_count, ctx->cell_start);
+    } else {
+        k_scan_tiles<<<(unsigned)ntiles, TPB, 0, st>>>(m, ctx->cell_count, ctx->scan_tmp);
+        k_scan_top<<<1, TPB, 0, st>>>((int)ntiles, ctx->scan_tmp, m, ctx->cell_start);
+        k_scan_apply<<<(unsigned)ntiles, TPB, 0, st>>>(m, ctx->cell_count, ctx->scan_tmp, ctx->cell_start);
+    }
     prof_end(ctx, RBE_K_SCAN, st);
 }
+
+long scan_tiles(long ncells) { return (ncells + SCAN_TILE - 1) / SCAN_TILE; }
 
 void launch_scatter_sort_gather(rbe_ctx* ctx, int n, const double* pos, const double* q, const int32_t* type,
                                 const int32_t* mol, cudaStream_t st)
 {
     int g = (n + TPB - 1) / TPB;
     prof_begin(ctx, RBE_K_SCATTER, st);
-    k_scatter<<<g, TPB, 0, st>>>(n, ctx->cell_of, ctx->slot, ctx->cell_start, ctx->perm);
+    k_scatter<<<g, TPB, 0, st>>>(n, ctx->cell_of, ctx->slot, ctx->sx_of, ctx->cell_start, ctx->skey);
     prof_end(ctx, RBE_K_SCATTER, st);
     prof_begin(ctx, RBE_K_SORT, st);
     k_sort_cells<<<(unsigned)((ctx->ncells + TPB - 1) / TPB), TPB, 0, st>>>(ctx->ncells, ctx->cell_start,
-                                                                            ctx->sx_of, ctx->perm);
+                                                                            ctx->skey, ctx->perm);
     prof_end(ctx, RBE_K_SORT, st);
     prof_begin(ctx, RBE_K_GATHER, st);
     k_gather<<<g, TPB, 0, st>>>(n, ctx->perm, pos, q, type, mol, ctx->c, ctx->s4, ctx->f4, ctx->p4, ctx->tm,

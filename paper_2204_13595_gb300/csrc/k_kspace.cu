@@ -27,6 +27,7 @@ namespace {
 
 constexpr int TILE = 256;
 constexpr int TPB = 256;
+constexpr int FIN_TPB = 256;   // threads of the finalisation block (both paths: same reduction order)
 
 __device__ __forceinline__ int inv_cdf(uint64_t u, const uint64_t* __restrict__ T, int M)
 {
@@ -185,18 +186,24 @@ __global__ void k_rho(int n, int chunk, RbeConsts c, const uint4* __restrict__ s
 
 // Fixed-order sum over blocks; per-k energy and virial terms of the
 // reweighted reciprocal sum (E_k = sum_l c_l/2 |rho_l|^2).
+// One warp per k: lane t sums the partials of blocks t, t + 32, ... in order,
+// then a fixed butterfly; lane 0's result is used (a fixed order).
 __device__ __forceinline__ void rho_sum_body(int bx, int nblk, const RbeConsts& c, const double2* __restrict__ part,
                                              const double4_32a* __restrict__ kv, double2* __restrict__ rho,
                                              double* __restrict__ kterms)
 {
-    int l = bx * TPB + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int l = bx * (TPB / 32) + (threadIdx.x >> 5);
     if (l >= c.P) return;
     double re = 0.0, im = 0.0;
-    for (int b = 0; b < nblk; ++b) {
+    for (int b = lane; b < nblk; b += 32) {
         double2 v = part[(size_t)b * c.P + l];
         re += v.x;
         im += v.y;
     }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane != 0) return;
     rho[l] = make_double2(re, im);
     double4_32a k = kv[l];
     double k2 = k.x * k.x + k.y * k.y + k.z * k.z;
@@ -277,24 +284,30 @@ __global__ void __launch_bounds__(TPB) k_bonded(int nmol, const double* __restri
 }
 
 // Fixed-order block reduction of a strided column.
+// Fixed-order block sum of one value per thread: a butterfly inside each warp
+// (lane 0's result), then the warp results in warp order, read by every
+// thread in the same order.  sh holds at least blockDim/32 doubles.
+__device__ double block_reduce(double v, double* sh)
+{
+    v = warp_sum(v);
+    __syncthreads();                      // earlier readers of sh are done
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
+    return r;
+}
+
 __device__ double block_sum_col(const double* __restrict__ src, int nrow, int stride, int col, double* sh)
 {
     double s = 0.0;
     for (int r = threadIdx.x; r < nrow; r += blockDim.x) s += src[(size_t)r * stride + col];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    double r = sh[0];
-    __syncthreads();
-    return r;
+    return block_reduce(s, sh);
 }
 
 // Fixed-order block reduction of the rows of a row-major [nrow][NC] table:
 // thread t sums rows t, t + blockDim, ... (each row one contiguous read),
-// then a tree over the threads, column by column.
+// then a block reduction, column by column.
 template <int NC>
 __device__ void block_sum_rows(const double* __restrict__ src, int nrow, double* out, double* sh)
 {
@@ -306,16 +319,7 @@ __device__ void block_sum_rows(const double* __restrict__ src, int nrow, double*
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] += row[c];
     }
-    for (int c = 0; c < NC; ++c) {
-        sh[threadIdx.x] = acc[c];
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-            __syncthreads();
-        }
-        out[c] = sh[0];
-        __syncthreads();
-    }
+    for (int c = 0; c < NC; ++c) out[c] = block_reduce(acc[c], sh);
 }
 
 // totals: E[0..5], W[6..11], corr[12..14]
@@ -324,7 +328,7 @@ __device__ __forceinline__ void finalize_body(int n, const RbeConsts& c, const d
                                               const double* __restrict__ kterms, const double* __restrict__ part_bond,
                                               int grid_bond, double* __restrict__ totals, int* __restrict__ status)
 {
-    __shared__ double sh[TPB];
+    __shared__ double sh[FIN_TPB];
     double r[RBE_NPART_RBL];
     block_sum_rows<RBE_NPART_RBL>(part_rbl, grid_rbl, r, sh);
     double qs[RBE_NPART_Q];
@@ -348,7 +352,7 @@ __device__ __forceinline__ void finalize_body(int n, const RbeConsts& c, const d
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_finalize(int n, RbeConsts c, const double* __restrict__ part_rbl, int grid_rbl,
+__global__ void __launch_bounds__(FIN_TPB) k_finalize(int n, RbeConsts c, const double* __restrict__ part_rbl, int grid_rbl,
                                                   const double* __restrict__ part_q, int grid_q,
                                                   const double* __restrict__ kterms,
                                                   const double* __restrict__ part_bond, int grid_bond,
@@ -545,9 +549,9 @@ __global__ void __launch_bounds__(TPB) k_trace(const double* __restrict__ part, 
 }
 
 // ---- batched forms: one launch over all replicas of a plan -----------------
-// Per-replica grids: BK_KS = ceil(P / TPB) (sampling and the rho sum),
-// BK_RHO = grid_rho, BK_BOND = grid_bond (0 without bonds), BK_ATOMS =
-// ceil(n / TPB), BK_Q = grid_q, BK_REP = 1.
+// Per-replica grids: BK_KS = ceil(P / TPB) (sampling), BK_RS = ceil(P / 8)
+// (rho sum, a warp per k), BK_RHO = grid_rho, BK_BOND = grid_bond (0 without
+// bonds), BK_ATOMS = ceil(n / TPB), BK_Q = grid_q, BK_REP = 1.
 
 __global__ void k_ctl_b(BatchCtl* ctl, int op, unsigned long long step0, double* trace, int nsteps)
 {
@@ -578,7 +582,7 @@ __global__ void k_rho_b(const RepDev* __restrict__ R, const int* __restrict__ of
     rho_body<MIXED>(bx, d.n, d.rho_chunk, d.c, d.s4, d.p4, d.km, d.rho_part);
 }
 
-__global__ void __launch_bounds__(TPB) k_rho_sum_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
+__global__ void __launch_bounds__(TPB) k_rho_sum_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)  // BK_RS
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
@@ -592,7 +596,7 @@ __global__ void __launch_bounds__(TPB) k_bonded_b(const RepDev* __restrict__ R, 
     bonded_body(bx, nbx, d.nmol, d.pos, d.c, d.kb, d.r0, d.kth, d.th0, d.F_bond, d.part_bond);
 }
 
-__global__ void __launch_bounds__(TPB) k_finalize_b(const RepDev* __restrict__ R)
+__global__ void __launch_bounds__(FIN_TPB) k_finalize_b(const RepDev* __restrict__ R)
 {
     const RepDev& d = R[blockIdx.x];
     finalize_body(d.n, d.c, d.part_rbl, d.grid_rbl, d.part_q, d.grid_q, d.totals + 32, d.part_bond, d.grid_bond,
@@ -671,7 +675,8 @@ void launch_rho(rbe_ctx* ctx, int n, cudaStream_t st)
     prof_end(ctx, RBE_K_RHO, st);
     prof_begin(ctx, RBE_K_RHOSUM, st);
     double* kterms = ctx->totals + 32;
-    k_rho_sum<<<(P + TPB - 1) / TPB, TPB, 0, st>>>(ctx->grid_rho, ctx->c, ctx->rho_part, ctx->kv, ctx->rho, kterms);
+    k_rho_sum<<<(P + TPB / 32 - 1) / (TPB / 32), TPB, 0, st>>>(ctx->grid_rho, ctx->c, ctx->rho_part, ctx->kv, ctx->rho,
+                                                                kterms);
     prof_end(ctx, RBE_K_RHOSUM, st);
 }
 
@@ -687,7 +692,7 @@ void launch_bonded(rbe_ctx* ctx, int n, const double* pos, cudaStream_t st)
 void launch_finalize(rbe_ctx* ctx, int n, cudaStream_t st)
 {
     prof_begin(ctx, RBE_K_FINAL, st);
-    k_finalize<<<1, TPB, 0, st>>>(n, ctx->c, ctx->part_rbl, ctx->grid_rbl, ctx->part_q, ctx->grid_q, ctx->totals + 32,
+    k_finalize<<<1, FIN_TPB, 0, st>>>(n, ctx->c, ctx->part_rbl, ctx->grid_rbl, ctx->part_q, ctx->grid_q, ctx->totals + 32,
                                   ctx->part_bond, ctx->n_wmol > 0 ? ctx->grid_bond : 0, ctx->totals, ctx->status);
     prof_end(ctx, RBE_K_FINAL, st);
 }
@@ -749,14 +754,14 @@ void launch_kspace_pre_batch(const BatchPlan& bp, cudaStream_t st)
         k_rho_b<true><<<bp.total[BK_RHO], bp.rho_threads, 0, st>>>(bp.rep, bp.off[BK_RHO], nr);
     else
         k_rho_b<false><<<bp.total[BK_RHO], bp.rho_threads, 0, st>>>(bp.rep, bp.off[BK_RHO], nr);
-    k_rho_sum_b<<<bp.total[BK_KS], TPB, 0, st>>>(bp.rep, bp.off[BK_KS], nr);
+    k_rho_sum_b<<<bp.total[BK_RS], TPB, 0, st>>>(bp.rep, bp.off[BK_RS], nr);
     if (bp.total[BK_BOND] > 0) k_bonded_b<<<bp.total[BK_BOND], TPB, 0, st>>>(bp.rep, bp.off[BK_BOND], nr);
 }
 
 void launch_kspace_post_batch(const BatchPlan& bp, cudaStream_t st)
 {
     const int nr = bp.nrep;
-    k_finalize_b<<<nr, TPB, 0, st>>>(bp.rep);
+    k_finalize_b<<<nr, FIN_TPB, 0, st>>>(bp.rep);
     if (bp.precision == RBE_MIXED)
         k_kforce_b<true><<<bp.total[BK_ATOMS], TPB, 0, st>>>(bp.rep, bp.off[BK_ATOMS], nr);
     else

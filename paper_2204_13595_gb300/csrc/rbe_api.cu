@@ -122,7 +122,7 @@ void refresh_consts(rbe_ctx* ctx)
 
 void free_dev(rbe_ctx* ctx)
 {
-    void* ptrs[] = {ctx->sx_of, ctx->F_lang, ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
+    void* ptrs[] = {ctx->skey, ctx->scan_tmp, ctx->sx_of, ctx->F_lang, ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
                     ctx->F_real, ctx->F_bond, ctx->part_rbl, ctx->part_q, ctx->part_bond, ctx->kT, ctx->km, ctx->kv,
                     ctx->rho_part, ctx->rho, ctx->totals, ctx->status, ctx->lj, ctx->dbg_ncore, ctx->dbg_nshell,
                     ctx->dbg_core, ctx->dbg_batch, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
@@ -139,7 +139,7 @@ void free_dev(rbe_ctx* ctx)
     ctx->h_q = nullptr; ctx->h_type = nullptr; ctx->h_mol = nullptr; ctx->h_F = nullptr; ctx->ke_part = nullptr;
     ctx->vs = nullptr; ctx->gq_own = nullptr; ctx->gq_tr = nullptr; ctx->part_lj = nullptr; ctx->part_v = nullptr;
     ctx->tau_part = nullptr; ctx->tau = nullptr; ctx->kpool_buf = nullptr; ctx->kpool_dirty = 1;
-    ctx->F_lang = nullptr; ctx->F_lang_cap = 0; ctx->sx_of = nullptr;
+    ctx->F_lang = nullptr; ctx->F_lang_cap = 0; ctx->sx_of = nullptr; ctx->scan_tmp = nullptr; ctx->skey = nullptr;
     ctx->n_cap = 0; ctx->dbg_n_cap = 0; ctx->h_cap = 0;
     for (int k = 0; k < 24; ++k) ctx->cap_atoms[k] = 0;
     for (int k = 0; k < 8; ++k) ctx->cap_adj[k] = 0;
@@ -256,6 +256,7 @@ int ensure(rbe_ctx* ctx, int n)
         if ((rc = dev_alloc(ctx, &ctx->lj, 1))) return rc;
         if ((rc = dev_alloc(ctx, &ctx->cell_count, ctx->ncells + 1))) return rc;
         if ((rc = dev_alloc(ctx, &ctx->cell_start, ctx->ncells + 1))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->scan_tmp, (size_t)scan_tiles(ctx->ncells) + 1))) return rc;
         ctx->lj_dirty = 1;
     }
     if (ctx->lj_dirty) {
@@ -348,6 +349,7 @@ int ensure(rbe_ctx* ctx, int n)
     if ((rc = grow(ctx, &ctx->cell_of, &ctx->cap_atoms[4], n))) return rc;
     if ((rc = grow(ctx, &ctx->slot, &ctx->cap_atoms[5], n))) return rc;
     if ((rc = grow(ctx, &ctx->sx_of, &ctx->cap_atoms[20], n))) return rc;
+    if ((rc = grow(ctx, &ctx->skey, &ctx->cap_atoms[21], n))) return rc;
     if ((rc = grow(ctx, &ctx->F_real, &ctx->cap_atoms[6], 3 * (size_t)n))) return rc;
     if ((rc = grow(ctx, &ctx->part_rbl, &ctx->cap_atoms[7], (size_t)ctx->grid_rbl * RBE_NPART_RBL))) return rc;
     if ((rc = grow(ctx, &ctx->part_q, &ctx->cap_atoms[8], (size_t)ctx->grid_q * RBE_NPART_Q))) return rc;

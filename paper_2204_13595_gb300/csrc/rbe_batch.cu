@@ -176,7 +176,7 @@ int build_plan(rbe_batch* b)
         d.pos = b->pos[r]; d.vel = b->vel[r]; d.mass = b->mass[r]; d.q = b->q[r];
         d.type = b->type[r]; d.mol = b->mol[r]; d.F = b->F[r];
         d.cell_count = ctx->cell_count; d.cell_start = ctx->cell_start; d.cell_of = ctx->cell_of;
-        d.slot = ctx->slot; d.perm = ctx->perm; d.sx_of = ctx->sx_of;
+        d.slot = ctx->slot; d.perm = ctx->perm; d.sx_of = ctx->sx_of; d.skey = ctx->skey;
         d.s4 = ctx->s4; d.f4 = ctx->f4; d.p4 = ctx->p4; d.tm = ctx->tm;
         d.part_q = ctx->part_q; d.part_rbl = ctx->part_rbl; d.part_bond = ctx->part_bond; d.ke_part = ctx->ke_part;
         d.kT = ctx->kT; d.km = ctx->km; d.kv = ctx->kv; d.rho_part = ctx->rho_part; d.rho = ctx->rho;
@@ -201,6 +201,7 @@ int build_plan(rbe_batch* b)
         cnt[BK_RHO][r] = ctx->grid_rho;
         cnt[BK_BOND][r] = d.grid_bond;
         cnt[BK_REP][r] = 1;
+        cnt[BK_RS][r] = ceil_div(ctx->c.P, 8);         // rho sum: one warp per k
         if (d.grid_bond > 0) bonds = true;
         const int P = ctx->c.P;
         const int th = ((P < 1024 ? P : 1024) + 31) / 32 * 32;

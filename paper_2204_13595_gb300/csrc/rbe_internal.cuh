@@ -106,8 +106,10 @@ struct rbe_ctx {
     int* cell_of;
     int* slot;
     uint32_t* sx_of;     // [n] fixed-point x code, caller order (in-cell sort key)
+    unsigned long long* skey;   // [n] in-cell sort keys (x code << 32 | index), cell ranges
     int* cell_count;     // [ncells + 1]
     int* cell_start;     // [ncells + 1]
+    int* scan_tmp;       // [scan tiles] tile sums / offsets of the cell scan
     double* F_real;      // [3n] sorted (FP32 [3n] on the mixed path)
     double* F_bond;      // [3n] caller order
     double* part_rbl;    // [grid_rbl * 12]
@@ -181,6 +183,7 @@ struct RepDev {
     int* cell_of;
     int* slot;
     uint32_t* sx_of;
+    unsigned long long* skey;
     int* perm;
     uint4* s4;
     float4* f4;
@@ -214,7 +217,7 @@ struct BatchCtl {
 };
 
 // Stages of a batched step, each with its own per-replica block counts.
-enum { BK_CELLS = 0, BK_ATOMS, BK_Q, BK_KS, BK_RHO, BK_BOND, BK_REP, BK_COUNT };
+enum { BK_CELLS = 0, BK_ATOMS, BK_Q, BK_KS, BK_RHO, BK_BOND, BK_REP, BK_RS, BK_COUNT };
 
 struct BatchPlan {
     int nrep;
@@ -314,6 +317,7 @@ void prof_end(rbe_ctx* ctx, int kid, cudaStream_t st);
 // cells / sort (k_cells.cu)
 void launch_quantize_count(rbe_ctx* ctx, int n, const double* pos, const double* q, cudaStream_t st);
 void launch_scan(rbe_ctx* ctx, cudaStream_t st);
+long scan_tiles(long ncells);
 void launch_scatter_sort_gather(rbe_ctx* ctx, int n, const double* pos, const double* q,
                                 const int32_t* type, const int32_t* mol, cudaStream_t st);
 // pair kernel (k_rbl.cu)
