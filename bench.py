@@ -50,7 +50,54 @@ L2_FLUSH_BYTES = 512 << 20
 RBL_OPS_PER_ATOM = 420 * 9 + 72.5 * 45
 SM_COUNT = 152
 LANES_PER_SM = 128
+SFU_LANES_PER_SM = 16
 SM_MAX_MHZ = 2070.0
+HBM_FALLBACK_GBS = 6800.0
+
+
+def _kernel_roofline(prof, n, P, ncells, peaks_meas):
+    """Roofline fraction of every kernel of the mixed step (per-launch CUDA-event
+    times from the library's profiler).  Denominators: HBM from MEASURED_PEAKS.json
+    if present, else the recipe's fallback; the FP32 lane and special-function
+    peaks derived from the unit counts and the maximum SM clock."""
+    peaks, src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    lane = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6
+    sfu = SM_COUNT * SFU_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    work = {   # algorithmic bytes or operations per launch
+        "quantize": ("hbm", 48.0 * n),                       # pos, q in; cell, slot, x code out
+        "scan": ("hbm", 12.0 * ncells),                      # counts read twice, starts written
+        "scatter": ("hbm", 24.0 * n),                        # cell, slot, x code, start in; key out
+        "sort": ("hbm", 20.0 * n + 8.0 * ncells),            # keys read and written, perm out
+        "gather": ("hbm", 116.0 * n),                        # perm, pos, q, type, mol in; s4 f4 p4 tm out
+        "rho": ("sfu", 2.0 * n * P),                         # one FP32 sincos per (atom, k)
+        "kforce": ("sfu", 2.0 * n * P),
+        "rbl": ("alu", RBL_OPS_PER_ATOM * n),
+    }
+    out = {}
+    for k, (bound, w) in work.items():
+        ms, cnt = prof.get(k, (0.0, 0))
+        if not cnt:
+            continue
+        t = ms / cnt * 1e-3
+        if bound == "hbm":
+            a = w / t / 1e9
+            out[k] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                      "peak_source": f"{src} HBM"}
+        elif bound == "sfu":
+            a = w / t / 1e12
+            out[k] = {"bound": "sfu", "achieved": a, "peak": sfu / 1e12, "unit": "Top/s", "frac": a / (sfu / 1e12),
+                      "peak_source": "derived: 152 SMs x 16 SFU lanes x 2070 MHz"}
+        else:
+            a = w / t / 1e12
+            out[k] = {"bound": "alu", "achieved": a, "peak": lane / 1e12, "unit": "Top/s", "frac": a / (lane / 1e12),
+                      "peak_source": "derived: 152 SMs x 128 lanes x 2070 MHz"}
+        out[k]["avg_launch_ms"] = t * 1e3
+    for k in ("rhosum", "finalize", "ksample"):
+        ms, cnt = prof.get(k, (0.0, 0))
+        if cnt:
+            out[k] = {"bound": "latency", "avg_launch_ms": ms / cnt}
+    return out
 
 
 def _dist():
@@ -306,6 +353,13 @@ def run_ours(args):
     f64.forces(123, pos, q, typ, mol, F)
     err = float(torch.sqrt(((Fm - F) ** 2).mean()) / torch.sqrt((F ** 2).mean()))
 
+    # measured pipe and memory throughput of this GPU (context for the derived peaks)
+    meas = {}
+    for kind in ("ffma", "dfma", "sfu", "alu", "copy"):
+        try:
+            meas[kind] = rbe.peak_probe(kind)
+        except Exception as e:        # report, do not fail the bench
+            meas[kind] = f"unavailable: {e}"
     clocks_proc = _clock_sampler() if rank == 0 else None
     ms_mixed, prof, launches = timed(mixed, args.steps, args.warmup, profile=True)
     ms_f64, _, _ = timed(f64, max(3, min(args.steps, 10)), max(3, min(args.warmup, 3)))
@@ -367,6 +421,11 @@ def run_ours(args):
                      "traffic": traffic, "peak_source": "derived: 152 SMs x 128 lanes x 2070 MHz, 1 op/lane/clk",
                      "avg_launch_ms": rbl_avg_s * 1e3},
         "kernel_share": kshare,
+        "kernel_roofline": _kernel_roofline(prof, s.n, s.P, mixed.info()["n_cell"] ** 3, meas),
+        "measured_pipes": {
+            "ffma_per_s": meas.get("ffma"), "dfma_per_s": meas.get("dfma"), "sfu_sin_per_s": meas.get("sfu"),
+            "int_ops_per_s": meas.get("alu"), "copy_bytes_per_s": meas.get("copy"),
+            "note": "rbe_peak_probe in this run (best of 3 launches): context for the derived peaks"},
         "cpu_baseline": {"value": 1.0 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "one full FP64 oracle force evaluation of the same 1.2M-atom system"},
         "e2e": {"value": replicas.throughput(ws, 1, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

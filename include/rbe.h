@@ -236,6 +236,22 @@ int rbe_rho_noalloc(int n, const double* pos, const double* q, double box_L, int
  * idle). */
 void rbe_destroy(rbe_ctx* ctx);
 
+/* Throughput probes of the GPU's plain pipes and memory, the roofline
+ * denominators of kernels bound by arithmetic issue, the special-function unit
+ * or HBM.  kind: RBE_PROBE_FFMA (FP32 fused multiply-adds per second, one per
+ * lane), RBE_PROBE_DFMA (FP64 fused multiply-adds per second),
+ * RBE_PROBE_SFU (hardware sines per second), RBE_PROBE_ALU (32-bit integer
+ * shift/xor/add operations per second), RBE_PROBE_COPY (device-to-device copy
+ * bytes read + written per second, 2 GiB per launch).  Each is the best of
+ * three timed launches after a warm-up, on cuda_stream (the call waits).
+ * Allocates (and frees) a small sink, and 2 GiB for the copy probe. */
+#define RBE_PROBE_FFMA 0
+#define RBE_PROBE_DFMA 1
+#define RBE_PROBE_SFU  2
+#define RBE_PROBE_ALU  3
+#define RBE_PROBE_COPY 4
+int rbe_peak_probe(int kind, double* ops_per_s, void* cuda_stream);
+
 /* Variants of the method (the paper leaves them open; defaults = base method).
  *
  * Shell batch (Algorithm 1, shell selection step): RBE_SHELL_FLOYD draws the

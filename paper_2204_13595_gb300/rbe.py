@@ -27,7 +27,8 @@ EXPORTS = ["rbe_create", "rbe_set_coulomb", "rbe_set_lj", "rbe_set_precision", "
            "rbe_destroy", "rbe_rho_noalloc", "rbe_adjoint", "rbe_set_rbl_tiling", "rbe_batch_create",
            "rbe_batch_bind", "rbe_batch_forces", "rbe_batch_step", "rbe_batch_autotune", "rbe_batch_info",
            "rbe_batch_sync_status", "rbe_batch_last_error", "rbe_batch_destroy", "rbe_set_shell_sampling",
-           "rbe_set_lj_cutoff", "rbe_set_kpool", "rbe_set_langevin"]
+           "rbe_set_lj_cutoff", "rbe_set_kpool", "rbe_set_langevin", "rbe_peak_probe"]
+PROBES = {"ffma": 0, "dfma": 1, "sfu": 2, "alu": 3, "copy": 4}
 SHELL_FLOYD, SHELL_REPLACE = 0, 1
 WCA_FACTOR = 2.0 ** (1.0 / 6.0)
 ELIMIT = -8
@@ -71,6 +72,7 @@ def load(path: str = LIB_PATH):
     L.rbe_set_lj_cutoff.argtypes = [vp, d]
     L.rbe_set_kpool.argtypes = [vp, i, i]
     L.rbe_set_langevin.argtypes = [vp, d, d]
+    L.rbe_peak_probe.argtypes = [i, ctypes.POINTER(d), vp]
     L.rbe_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
     L.rbe_batch_bind.argtypes = [vp, ctypes.POINTER(i)] + [ctypes.POINTER(vp)] * 7 + [ctypes.POINTER(d)] * 2
     L.rbe_batch_forces.argtypes = [vp, u64, vp, vp]
@@ -109,6 +111,17 @@ def _stream(stream):
         return stream if isinstance(stream, int) else stream.cuda_stream
     import torch
     return torch.cuda.current_stream().cuda_stream
+
+
+def peak_probe(kind, stream=None):
+    """rbe_peak_probe: measured throughput of a pipe ('ffma', 'dfma', 'sfu',
+    'alu': operations per second) or of device memory ('copy': bytes per
+    second)."""
+    out = ctypes.c_double()
+    rc = lib().rbe_peak_probe(PROBES[kind], ctypes.byref(out), _stream(stream))
+    if rc != OK:
+        raise RbeError(rc, f"rbe_peak_probe({kind}) failed")
+    return out.value
 
 
 def rho_noalloc(pos, q, box_L, m, rho, stream=None):
