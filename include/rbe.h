@@ -292,6 +292,19 @@ int rbe_set_kpool(rbe_ctx* ctx, int size, int burn_in);
  * F returned by rbe_step stays the conservative force. */
 int rbe_set_langevin(rbe_ctx* ctx, double kT, double tau);
 
+/* Resume support for thermostatted runs.  The state of a velocity-Verlet run
+ * at step s is (pos, vel, F, s) and, with the thermostat, the Langevin force
+ * F^L made at step s, which the first half kick of step s + 1 uses.  An
+ * rbe_step (or rbe_batch_step) call that starts at the step where the
+ * context's previous run ended reuses the held F^L, so a run split into
+ * several calls equals one call bit for bit; a call that starts anywhere else
+ * makes F^L from the entry velocities.  For a checkpoint, get copies the held
+ * F^L ([n][3], any host or device pointer) and its step (RBE_EINVAL if none is
+ * held for n atoms); set installs them in a context (e.g. a fresh one after a
+ * restart), so that resuming at that step is exact. */
+int rbe_get_langevin_force(rbe_ctx* ctx, int n, double* FL, uint64_t* step);
+int rbe_set_langevin_force(rbe_ctx* ctx, int n, const double* FL, uint64_t step);
+
 /* Work decomposition of the RBL pair kernel (Sec. 2.3 stencil walk): a work
  * unit is a run of cells along x holding about atoms_per_unit atoms (0: 48;
  * shared memory caps the width); the kernel's grid has

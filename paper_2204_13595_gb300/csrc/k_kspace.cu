@@ -620,12 +620,15 @@ __global__ void __launch_bounds__(TPB) k_vv_b(const RepDev* __restrict__ R, cons
     vv_body(bx, d.n, d.pos, d.vel, d.mass, d.F, d.FL, 0.5 * d.dt * d.accel, d.dt, drift);
 }
 
+// mask (may be null: every replica): replicas whose force is (re)computed
 __global__ void __launch_bounds__(TPB) k_langevin_b(const RepDev* __restrict__ R, const int* __restrict__ off,
-                                                    int nrep, const BatchCtl* __restrict__ ctl)
+                                                    int nrep, const BatchCtl* __restrict__ ctl,
+                                                    const int* __restrict__ mask)
 {
     int bx, nbx;
-    const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    if (!d.FL) return;
+    const int r = rep_of_block(off, nrep, blockIdx.x, bx, nbx);
+    const RepDev& d = R[r];
+    if (!d.FL || (mask && !mask[r])) return;
     langevin_body(bx, d.n, d.vel, d.mass, d.c.seed, ctl->step, d.lang_c1, d.lang_c2, d.FL);
 }
 
@@ -773,9 +776,9 @@ void launch_vv_batch(const BatchPlan& bp, int drift, cudaStream_t st)
     k_vv_b<<<bp.total[BK_ATOMS], TPB, 0, st>>>(bp.rep, bp.off[BK_ATOMS], bp.nrep, drift);
 }
 
-void launch_langevin_batch(const BatchPlan& bp, cudaStream_t st)
+void launch_langevin_batch(const BatchPlan& bp, const int* mask, cudaStream_t st)
 {
-    k_langevin_b<<<bp.total[BK_ATOMS], TPB, 0, st>>>(bp.rep, bp.off[BK_ATOMS], bp.nrep, bp.ctl);
+    k_langevin_b<<<bp.total[BK_ATOMS], TPB, 0, st>>>(bp.rep, bp.off[BK_ATOMS], bp.nrep, bp.ctl, mask);
 }
 
 void launch_ke_trace_batch(const BatchPlan& bp, cudaStream_t st)

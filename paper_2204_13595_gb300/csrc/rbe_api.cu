@@ -17,6 +17,8 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rbe_internal.cuh"
 
 namespace {
@@ -391,7 +393,13 @@ int ctx_prepare(rbe_ctx* ctx, int n)
     return ensure(ctx, n);
 }
 
-int ctx_grow_lang(rbe_ctx* ctx, int n) { return grow(ctx, &ctx->F_lang, &ctx->F_lang_cap, 3 * (size_t)n); }
+int ctx_grow_lang(rbe_ctx* ctx, int n)
+{
+    double* old = ctx->F_lang;
+    int rc = grow(ctx, &ctx->F_lang, &ctx->F_lang_cap, 3 * (size_t)n);
+    if (ctx->F_lang != old) ctx->lang_valid = 0;      // a new buffer holds no force
+    return rc;
+}
 
 namespace {
 
@@ -441,11 +449,16 @@ int status_code(int bits)
 // ---------------------------------------------------------------------------
 // profiling helpers
 // ---------------------------------------------------------------------------
+const char* const KERNEL_NAMES[RBE_NKERNELS] = {"quantize", "scan", "scatter", "sort", "gather", "ksample", "rho",
+                                                "rhosum", "rbl", "bonded", "finalize", "kforce", "vv", "misc"};
+
+// With profiling on, every launch is bracketed by CUDA events (timing) and an
+// NVTX range named after the kernel (for timeline tools).
 void prof_begin(rbe_ctx* ctx, int kid, cudaStream_t st)
 {
-    (void)kid;
     ctx->last_launches++;
     if (!ctx->profiling) return;
+    nvtxRangePushA(KERNEL_NAMES[kid]);
     ProfState* ps = (ProfState*)ctx->prof;
     cudaEvent_t a;
     if (!ps->pool.empty()) { a = ps->pool.back(); ps->pool.pop_back(); }
@@ -463,6 +476,7 @@ void prof_end(rbe_ctx* ctx, int kid, cudaStream_t st)
     else cudaEventCreate(&b);
     cudaEventRecord(b, st);
     ps->recs.push_back({kid, ps->pending_a, b});
+    nvtxRangePop();
 }
 
 // ---------------------------------------------------------------------------
@@ -587,6 +601,30 @@ int rbe_set_langevin(rbe_ctx* ctx, double kT, double tau)
     if (!ctx || !isfinite(kT) || !isfinite(tau) || kT < 0.0) return RBE_EINVAL;
     ctx->lang_kT = kT;
     ctx->lang_tau = tau > 0.0 ? tau : 0.0;
+    ctx->lang_valid = 0;
+    return RBE_OK;
+}
+
+int rbe_get_langevin_force(rbe_ctx* ctx, int n, double* FL, uint64_t* step)
+{
+    if (!ctx || !FL || !step || n < 1) return RBE_EINVAL;
+    if (!ctx->lang_valid || ctx->lang_n != n || !ctx->F_lang)
+        return set_err(ctx, RBE_EINVAL, "no Langevin force for %d atoms is held", n);
+    CUDA_TRY(ctx, cudaMemcpy(FL, ctx->F_lang, sizeof(double) * 3 * (size_t)n, cudaMemcpyDefault));
+    *step = ctx->lang_step;
+    return RBE_OK;
+}
+
+int rbe_set_langevin_force(rbe_ctx* ctx, int n, const double* FL, uint64_t step)
+{
+    if (!ctx || !FL || n < 1) return RBE_EINVAL;
+    int rc = ensure(ctx, n);
+    if (rc) return rc;
+    if ((rc = ctx_grow_lang(ctx, n))) return rc;
+    CUDA_TRY(ctx, cudaMemcpy(ctx->F_lang, FL, sizeof(double) * 3 * (size_t)n, cudaMemcpyDefault));
+    ctx->lang_step = step;
+    ctx->lang_valid = 1;
+    ctx->lang_n = n;
     return RBE_OK;
 }
 
@@ -672,10 +710,13 @@ int rbe_step(rbe_ctx* ctx, uint64_t step0, int nsteps, double dt, double accel, 
     if (rc) return rc;
     // Langevin thermostat: F^L from the entry velocities at step0, then after
     // every force evaluation from the half-kicked velocities
+    // (a call that starts where the context's previous run ended reuses that
+    // run's last F^L, so a run split into calls equals one call bit for bit)
     const bool lang = ctx->lang_tau > 0.0;
     if (lang) {
-        if ((rc = grow(ctx, &ctx->F_lang, &ctx->F_lang_cap, 3 * (size_t)n))) return rc;
-        launch_langevin(ctx, n, vel, mass, step0, dt, accel, st);
+        if ((rc = ctx_grow_lang(ctx, n))) return rc;
+        if (!(ctx->lang_valid && ctx->lang_step == step0 && ctx->lang_n == n))
+            launch_langevin(ctx, n, vel, mass, step0, dt, accel, st);
     }
     const double* FL = lang ? ctx->F_lang : nullptr;
     for (int k = 0; k < nsteps; ++k) {
@@ -685,6 +726,11 @@ int rbe_step(rbe_ctx* ctx, uint64_t step0, int nsteps, double dt, double accel, 
         if (lang) launch_langevin(ctx, n, vel, mass, step0 + (uint64_t)k + 1, dt, accel, st);
         launch_vv_kick_drift(ctx, n, pos, vel, mass, F, FL, dt, accel, 0, st);
         if (energy_trace) launch_ke_trace(ctx, n, vel, mass, accel, energy_trace + 2 * (size_t)k, st);
+    }
+    if (lang) {
+        ctx->lang_step = step0 + (uint64_t)nsteps;
+        ctx->lang_valid = 1;
+        ctx->lang_n = n;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(ctx, RBE_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));

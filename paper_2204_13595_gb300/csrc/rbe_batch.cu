@@ -46,6 +46,7 @@ struct rbe_batch {
     int2* d_tasks = nullptr;
     size_t tasks_cap = 0;
     BatchCtl* d_ctl = nullptr;
+    int* d_mask = nullptr;   // replicas whose Langevin force is made at entry
     BatchPlan plan{};
     int persistent = 1;      // pair kernel form (autotuned)
     bool lang = false;       // some replica runs the Langevin thermostat
@@ -97,10 +98,11 @@ void drop_graph(rbe_batch* b)
 void free_plan(rbe_batch* b)
 {
     drop_graph(b);
-    void* ptrs[] = {b->d_rep, b->d_rbl, b->d_off, b->d_tasks, b->d_ctl};
+    void* ptrs[] = {b->d_rep, b->d_rbl, b->d_off, b->d_tasks, b->d_ctl, b->d_mask};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     b->d_rep = nullptr; b->d_rbl = nullptr; b->d_off = nullptr; b->d_tasks = nullptr; b->d_ctl = nullptr;
+    b->d_mask = nullptr;
     b->tasks_cap = 0;
 }
 
@@ -303,7 +305,7 @@ int ensure_graph(rbe_batch* b)
     launch_vv_batch(p, 1, b->cap_stream);
     launch_ctl_batch(p, 1, 0, nullptr, 0, b->cap_stream);
     enqueue_forces(p, b->cap_stream);
-    if (b->lang) launch_langevin_batch(p, b->cap_stream);
+    if (b->lang) launch_langevin_batch(p, nullptr, b->cap_stream);
     launch_vv_batch(p, 0, b->cap_stream);
     launch_ke_trace_batch(p, b->cap_stream);
     cudaGraph_t g = nullptr;
@@ -445,8 +447,29 @@ int rbe_batch_step(rbe_batch* b, uint64_t step0, int nsteps, double* energy_trac
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     launch_ctl_batch(b->plan, 0, step0, energy_trace, nsteps, st);
-    if (b->lang) launch_langevin_batch(b->plan, st);     // F^L at entry (step0)
+    if (b->lang) {
+        // F^L at entry (step0) for the thermostatted replicas whose context does
+        // not already hold it from a run that ended at step0 (as rbe_step)
+        std::vector<int> mask(b->nrep, 0);
+        bool any = false;
+        for (int r = 0; r < b->nrep; ++r) {
+            const rbe_ctx* c = b->ctx[r];
+            mask[r] = (c->lang_tau > 0.0 && !(c->lang_valid && c->lang_step == step0 && c->lang_n == b->n[r])) ? 1 : 0;
+            any = any || mask[r];
+        }
+        if (any) {
+            if (!b->d_mask) BATCH_TRY(b, cudaMalloc((void**)&b->d_mask, sizeof(int) * b->nrep));
+            BATCH_TRY(b, cudaMemcpyAsync(b->d_mask, mask.data(), sizeof(int) * b->nrep, cudaMemcpyHostToDevice, st));
+            BATCH_TRY(b, cudaStreamSynchronize(st));      // mask is host memory of this call
+            launch_langevin_batch(b->plan, b->d_mask, st);
+        }
+    }
     for (int k = 0; k < nsteps; ++k) BATCH_TRY(b, cudaGraphLaunch(b->exec, st));
+    if (b->lang)
+        for (int r = 0; r < b->nrep; ++r) {
+            rbe_ctx* c = b->ctx[r];
+            if (c->lang_tau > 0.0) { c->lang_step = step0 + (uint64_t)nsteps; c->lang_valid = 1; c->lang_n = b->n[r]; }
+        }
     return launch_status(b);
 }
 

@@ -90,6 +90,8 @@ struct rbe_ctx {
     double lang_kT, lang_tau;   // Langevin thermostat (tau <= 0: off)
     double* F_lang;       // [3n] Langevin force, caller order
     size_t F_lang_cap;
+    uint64_t lang_step;   // step whose Langevin force F_lang holds (valid if lang_valid)
+    int lang_valid, lang_n;
     // water bonds
     int n_wmol;
     double kb, r0, kth, th0;
@@ -337,7 +339,7 @@ void launch_vv_kick_drift(rbe_ctx* ctx, int n, double* pos, double* vel, const d
                           const double* F, const double* FL, double dt, double accel, int drift, cudaStream_t st);
 void launch_langevin(rbe_ctx* ctx, int n, const double* vel, const double* mass, uint64_t s, double dt,
                      double accel, cudaStream_t st);
-void launch_langevin_batch(const BatchPlan& bp, cudaStream_t st);
+void launch_langevin_batch(const BatchPlan& bp, const int* mask, cudaStream_t st);
 void launch_ke_trace(rbe_ctx* ctx, int n, const double* vel, const double* mass, double accel,
                      double* trace_slot, cudaStream_t st);
 int rbl_smem_bytes(const rbe_ctx* ctx);

@@ -27,7 +27,8 @@ EXPORTS = ["rbe_create", "rbe_set_coulomb", "rbe_set_lj", "rbe_set_precision", "
            "rbe_destroy", "rbe_rho_noalloc", "rbe_adjoint", "rbe_set_rbl_tiling", "rbe_batch_create",
            "rbe_batch_bind", "rbe_batch_forces", "rbe_batch_step", "rbe_batch_autotune", "rbe_batch_info",
            "rbe_batch_sync_status", "rbe_batch_last_error", "rbe_batch_destroy", "rbe_set_shell_sampling",
-           "rbe_set_lj_cutoff", "rbe_set_kpool", "rbe_set_langevin", "rbe_peak_probe"]
+           "rbe_set_lj_cutoff", "rbe_set_kpool", "rbe_set_langevin", "rbe_peak_probe", "rbe_get_langevin_force",
+           "rbe_set_langevin_force"]
 PROBES = {"ffma": 0, "dfma": 1, "sfu": 2, "alu": 3, "copy": 4}
 SHELL_FLOYD, SHELL_REPLACE = 0, 1
 WCA_FACTOR = 2.0 ** (1.0 / 6.0)
@@ -73,6 +74,8 @@ def load(path: str = LIB_PATH):
     L.rbe_set_kpool.argtypes = [vp, i, i]
     L.rbe_set_langevin.argtypes = [vp, d, d]
     L.rbe_peak_probe.argtypes = [i, ctypes.POINTER(d), vp]
+    L.rbe_get_langevin_force.argtypes = [vp, i, vp, ctypes.POINTER(u64)]
+    L.rbe_set_langevin_force.argtypes = [vp, i, vp, u64]
     L.rbe_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
     L.rbe_batch_bind.argtypes = [vp, ctypes.POINTER(i)] + [ctypes.POINTER(vp)] * 7 + [ctypes.POINTER(d)] * 2
     L.rbe_batch_forces.argtypes = [vp, u64, vp, vp]
@@ -186,6 +189,17 @@ class Context:
     def set_langevin(self, kT, tau):
         """Langevin thermostat of rbe_step (tau <= 0: off)."""
         self._check(self.L.rbe_set_langevin(self.h, float(kT), float(tau)))
+
+    def get_langevin_force(self, n):
+        """The held Langevin force [n, 3] (host array) and its step (checkpoint)."""
+        FL = np.zeros((n, 3))
+        st = ctypes.c_uint64()
+        self._check(self.L.rbe_get_langevin_force(self.h, n, _ptr(FL), ctypes.byref(st)))
+        return FL, st.value
+
+    def set_langevin_force(self, FL, step):
+        FL = np.ascontiguousarray(FL, dtype=np.float64)
+        self._check(self.L.rbe_set_langevin_force(self.h, int(FL.shape[0]), _ptr(FL), int(step)))
 
     def set_rbl_tiling(self, atoms_per_unit=0, units_per_slot=0):
         self._check(self.L.rbe_set_rbl_tiling(self.h, int(atoms_per_unit), int(units_per_slot)))
