@@ -144,22 +144,27 @@ __device__ __forceinline__ unsigned long long d2_exact(uint4 a, uint4 b)
 __device__ __forceinline__ void trim_segment(const float4* __restrict__ src, int& b, int& e, int cnt_lo, int cnt_hi,
                                              bool one_cell, float xref, float H)
 {
+    // the lower cut (first x >= xref - H in the first cell) and the upper cut
+    // (first x > xref + H in the last cell) are independent searches, run
+    // together so that their shared-memory loads overlap
     const float lo_x = xref - H, hi_x = xref + H;
     int l = b, r = b + cnt_lo;
-    while (l < r) {
-        const int m = (l + r) >> 1;
-        if (src[m].x < lo_x) l = m + 1;
-        else r = m;
+    int l2 = one_cell ? b : e - cnt_hi, r2 = e;
+    while (l < r || l2 < r2) {
+        const int m = (l + r) >> 1, m2 = (l2 + r2) >> 1;
+        const float xa = l < r ? src[m].x : 0.f;
+        const float xb = l2 < r2 ? src[m2].x : 0.f;
+        if (l < r) {
+            if (xa < lo_x) l = m + 1;
+            else r = m;
+        }
+        if (l2 < r2) {
+            if (xb <= hi_x) l2 = m2 + 1;
+            else r2 = m2;
+        }
     }
-    const int nb = l;
-    int l2 = one_cell ? nb : e - cnt_hi, r2 = e;
-    while (l2 < r2) {
-        const int m = (l2 + r2) >> 1;
-        if (src[m].x <= hi_x) l2 = m + 1;
-        else r2 = m;
-    }
-    b = nb;
-    e = l2 < nb ? nb : l2;
+    b = l;
+    e = l2 < l ? l : l2;
 }
 
 // Classification of one canonical segment [beg, end) of the source array:
