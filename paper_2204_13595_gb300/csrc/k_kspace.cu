@@ -120,14 +120,40 @@ __global__ void k_kpool_build(uint64_t seed, int M, int K, int burn, const doubl
     }
 }
 
+// FP64 phase factor e^{i theta}, theta = k . x, from the exact 32-bit phase
+// ph = m . s mod 2^32 of the fixed-point coordinates (theta = 2 pi ph / 2^32
+// + k . delta, delta = x - s L / 2^32 the sub-quantum residual of the
+// position, |delta| < L 2^-32): a table of e^{2 pi i j / 4096} for the top 12
+// bits of ph times a Taylor polynomial of the rest, |x| < 2 pi / 4096 + |k|
+// |delta| < 1.6e-3 (cos to x^4, sin to x^5: the first omitted terms are below
+// 2e-20).  About half the FP64 work of a general sincos.
+__device__ __forceinline__ void cis_fp64(uint32_t ph, double dk, const double2* __restrict__ tab, double& cs,
+                                         double& sn)
+{
+    const double2 e = __ldg(tab + (ph >> 20));
+    const double x = fma((double)(ph & 0xFFFFFu), 6.283185307179586 * 2.3283064365386963e-10, dk);
+    const double x2 = x * x;
+    const double c = fma(x2, fma(x2, 1.0 / 24.0, -0.5), 1.0);
+    const double sx = fma(x * x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
+    cs = e.x * c - e.y * sx;
+    sn = e.y * c + e.x * sx;
+}
+
+// Residual delta = x - s L 2^-32 of a wrapped FP64 coordinate and its code.
+__device__ __forceinline__ double fixed_residual(double xw, uint32_t s, double Lq)
+{
+    return fma(-(double)s, Lq, xw);
+}
+
 // rho partial sums: block b owns atoms [b*chunk, min(n,(b+1)*chunk)).
 template <bool MIXED>
 __device__ __forceinline__ void rho_body(int bx, int n, int chunk, const RbeConsts& c, const uint4* __restrict__ s4,
                                          const double4_32a* __restrict__ p4, const int4* __restrict__ km,
+                                         const double4_32a* __restrict__ kv, const double2* __restrict__ cis,
                                          double2* __restrict__ part)
 {
-    __shared__ double4_32a tile_d[MIXED ? 1 : TILE];
-    __shared__ uint4 tile_u[MIXED ? TILE : 1];
+    __shared__ double4_32a tile_d[MIXED ? 1 : TILE];     // FP64: residuals (dx, dy, dz) and q
+    __shared__ uint4 tile_u[TILE];
     const int b0 = bx * chunk;
     const int b1 = min(n, b0 + chunk);
     for (int l0 = 0; l0 < c.P; l0 += blockDim.x) {
@@ -139,8 +165,14 @@ __device__ __forceinline__ void rho_body(int bx, int n, int chunk, const RbeCons
             const int cnt = min(TILE, b1 - t0);
             __syncthreads();
             for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-                if (MIXED) tile_u[k] = s4[t0 + k];
-                else tile_d[k] = p4[t0 + k];
+                const uint4 su = s4[t0 + k];
+                tile_u[k] = su;
+                if (!MIXED) {
+                    const double4_32a p = p4[t0 + k];
+                    const double Lq = c.L * 2.3283064365386963e-10;
+                    tile_d[k] = make_double4_32a(fixed_residual(p.x, su.x, Lq), fixed_residual(p.y, su.y, Lq),
+                                                 fixed_residual(p.z, su.z, Lq), p.w);
+                }
             }
             __syncthreads();
             if (act) {
@@ -160,15 +192,16 @@ __device__ __forceinline__ void rho_body(int bx, int n, int chunk, const RbeCons
                     re += (double)fre;
                     im += (double)fim;
                 } else {
-                    const double mxd = m.x, myd = m.y, mzd = m.z;
+                    const double4_32a kk = act ? kv[l] : make_double4_32a(0, 0, 0, 0);
+                    const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
                     for (int k = 0; k < cnt; ++k) {
-                        double4_32a p = tile_d[k];
-                        double t = (mxd * p.x + myd * p.y + mzd * p.z) * c.invL;
-                        t -= rint(t);
+                        const uint4 su = tile_u[k];
+                        const double4_32a d = tile_d[k];
+                        const uint32_t ph = mx * su.x + my * su.y + mz * su.z;
                         double sn, cs;
-                        sincospi(2.0 * t, &sn, &cs);
-                        re += p.w * cs;
-                        im += p.w * sn;
+                        cis_fp64(ph, fma(kk.x, d.x, fma(kk.y, d.y, kk.z * d.z)), cis, cs, sn);
+                        re += d.w * cs;
+                        im += d.w * sn;
                     }
                 }
             }
@@ -179,9 +212,20 @@ __device__ __forceinline__ void rho_body(int bx, int n, int chunk, const RbeCons
 
 template <bool MIXED>
 __global__ void k_rho(int n, int chunk, RbeConsts c, const uint4* __restrict__ s4, const double4_32a* __restrict__ p4,
-                      const int4* __restrict__ km, double2* __restrict__ part)
+                      const int4* __restrict__ km, const double4_32a* __restrict__ kv, const double2* __restrict__ cis,
+                      double2* __restrict__ part)
 {
-    rho_body<MIXED>(blockIdx.x, n, chunk, c, s4, p4, km, part);
+    rho_body<MIXED>(blockIdx.x, n, chunk, c, s4, p4, km, kv, cis, part);
+}
+
+// Table of e^{2 pi i j / 4096}, j = 0..4095 (cos, sin), for cis_fp64.
+__global__ void k_cis_table(double2* __restrict__ tab)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 4096) return;
+    double sn, cs;
+    sincospi((double)j / 2048.0, &sn, &cs);
+    tab[j] = make_double2(cs, sn);
 }
 
 // Fixed-order sum over blocks; per-k energy and virial terms of the
@@ -365,6 +409,7 @@ template <bool MIXED>
 __device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, const uint4* __restrict__ s4,
                                             const double4_32a* __restrict__ p4, const int* __restrict__ perm,
                                             const int4* __restrict__ km, const double4_32a* __restrict__ kv,
+                                            const double2* __restrict__ cis,
                                             const double2* __restrict__ rho, const double* __restrict__ F_real,
                                             const double* __restrict__ totals, const double* __restrict__ F_bond,
                                             int n_bonded_atoms, double* __restrict__ F)
@@ -379,9 +424,16 @@ __device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, c
     const bool act = i < n;
     uint4 si = make_uint4(0, 0, 0, 0);
     double4_32a pi = make_double4_32a(0, 0, 0, 0);
+    double dxi = 0.0, dyi = 0.0, dzi = 0.0;     // FP64: residuals of the fixed-point code
     if (act) {
-        if (MIXED) si = s4[i];
-        else pi = p4[i];
+        si = s4[i];
+        if (!MIXED) {
+            pi = p4[i];
+            const double Lq = c.L * 2.3283064365386963e-10;
+            dxi = fixed_residual(pi.x, si.x, Lq);
+            dyi = fixed_residual(pi.y, si.y, Lq);
+            dzi = fixed_residual(pi.z, si.z, Lq);
+        }
     }
     double f[3] = {0.0, 0.0, 0.0};
     for (int l0 = 0; l0 < c.P; l0 += KT) {
@@ -418,14 +470,13 @@ __device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, c
                 for (int a = 0; a < 3; ++a) f[a] += (double)g[a];
             } else {
                 for (int k = 0; k < cnt; ++k) {
-                    int4 m = sm[k];
-                    double t = ((double)m.x * pi.x + (double)m.y * pi.y + (double)m.z * pi.z) * c.invL;
-                    t -= rint(t);
+                    const int4 m = sm[k];
+                    const double4_32a kk = sk_d[k];
+                    const uint32_t ph = (uint32_t)m.x * si.x + (uint32_t)m.y * si.y + (uint32_t)m.z * si.z;
                     double sn, cs;
-                    sincospi(2.0 * t, &sn, &cs);
-                    double2 ab = sab_d[k];
-                    double h = cs * ab.x - sn * ab.y;
-                    double4_32a kk = sk_d[k];
+                    cis_fp64(ph, fma(kk.x, dxi, fma(kk.y, dyi, kk.z * dzi)), cis, cs, sn);
+                    const double2 ab = sab_d[k];
+                    const double h = cs * ab.x - sn * ab.y;
                     f[0] += h * kk.x; f[1] += h * kk.y; f[2] += h * kk.z;
                 }
             }
@@ -446,11 +497,11 @@ template <bool MIXED>
 __global__ void __launch_bounds__(TPB) k_kforce(int n, RbeConsts c, const uint4* __restrict__ s4,
                                                 const double4_32a* __restrict__ p4, const int* __restrict__ perm,
                                                 const int4* __restrict__ km, const double4_32a* __restrict__ kv,
-                                                const double2* __restrict__ rho, const double* __restrict__ F_real,
+                                                const double2* __restrict__ cis, const double2* __restrict__ rho, const double* __restrict__ F_real,
                                                 const double* __restrict__ totals, const double* __restrict__ F_bond,
                                                 int n_bonded_atoms, double* __restrict__ F)
 {
-    kforce_body<MIXED>(blockIdx.x, n, c, s4, p4, perm, km, kv, rho, F_real, totals, F_bond, n_bonded_atoms, F);
+    kforce_body<MIXED>(blockIdx.x, n, c, s4, p4, perm, km, kv, cis, rho, F_real, totals, F_bond, n_bonded_atoms, F);
 }
 
 // Half kick v += (dt/2) accel (F + F^L) / m (F^L the Langevin force, or none)
@@ -579,7 +630,7 @@ __global__ void k_rho_b(const RepDev* __restrict__ R, const int* __restrict__ of
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    rho_body<MIXED>(bx, d.n, d.rho_chunk, d.c, d.s4, d.p4, d.km, d.rho_part);
+    rho_body<MIXED>(bx, d.n, d.rho_chunk, d.c, d.s4, d.p4, d.km, d.kv, d.cis, d.rho_part);
 }
 
 __global__ void __launch_bounds__(TPB) k_rho_sum_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)  // BK_RS
@@ -608,7 +659,7 @@ __global__ void __launch_bounds__(TPB) k_kforce_b(const RepDev* __restrict__ R, 
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    kforce_body<MIXED>(bx, d.n, d.c, d.s4, d.p4, d.perm, d.km, d.kv, d.rho, d.F_real, d.totals, d.F_bond,
+    kforce_body<MIXED>(bx, d.n, d.c, d.s4, d.p4, d.perm, d.km, d.kv, d.cis, d.rho, d.F_real, d.totals, d.F_bond,
                        d.n_bonded_atoms, d.F);
 }
 
@@ -665,6 +716,11 @@ void launch_kpool_build(rbe_ctx* ctx, const double* w, const double* q, const ui
                                     ctx->status);
 }
 
+void launch_cis_table(double2* tab, cudaStream_t st)
+{
+    k_cis_table<<<16, 256, 0, st>>>(tab);
+}
+
 void launch_rho(rbe_ctx* ctx, int n, cudaStream_t st)
 {
     int P = ctx->c.P;
@@ -672,9 +728,11 @@ void launch_rho(rbe_ctx* ctx, int n, cudaStream_t st)
     int chunk = (n + ctx->grid_rho - 1) / ctx->grid_rho;
     prof_begin(ctx, RBE_K_RHO, st);
     if (ctx->precision == RBE_MIXED)
-        k_rho<true><<<ctx->grid_rho, threads, 0, st>>>(n, chunk, ctx->c, ctx->s4, ctx->p4, ctx->km, ctx->rho_part);
+        k_rho<true><<<ctx->grid_rho, threads, 0, st>>>(n, chunk, ctx->c, ctx->s4, ctx->p4, ctx->km, ctx->kv, ctx->cis,
+                                                         ctx->rho_part);
     else
-        k_rho<false><<<ctx->grid_rho, threads, 0, st>>>(n, chunk, ctx->c, ctx->s4, ctx->p4, ctx->km, ctx->rho_part);
+        k_rho<false><<<ctx->grid_rho, threads, 0, st>>>(n, chunk, ctx->c, ctx->s4, ctx->p4, ctx->km, ctx->kv, ctx->cis,
+                                                          ctx->rho_part);
     prof_end(ctx, RBE_K_RHO, st);
     prof_begin(ctx, RBE_K_RHOSUM, st);
     double* kterms = ctx->totals + 32;
@@ -706,11 +764,11 @@ void launch_kforce(rbe_ctx* ctx, int n, double* F, cudaStream_t st)
     int nb = ctx->n_wmol > 0 ? 3 * ctx->n_wmol : 0;
     prof_begin(ctx, RBE_K_KFORCE, st);
     if (ctx->precision == RBE_MIXED)
-        k_kforce<true><<<g, TPB, 0, st>>>(n, ctx->c, ctx->s4, ctx->p4, ctx->perm, ctx->km, ctx->kv, ctx->rho, ctx->F_real,
-                                          ctx->totals, ctx->F_bond, nb, F);
+        k_kforce<true><<<g, TPB, 0, st>>>(n, ctx->c, ctx->s4, ctx->p4, ctx->perm, ctx->km, ctx->kv, ctx->cis, ctx->rho,
+                                          ctx->F_real, ctx->totals, ctx->F_bond, nb, F);
     else
-        k_kforce<false><<<g, TPB, 0, st>>>(n, ctx->c, ctx->s4, ctx->p4, ctx->perm, ctx->km, ctx->kv, ctx->rho, ctx->F_real,
-                                           ctx->totals, ctx->F_bond, nb, F);
+        k_kforce<false><<<g, TPB, 0, st>>>(n, ctx->c, ctx->s4, ctx->p4, ctx->perm, ctx->km, ctx->kv, ctx->cis, ctx->rho,
+                                           ctx->F_real, ctx->totals, ctx->F_bond, nb, F);
     prof_end(ctx, RBE_K_KFORCE, st);
 }
 

@@ -124,7 +124,7 @@ void refresh_consts(rbe_ctx* ctx)
 
 void free_dev(rbe_ctx* ctx)
 {
-    void* ptrs[] = {ctx->skey, ctx->scan_tmp, ctx->sx_of, ctx->F_lang, ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
+    void* ptrs[] = {ctx->cis, ctx->skey, ctx->scan_tmp, ctx->sx_of, ctx->F_lang, ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
                     ctx->F_real, ctx->F_bond, ctx->part_rbl, ctx->part_q, ctx->part_bond, ctx->kT, ctx->km, ctx->kv,
                     ctx->rho_part, ctx->rho, ctx->totals, ctx->status, ctx->lj, ctx->dbg_ncore, ctx->dbg_nshell,
                     ctx->dbg_core, ctx->dbg_batch, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
@@ -141,7 +141,7 @@ void free_dev(rbe_ctx* ctx)
     ctx->h_q = nullptr; ctx->h_type = nullptr; ctx->h_mol = nullptr; ctx->h_F = nullptr; ctx->ke_part = nullptr;
     ctx->vs = nullptr; ctx->gq_own = nullptr; ctx->gq_tr = nullptr; ctx->part_lj = nullptr; ctx->part_v = nullptr;
     ctx->tau_part = nullptr; ctx->tau = nullptr; ctx->kpool_buf = nullptr; ctx->kpool_dirty = 1;
-    ctx->F_lang = nullptr; ctx->F_lang_cap = 0; ctx->sx_of = nullptr; ctx->scan_tmp = nullptr; ctx->skey = nullptr;
+    ctx->F_lang = nullptr; ctx->F_lang_cap = 0; ctx->sx_of = nullptr; ctx->scan_tmp = nullptr; ctx->skey = nullptr; ctx->cis = nullptr;
     ctx->n_cap = 0; ctx->dbg_n_cap = 0; ctx->h_cap = 0;
     for (int k = 0; k < 24; ++k) ctx->cap_atoms[k] = 0;
     for (int k = 0; k < 8; ++k) ctx->cap_adj[k] = 0;
@@ -251,6 +251,9 @@ int ensure(rbe_ctx* ctx, int n)
         if ((rc = dev_alloc(ctx, &ctx->km, ctx->c.P))) return rc;
         if ((rc = dev_alloc(ctx, &ctx->kv, ctx->c.P))) return rc;
         if ((rc = dev_alloc(ctx, &ctx->rho, ctx->c.P))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->cis, 4096))) return rc;
+        launch_cis_table(ctx->cis, 0);
+        CUDA_TRY(ctx, cudaDeviceSynchronize());
         if ((rc = dev_alloc(ctx, &ctx->totals, 32 + 7 * (size_t)ctx->c.P))) return rc;
         if ((rc = dev_alloc(ctx, &ctx->status, 1))) return rc;
         CUDA_TRY(ctx, cudaMemset(ctx->status, 0, sizeof(int)));

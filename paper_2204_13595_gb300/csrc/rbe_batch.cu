@@ -184,6 +184,7 @@ int build_plan(rbe_batch* b)
         d.kT = ctx->kT; d.km = ctx->km; d.kv = ctx->kv; d.rho_part = ctx->rho_part; d.rho = ctx->rho;
         d.totals = ctx->totals; d.F_real = ctx->F_real; d.F_bond = ctx->F_bond; d.status = ctx->status;
         d.kpool = ctx->kpool_buf;
+        d.cis = ctx->cis;
         d.FL = nullptr;
         d.lang_c1 = d.lang_c2 = 0.0;
         if (ctx->lang_tau > 0.0 && b->can_step) {

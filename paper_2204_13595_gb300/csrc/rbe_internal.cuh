@@ -122,6 +122,7 @@ struct rbe_ctx {
     int4* km;            // [P] m
     double4_32a* kv;         // [P] kx, ky, kz, c_l
     double2* rho_part;   // [grid_rho * P]
+    double2* cis;        // [4096] e^{2 pi i j / 4096}: FP64 phase table
     double2* rho;        // [P]
     double* totals;      // [32]: E[6], W[6], corr[3], spare
     int* status;         // [1]
@@ -205,6 +206,7 @@ struct RepDev {
     double* F_bond;
     int* status;
     const int4* kpool;
+    const double2* cis;
     double* FL;               // Langevin force [3n] (null: thermostat off)
     double lang_c1, lang_c2;  // accel tau, 24 kT / (accel tau dt)
 };
@@ -332,6 +334,7 @@ void launch_ksample(rbe_ctx* ctx, uint64_t step, cudaStream_t st);
 // Metropolis-Hastings pool of k samples from host-made tables (k_kspace.cu)
 void launch_kpool_build(rbe_ctx* ctx, const double* w, const double* q, const uint64_t* Tq, int M, cudaStream_t st);
 void launch_rho(rbe_ctx* ctx, int n, cudaStream_t st);
+void launch_cis_table(double2* tab, cudaStream_t st);
 void launch_bonded(rbe_ctx* ctx, int n, const double* pos, cudaStream_t st);
 void launch_finalize(rbe_ctx* ctx, int n, cudaStream_t st);
 void launch_kforce(rbe_ctx* ctx, int n, double* F, cudaStream_t st);
