@@ -889,11 +889,12 @@ __global__ void __launch_bounds__(TPB) k_vbar(int n, int nblk, const double* __r
 template <bool MIXED>
 __global__ void k_tau(int n, int chunk, RbeConsts c, const uint4* __restrict__ s4, const double4_32a* __restrict__ p4,
                       const double* __restrict__ vs, const int4* __restrict__ km, const double4_32a* __restrict__ kv,
-                      double2* __restrict__ part)
+                      const double2* __restrict__ cis, double2* __restrict__ part)
 {
     __shared__ double4_32a tile_d[TILE];
     __shared__ double tile_v[TILE][3];
-    __shared__ uint4 tile_u[MIXED ? TILE : 1];
+    __shared__ double tile_r[MIXED ? 1 : TILE][3];    // FP64: residuals of the fixed-point codes
+    __shared__ uint4 tile_u[TILE];
     const int b0 = blockIdx.x * chunk;
     const int b1 = min(n, b0 + chunk);
     for (int l0 = 0; l0 < c.P; l0 += blockDim.x) {
@@ -906,8 +907,16 @@ __global__ void k_tau(int n, int chunk, RbeConsts c, const uint4* __restrict__ s
             const int cnt = min(TILE, b1 - t0);
             __syncthreads();
             for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-                tile_d[e] = p4[t0 + e];
-                if (MIXED) tile_u[e] = s4[t0 + e];
+                const double4_32a pe = p4[t0 + e];
+                const uint4 se = s4[t0 + e];
+                tile_d[e] = pe;
+                tile_u[e] = se;
+                if (!MIXED) {
+                    const double Lq = c.L * 2.3283064365386963e-10;
+                    tile_r[e][0] = fixed_residual(pe.x, se.x, Lq);
+                    tile_r[e][1] = fixed_residual(pe.y, se.y, Lq);
+                    tile_r[e][2] = fixed_residual(pe.z, se.z, Lq);
+                }
                 for (int a = 0; a < 3; ++a) tile_v[e][a] = vs[3 * (size_t)(t0 + e) + a];
             }
             __syncthreads();
@@ -923,9 +932,9 @@ __global__ void k_tau(int n, int chunk, RbeConsts c, const uint4* __restrict__ s
                         __sincosf((float)(int)ph * 1.4629180792671596e-09f, &fs, &fc);
                         sn = fs; cs = fc;
                     } else {
-                        double t = ((double)m.x * p.x + (double)m.y * p.y + (double)m.z * p.z) * c.invL;
-                        t -= rint(t);
-                        sincospi(2.0 * t, &sn, &cs);
+                        const uint4 s = tile_u[e];
+                        const uint32_t ph = (uint32_t)m.x * s.x + (uint32_t)m.y * s.y + (uint32_t)m.z * s.z;
+                        cis_fp64(ph, fma(k.x, tile_r[e][0], fma(k.y, tile_r[e][1], k.z * tile_r[e][2])), cis, cs, sn);
                     }
                     re += wv * cs;
                     im += wv * sn;
@@ -957,6 +966,7 @@ template <bool MIXED>
 __global__ void __launch_bounds__(TPB) k_kadj(int n, RbeConsts c, const uint4* __restrict__ s4,
                                               const double4_32a* __restrict__ p4, const int* __restrict__ perm,
                                               const int4* __restrict__ km, const double4_32a* __restrict__ kv,
+                                              const double2* __restrict__ cis,
                                               const double2* __restrict__ rho, const double2* __restrict__ tau,
                                               const double* __restrict__ vs, const double* __restrict__ gq_own,
                                               const double* __restrict__ gq_tr, double* __restrict__ dEdq,
@@ -970,6 +980,10 @@ __global__ void __launch_bounds__(TPB) k_kadj(int n, RbeConsts c, const uint4* _
     const bool act = i < n;
     const double4_32a pi = act ? p4[i] : make_double4_32a(0, 0, 0, 0);
     const uint4 si = act ? s4[i] : make_uint4(0, 0, 0, 0);
+    const double Lq = c.L * 2.3283064365386963e-10;
+    const double rxi = MIXED ? 0.0 : fixed_residual(pi.x, si.x, Lq);
+    const double ryi = MIXED ? 0.0 : fixed_residual(pi.y, si.y, Lq);
+    const double rzi = MIXED ? 0.0 : fixed_residual(pi.z, si.z, Lq);
     const double vx = act ? vs[3 * (size_t)i] : 0.0, vy = act ? vs[3 * (size_t)i + 1] : 0.0;
     const double vz = act ? vs[3 * (size_t)i + 2] : 0.0;
     double gE = 0.0, gL = 0.0;
@@ -995,9 +1009,8 @@ __global__ void __launch_bounds__(TPB) k_kadj(int n, RbeConsts c, const uint4* _
                     sn = fs; cs = fc;
                 } else {
                     const int4 m = sm[k];
-                    double t = ((double)m.x * pi.x + (double)m.y * pi.y + (double)m.z * pi.z) * c.invL;
-                    t -= rint(t);
-                    sincospi(2.0 * t, &sn, &cs);
+                    const uint32_t ph = (uint32_t)m.x * si.x + (uint32_t)m.y * si.y + (uint32_t)m.z * si.z;
+                    cis_fp64(ph, fma(kk.x, rxi, fma(kk.y, ryi, kk.z * rzi)), cis, cs, sn);
                 }
                 const double4_32a rt = srt[k];
                 gE += kk.w * (rt.x * cs + rt.y * sn);
@@ -1031,10 +1044,10 @@ void launch_adj_prep(rbe_ctx* ctx, int n, const double* gF, cudaStream_t st)
     prof_begin(ctx, RBE_K_RHO, st);
     if (ctx->precision == RBE_MIXED)
         k_tau<true><<<ctx->grid_rho, threads, 0, st>>>(n, chunk, ctx->c, ctx->s4, ctx->p4, ctx->vs, ctx->km, ctx->kv,
-                                                       ctx->tau_part);
+                                                       ctx->cis, ctx->tau_part);
     else
         k_tau<false><<<ctx->grid_rho, threads, 0, st>>>(n, chunk, ctx->c, ctx->s4, ctx->p4, ctx->vs, ctx->km, ctx->kv,
-                                                        ctx->tau_part);
+                                                        ctx->cis, ctx->tau_part);
     prof_end(ctx, RBE_K_RHO, st);
     prof_begin(ctx, RBE_K_RHOSUM, st);
     k_tau_sum<<<(P + TPB - 1) / TPB, TPB, 0, st>>>(ctx->grid_rho, P, ctx->tau_part, ctx->tau);
@@ -1046,11 +1059,11 @@ void launch_adj_final(rbe_ctx* ctx, int n, double* dEdq, double* dLdq, cudaStrea
     prof_begin(ctx, RBE_K_KFORCE, st);
     if (ctx->precision == RBE_MIXED)
         k_kadj<true><<<(n + TPB - 1) / TPB, TPB, 0, st>>>(n, ctx->c, ctx->s4, ctx->p4, ctx->perm, ctx->km, ctx->kv,
-                                                           ctx->rho, ctx->tau, ctx->vs, ctx->gq_own, ctx->gq_tr, dEdq,
+                                                           ctx->cis, ctx->rho, ctx->tau, ctx->vs, ctx->gq_own, ctx->gq_tr, dEdq,
                                                            dLdq);
     else
         k_kadj<false><<<(n + TPB - 1) / TPB, TPB, 0, st>>>(n, ctx->c, ctx->s4, ctx->p4, ctx->perm, ctx->km, ctx->kv,
-                                                            ctx->rho, ctx->tau, ctx->vs, ctx->gq_own, ctx->gq_tr, dEdq,
+                                                            ctx->cis, ctx->rho, ctx->tau, ctx->vs, ctx->gq_own, ctx->gq_tr, dEdq,
                                                             dLdq);
     prof_end(ctx, RBE_K_KFORCE, st);
 }
