@@ -643,8 +643,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                         dy -= c.L * rint(dy * c.invL);
                         dz -= c.L * rint(dz * c.invL);
                         r2 = dx * dx + dy * dy + dz * dz;
-                        const double rr = sqrt(r2);
-                        const double rinv = 1.0 / rr;
+                        const double rinv = rsqrt(r2);     // one reciprocal square root, no division
+                        const double rr = r2 * rinv;
                         const double ar = c.sqrt_alpha * rr;
                         const double gauss = c.two_sqrt_alpha_over_sqrt_pi * exp(-ar * ar);
                         const double ec = ex ? -erf(ar) : erfc(ar);
@@ -766,8 +766,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     dy -= c.L * rint(dy * c.invL);
                     dz -= c.L * rint(dz * c.invL);
                     const double r2 = dx * dx + dy * dy + dz * dz;
-                    const double r = sqrt(r2);
-                    const double rinv = 1.0 / r;
+                    const double rinv = rsqrt(r2);         // one reciprocal square root, no division
+                    const double r = r2 * rinv;
                     const double qq = c.k_e * pi.w * pj.w;
                     const double ar = c.sqrt_alpha * r;
                     const double gauss = c.two_sqrt_alpha_over_sqrt_pi * exp(-ar * ar);
