@@ -570,12 +570,19 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                 if (p <= 32) {
                     // slot k on lane k; the insertions resolved in slot order
                     const uint32_t jk = (uint32_t)(nshell - p + lane);
-                    const int tk = lane < p ? (int)uniform_below(wa[lane], jk + 1u) : -1;
-                    int mysel = -1;
-                    for (int k = 0; k < p; ++k) {
-                        const int t = __shfl_sync(FULL, tk, k);
-                        const bool dup = __any_sync(FULL, lane < k && mysel == t);
-                        if (lane == k) mysel = dup ? (int)jk : t;
+                    const int tk = lane < p ? (int)uniform_below(wa[lane], jk + 1u) : -1 - lane;
+                    // if the p draws are distinct, no slot is replaced and every
+                    // slot keeps its draw (by induction over the slots);
+                    // otherwise resolve the slots in order
+                    const bool distinct = !__any_sync(FULL, (__match_any_sync(FULL, tk) & lt_mask) != 0u);
+                    int mysel = tk;
+                    if (!distinct) {
+                        mysel = -1;
+                        for (int k = 0; k < p; ++k) {
+                            const int t = __shfl_sync(FULL, tk, k);
+                            const bool dup = __any_sync(FULL, lane < k && mysel == t);
+                            if (lane == k) mysel = dup ? (int)jk : t;
+                        }
                     }
                     if (lane < p) sel[lane] = mysel;
                 } else {
@@ -686,9 +693,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                 const float qi = __uint_as_float(si.w);
                 const float kef = (float)c.k_e, saf = (float)c.sqrt_alpha, tsaf = (float)c.two_sqrt_alpha_over_sqrt_pi;
                 float ff[3] = {0.f, 0.f, 0.f};
-                for (int t = lane; t < npairs; t += 32) {
-                    int j;
-                    float w;
+                auto pair_of = [&](int t, int& j, float& w) {
                     if (t < ncore_c) { j = core_buf[t]; w = 1.0f; }
                     else {
                         const int k = t - ncore_c;
@@ -696,8 +701,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                         j = shell_buf[min(ord, a.shell_cap - 1)];
                         w = wsh;
                     }
-                    const uint4 sj = a.s4[j];
-                    const int2 tj = a.tm[j];
+                };
+                auto term = [&](const uint4 sj, const int2 tj, const float w) {
                     const float dx = (float)(int)(sj.x - si.x) * c.Lfix;
                     const float dy = (float)(int)(sj.y - si.y) * c.Lfix;
                     const float dz = (float)(int)(sj.z - si.z) * c.Lfix;
@@ -725,6 +730,22 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     facc_e[2] += ex ? w * ucoul : 0.f;
                     facc_w[0] += dx * gx; facc_w[1] += dy * gy; facc_w[2] += dz * gz;
                     facc_w[3] += dx * gy; facc_w[4] += dx * gz; facc_w[5] += dy * gz;
+                };
+                // two pairs per lane per iteration (t, t + 32: the order of the
+                // one-pair loop), their loads issued together
+                for (int t = lane; t < npairs; t += 64) {
+                    const bool v2 = t + 32 < npairs;
+                    int j1, j2;
+                    float w1, w2;
+                    pair_of(t, j1, w1);
+                    if (v2) pair_of(t + 32, j2, w2);
+                    else { j2 = j1; w2 = 0.f; }
+                    const uint4 sj1 = a.s4[j1];
+                    const int2 tj1 = a.tm[j1];
+                    const uint4 sj2 = a.s4[j2];
+                    const int2 tj2 = a.tm[j2];
+                    term(sj1, tj1, w1);
+                    if (v2) term(sj2, tj2, w2);
                 }
 #pragma unroll
                 for (int q = 0; q < 3; ++q) ff[q] = warp_sum(ff[q]);
