@@ -97,3 +97,9 @@ def test_batch_create_validates_contexts(L):
     assert L.rbe_set_rbl_tiling(h, -1, 0) == -1
     assert L.rbe_set_rbl_tiling(h, 32, 2) == 0
     L.rbe_destroy(h)
+
+
+def test_peak_probe_rejects_bad_arguments(L):
+    out = ctypes.c_double()
+    assert L.rbe_peak_probe(99, ctypes.byref(out), None) == -1
+    assert L.rbe_peak_probe(0, None, None) == -1
