@@ -183,7 +183,9 @@ int rbe_get_kspace(rbe_ctx* ctx, int32_t* m, double* rho, void* cuda_stream);
 /* Derived parameters: out[0] cells per axis, out[1] stencil reach in cells,
  * out[2] k truncation M, out[3] S = H^3 - 1 (Eq. (2.6)), out[4] core capacity,
  * out[5] shell capacity (after the last rbe_forces), out[6] kernel launches
- * of the last rbe_forces. */
+ * of the last rbe_forces, out[7] work units of the last pair-kernel launch
+ * whose stencil exceeded the shared-memory staging capacity and was read
+ * from global memory (counted with rbe_set_debug on; -1 otherwise). */
 int rbe_get_info(rbe_ctx* ctx, double* out, int nout);
 
 /* Kernel timing: when on, every launch is bracketed by CUDA events on its

@@ -67,6 +67,7 @@ struct RblArgs {
     int* __restrict__ dbg_nshell;
     int* __restrict__ dbg_core;
     int* __restrict__ dbg_batch;
+    int* __restrict__ dbg_unstaged;
 };
 
 // Per-row description of the staged region of the current unit (64 bytes).
@@ -82,7 +83,12 @@ struct __align__(16) RowInfo {
 };
 static_assert(sizeof(RowInfo) == 64, "RowInfo layout");
 
+// Candidate ranges of one pass of 32 stencil rows: at most two per row.
+constexpr int RBL_MAX_RANGES = 64;
+
 // Shared-memory layout of k_rbl; every section starts on a 16-byte boundary.
+// Per warp: the range table of the current pass [RBL_MAX_RANGES] int4, the
+// Philox words [ga][p_pad], the core and shell lists and the batch ordinals.
 struct SmemLayout {
     size_t rows, cellpos, lj, warps, wbytes, total;
     int ga;                // atoms whose Philox words are made in one warp pass
@@ -104,7 +110,8 @@ __host__ __device__ inline SmemLayout smem_layout(const RblGeom& g, int nt2, int
     L.lj = o;
     o = up16(o + sizeof(double) * 12 * (size_t)nt2);
     L.warps = o;
-    L.wbytes = up16(sizeof(uint64_t) * (size_t)p_pad * L.ga + sizeof(int) * (size_t)(core_cap + shell_cap + p_pad));
+    L.wbytes = sizeof(int4) * RBL_MAX_RANGES +
+               up16(sizeof(uint64_t) * (size_t)p_pad * L.ga + sizeof(int) * (size_t)(core_cap + shell_cap + p_pad));
     L.total = o + L.wbytes * WARPS;
     return L;
 }
@@ -267,6 +274,86 @@ __device__ __forceinline__ void classify(const float4* __restrict__ src, int beg
     }
 }
 
+// Exact decision of one candidate inside the rounding bands of its FP32
+// distance (same rules as the stencil walk).
+__device__ __forceinline__ void exact_class(const RblArgs& a, int i, uint4 si, int gj, bool& is_core, bool& is_shell,
+                                            bool& overlap)
+{
+    const unsigned long long d2 = d2_exact(si, a.s4[gj]);
+    const bool other = gj != i;
+    is_core = other && d2 <= a.c.Rc2;
+    is_shell = other && d2 > a.c.Rc2 && d2 <= a.c.Rs2;
+    overlap |= other && d2 == 0ull;
+}
+
+// Classification of the concatenated candidate ranges of one pass of stencil
+// rows.  The ranges are listed in canonical order in the warp's table, entry
+// k = (end position, staged index - position, global index - position) over
+// virtual positions [0, T); lane l of a 32-wide chunk takes position v0 + l
+// and finds its range by advancing its own cursor (positions only grow), so
+// every chunk but the last is full whatever the lengths of the ranges.  The
+// staged positions carry their image shifts, so every candidate is compared
+// with atom i's position (xi, yi, zi).  Two chunks per iteration, appended in
+// order, as in the per-range walk.
+__device__ __forceinline__ void classify_packed(const float4* __restrict__ stage, const int4* __restrict__ ranges,
+                                                int T, float xi, float yi, float zi, const RblArgs& a, int i, uint4 si,
+                                                int lane, unsigned lt_mask, int* core_buf, int* shell_buf, int& ncore,
+                                                int& nshell, bool& overlap)
+{
+    const RblGeom& g = a.g;
+    const unsigned FULL = 0xffffffffu;
+    int ka = 0, kb = 0;
+    int4 ra = ranges[0], rb = ra;
+    int v0 = 0;
+    for (; T - v0 > 32; v0 += 64) {
+        const int va = v0 + lane, vb = va + 32;
+        const bool vbok = vb < T;
+        while (va >= ra.x) ra = ranges[++ka];
+        if (vbok)
+            while (vb >= rb.x) rb = ranges[++kb];
+        const float4 pa = stage[va + ra.y];
+        const float4 pb = stage[vbok ? vb + rb.y : va + ra.y];
+        bool ca, sha, ma, cb, shb, mb;
+        dist_class<false>(pa, true, xi, yi, zi, g, 0.f, 0.f, ca, sha, ma);
+        dist_class<false>(pb, vbok, xi, yi, zi, g, 0.f, 0.f, cb, shb, mb);
+        const int ga = va + ra.z, gb = vb + rb.z;
+        if (__any_sync(FULL, ma || mb)) {
+            if (ma) exact_class(a, i, si, ga, ca, sha, overlap);
+            if (mb) exact_class(a, i, si, gb, cb, shb, overlap);
+        }
+        const unsigned cma = __ballot_sync(FULL, ca), sma = __ballot_sync(FULL, sha);
+        const unsigned cmb = __ballot_sync(FULL, cb), smb = __ballot_sync(FULL, shb);
+        const int nca = __popc(cma), nsa = __popc(sma);
+        const int cpa = ncore + __popc(cma & lt_mask), spa = nshell + __popc(sma & lt_mask);
+        const int cpb = ncore + nca + __popc(cmb & lt_mask), spb = nshell + nsa + __popc(smb & lt_mask);
+        if (ca && cpa < a.core_cap) core_buf[cpa] = ga;
+        if (sha && spa < a.shell_cap) shell_buf[spa] = ga;
+        if (cb && cpb < a.core_cap) core_buf[cpb] = gb;
+        if (shb && spb < a.shell_cap) shell_buf[spb] = gb;
+        ncore += nca + __popc(cmb);
+        nshell += nsa + __popc(smb);
+    }
+    if (v0 < T) {
+        const int va = v0 + lane;
+        const bool vaok = va < T;
+        if (vaok)
+            while (va >= ra.x) ra = ranges[++ka];
+        const float4 pa = stage[vaok ? va + ra.y : ranges[0].y];
+        bool ca, sha, ma;
+        dist_class<false>(pa, vaok, xi, yi, zi, g, 0.f, 0.f, ca, sha, ma);
+        const int ga = va + ra.z;
+        if (__any_sync(FULL, ma)) {
+            if (ma) exact_class(a, i, si, ga, ca, sha, overlap);
+        }
+        const unsigned cma = __ballot_sync(FULL, ca), sma = __ballot_sync(FULL, sha);
+        const int cpa = ncore + __popc(cma & lt_mask), spa = nshell + __popc(sma & lt_mask);
+        if (ca && cpa < a.core_cap) core_buf[cpa] = ga;
+        if (sha && spa < a.shell_cap) shell_buf[spa] = ga;
+        ncore += __popc(cma);
+        nshell += __popc(sma);
+    }
+}
+
 template <bool MIXED, bool SMALL, bool ADJ>
 __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
 {
@@ -298,7 +385,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     double* s_dsds = s_dsde + nt2;
     double* s_rc2 = s_dsds + nt2;           // squared LJ cutoff per pair type
     double* s_glj = s_rc2 + nt2;            // adjoint: [4][nt2] block accumulators
-    uint64_t* words = reinterpret_cast<uint64_t*>(smem + lay.warps + lay.wbytes * wib);   // [ga][p_pad]
+    int4* ranges = reinterpret_cast<int4*>(smem + lay.warps + lay.wbytes * wib);          // [RBL_MAX_RANGES]
+    uint64_t* words = reinterpret_cast<uint64_t*>(ranges + RBL_MAX_RANGES);              // [ga][p_pad]
     int* core_buf = reinterpret_cast<int*>(words + (size_t)p_pad * lay.ga);
     int* shell_buf = core_buf + a.core_cap;
     int* sel = shell_buf + a.shell_cap;
@@ -410,6 +498,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
         }
         __syncthreads();
         const bool staged = s_unit_ok;
+        if (a.debug && !staged && threadIdx.x == 0) atomicAdd(a.dbg_unstaged, 1);
         // (d) global - source offsets of the three pieces of each row
         for (int t = threadIdx.x; t < nrows * 3; t += blockDim.x) {
             const int r = t / 3, pc = t - 3 * r;
@@ -423,20 +512,28 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
             }
             rows[r].goff[pc] = off;
         }
-        // (e) stage the FP32 positions row by row
+        // (e) stage the FP32 positions row by row, each piece moved to the
+        // periodic image adjacent to the unit (x: -L below cell 0, +L past
+        // cell nc-1; y, z: the row's shift), so that every staged candidate
+        // is compared with atom i's own position
         if (staged) {
             for (int r = wib; r < nrows; r += WARPS) {
                 const int zc = rows[r].zc, yc = rows[r].yc, sb = rows[r].sbase;
+                const float shy = rows[r].shy, shz = rows[r].shz;
                 const int rb = nc * (yc + nc * zc);
                 const int* cp = cellpos + r * cpr;
                 for (int pc = 0; pc < 3; ++pc) {
                     const int u0 = pc == 0 ? ul : (pc == 1 ? max(ul, 0) : max(ul, nc));
                     const int u1 = pc == 0 ? min(uh, -1) : (pc == 1 ? min(uh, nc - 1) : uh);
                     if (u0 > u1) continue;
+                    const float shx = pc == 0 ? -Lf : (pc == 2 ? Lf : 0.f);
                     const int gs = a.cell_start[rb + wrapc(u0, nc)];
                     const int len = cp[u1 - ul + 1] - cp[u0 - ul];
                     const int ss = sb + cp[u0 - ul];
-                    for (int k = lane; k < len; k += 32) stage[ss + k] = a.f4[gs + k];
+                    for (int k = lane; k < len; k += 32) {
+                        const float4 q4 = a.f4[gs + k];
+                        stage[ss + k] = make_float4(q4.x + shx, q4.y + shy, q4.z + shz, q4.w);
+                    }
                 }
             }
         }
@@ -481,8 +578,9 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                 if (r < nrows) {
                     const RowInfo& ri = rows[r];
                     const int* cp = cellpos + r * cpr;
-                    yie = fi4.y - ri.shy;
-                    zie = fi4.z - ri.shz;
+                    // staged positions carry the row's image shift already
+                    yie = staged ? fi4.y : fi4.y - ri.shy;
+                    zie = staged ? fi4.z : fi4.z - ri.shz;
                     const int rbw = nc * (ri.yc + nc * ri.zc);
                     const int base = staged ? ri.sbase : 0;
                     if (SMALL) {
@@ -511,7 +609,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                                 if (staged) { b1 = base + cp[lo1 - ul]; e1 = base + cp[hi1 - ul + 1]; }
                                 else { b1 = a.cell_start[rbw + wrapc(lo1, nc)]; e1 = b1 + cp[hi1 - ul + 1] - cp[lo1 - ul]; }
                                 o1 = ri.goff[pc];
-                                x1 = fi4.x - (pc == 2 ? Lf : 0.f);
+                                x1 = staged ? fi4.x : fi4.x - (pc == 2 ? Lf : 0.f);
                                 trim_segment(srcp, b1, e1, cp[lo1 - ul + 1] - cp[lo1 - ul], cp[hi1 - ul + 1] - cp[hi1 - ul],
                                              lo1 == hi1, x1, H);
                             }
@@ -520,12 +618,41 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                                 if (staged) { b2 = base + cp[lo2 - ul]; e2 = base + cp[hi2 - ul + 1]; }
                                 else { b2 = a.cell_start[rbw + wrapc(lo2, nc)]; e2 = b2 + cp[hi2 - ul + 1] - cp[lo2 - ul]; }
                                 o2 = ri.goff[pc];
-                                x2 = fi4.x - (pc == 0 ? -Lf : 0.f);
+                                x2 = staged ? fi4.x : fi4.x - (pc == 0 ? -Lf : 0.f);
                                 trim_segment(srcp, b2, e2, cp[lo2 - ul + 1] - cp[lo2 - ul], cp[hi2 - ul + 1] - cp[hi2 - ul],
                                              lo2 == hi2, x2, H);
                             }
                         }
                     }
+                }
+                if (!SMALL && staged) {
+                    // concatenate the pass's segments in canonical order (row
+                    // by row, each row's first segment before its second):
+                    // one warp scan of (candidates, segments), packed in one
+                    // word (both stay below 2^16: the segments are disjoint
+                    // parts of the staged array), gives each lane the virtual
+                    // position and table slot of its row's segments
+                    const int n1 = e1 - b1, n2 = e2 - b2;
+                    const int own = n1 + n2 + (((n1 > 0) + (n2 > 0)) << 16);
+                    int incl = own;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= o) incl += t;
+                    }
+                    const int T = __shfl_sync(FULL, incl, 31) & 0xffff;
+                    int v = (incl - own) & 0xffff, k = (incl - own) >> 16;
+                    if (n1 > 0) {
+                        ranges[k++] = make_int4(v + n1, b1 - v, b1 + o1 - v, 0);
+                        v += n1;
+                    }
+                    if (n2 > 0) ranges[k] = make_int4(v + n2, b2 - v, b2 + o2 - v, 0);
+                    __syncwarp();
+                    if (T > 0)
+                        classify_packed(stage, ranges, T, fi4.x, fi4.y, fi4.z, a, i, si, lane, lt_mask, core_buf,
+                                        shell_buf, ncore, nshell, overlap);
+                    __syncwarp();            // the table is rewritten by the next pass
+                    continue;
                 }
                 // walk the non-empty segments in canonical order
                 const unsigned m1 = __ballot_sync(FULL, e1 > b1), m2 = __ballot_sync(FULL, e2 > b2);
@@ -950,6 +1077,7 @@ void rbl_fill_args(const rbe_ctx* ctx, int n, void* out)
     a.core_cap = ctx->core_cap; a.shell_cap = ctx->shell_cap;
     a.debug = ctx->debug; a.dbg_cap = ctx->dbg_cap_core;
     a.dbg_ncore = ctx->dbg_ncore; a.dbg_nshell = ctx->dbg_nshell; a.dbg_core = ctx->dbg_core; a.dbg_batch = ctx->dbg_batch;
+    a.dbg_unstaged = ctx->dbg_unstaged;
     a.vs = ctx->vs; a.vbar = ctx->totals + 16; a.gq_own = ctx->gq_own; a.gq_tr = ctx->gq_tr; a.part_lj = ctx->part_lj;
     a.nslots = ctx->grid_rbl;
 }
@@ -966,6 +1094,7 @@ void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st, bool adjoin
     rbl_fill_args(ctx, n, &a);
     a.step = step;
     if (adjoint) a.debug = 0;
+    if (a.debug) cudaMemsetAsync(ctx->dbg_unstaged, 0, sizeof(int), st);
     int smem = rbl_smem_bytes(ctx);
     prof_begin(ctx, RBE_K_RBL, st);
     const bool small = ctx->rbl.small;

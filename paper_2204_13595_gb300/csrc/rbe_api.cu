@@ -127,7 +127,7 @@ void free_dev(rbe_ctx* ctx)
     void* ptrs[] = {ctx->cis, ctx->skey, ctx->scan_tmp, ctx->sx_of, ctx->F_lang, ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
                     ctx->F_real, ctx->F_bond, ctx->part_rbl, ctx->part_q, ctx->part_bond, ctx->kT, ctx->km, ctx->kv,
                     ctx->rho_part, ctx->rho, ctx->totals, ctx->status, ctx->lj, ctx->dbg_ncore, ctx->dbg_nshell,
-                    ctx->dbg_core, ctx->dbg_batch, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
+                    ctx->dbg_core, ctx->dbg_batch, ctx->dbg_unstaged, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
                     ctx->ke_part, ctx->vs, ctx->gq_own, ctx->gq_tr, ctx->part_lj, ctx->part_v, ctx->tau_part,
                     ctx->tau};
     for (void* p : ptrs)
@@ -137,7 +137,8 @@ void free_dev(rbe_ctx* ctx)
     ctx->F_bond = nullptr; ctx->part_rbl = nullptr; ctx->part_q = nullptr; ctx->part_bond = nullptr;
     ctx->kT = nullptr; ctx->km = nullptr; ctx->kv = nullptr; ctx->rho_part = nullptr; ctx->rho = nullptr;
     ctx->totals = nullptr; ctx->status = nullptr; ctx->lj = nullptr; ctx->dbg_ncore = nullptr;
-    ctx->dbg_nshell = nullptr; ctx->dbg_core = nullptr; ctx->dbg_batch = nullptr; ctx->h_pos = nullptr;
+    ctx->dbg_nshell = nullptr; ctx->dbg_core = nullptr; ctx->dbg_batch = nullptr; ctx->dbg_unstaged = nullptr;
+    ctx->h_pos = nullptr;
     ctx->h_q = nullptr; ctx->h_type = nullptr; ctx->h_mol = nullptr; ctx->h_F = nullptr; ctx->ke_part = nullptr;
     ctx->vs = nullptr; ctx->gq_own = nullptr; ctx->gq_tr = nullptr; ctx->part_lj = nullptr; ctx->part_v = nullptr;
     ctx->tau_part = nullptr; ctx->tau = nullptr; ctx->kpool_buf = nullptr; ctx->kpool_dirty = 1;
@@ -192,8 +193,9 @@ void rbl_geometry(rbe_ctx* ctx, int n)
     double apc = (double)n / ((double)nc * nc * nc);
     int naxis = g.small ? nc : 2 * R + 1;
     g.nrows = naxis * naxis;
-    // shared memory per block: two resident blocks per SM
-    const int target = 110 * 1024;
+    // shared memory per block: two resident blocks per SM (228 KB per SM, of
+    // which 1 KB per block is reserved and under 1 KB is static)
+    const int target = 112 * 1024;
     const double apu = ctx->tune_apu > 0 ? (double)ctx->tune_apu : 48.0;
     int G = (int)lrint(apu / (apc > 1e-9 ? apc : 1e-9));
     G = G < 1 ? 1 : (G > nc ? nc : G);
@@ -369,6 +371,7 @@ int ensure(rbe_ctx* ctx, int n)
         if ((rc = grow(ctx, &ctx->dbg_nshell, &ctx->cap_atoms[14], n))) return rc;
         if ((rc = grow(ctx, &ctx->dbg_core, &ctx->cap_atoms[15], (size_t)n * cc))) return rc;
         if ((rc = grow(ctx, &ctx->dbg_batch, &ctx->cap_atoms[16], (size_t)n * ctx->c.p))) return rc;
+        if ((rc = grow(ctx, &ctx->dbg_unstaged, &ctx->cap_atoms[22], 1))) return rc;
         ctx->dbg_n_cap = n;
     }
     return RBE_OK;
@@ -853,9 +856,12 @@ int rbe_get_kspace(rbe_ctx* ctx, int32_t* m, double* rho, void* cuda_stream)
 int rbe_get_info(rbe_ctx* ctx, double* out, int nout)
 {
     if (!ctx || !out) return RBE_EINVAL;
-    double v[7] = {(double)ctx->c.n_cell, (double)ctx->c.reach, (double)ctx->c.M, ctx->c.S, (double)ctx->core_cap,
-                   (double)ctx->shell_cap, (double)ctx->last_launches};
-    for (int k = 0; k < nout && k < 7; ++k) out[k] = v[k];
+    int unstaged = -1;
+    if (nout > 7 && ctx->debug && ctx->dbg_unstaged)
+        CUDA_TRY(ctx, cudaMemcpy(&unstaged, ctx->dbg_unstaged, sizeof(int), cudaMemcpyDeviceToHost));
+    double v[8] = {(double)ctx->c.n_cell, (double)ctx->c.reach, (double)ctx->c.M, ctx->c.S, (double)ctx->core_cap,
+                   (double)ctx->shell_cap, (double)ctx->last_launches, (double)unstaged};
+    for (int k = 0; k < nout && k < 8; ++k) out[k] = v[k];
     return RBE_OK;
 }
 

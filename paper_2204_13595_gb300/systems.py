@@ -165,6 +165,25 @@ def electrolyte(n: int = 2000, L: float = 20.0, seed: int = 1, r_c: float = 2.5,
                   K_E_REDUCED, (1.0,), (1.0,), 1.0, dt, seed)
 
 
+def slab_ions(n: int = 8000, L: float = 32.0, slab_frac: float = 0.5, slab_width: float = 3.0, seed: int = 11,
+              r_c: float = 2.5, r_s: float = 5.0, p: int = 10, P: int = 100) -> System:
+    """A strongly inhomogeneous charged system (an edge case, not a paper
+    workload): n uniformly random point charges (+1/-1 alternating, no LJ),
+    the first slab_frac of them confined to the slab 0 <= z < slab_width, so
+    that the local density there is several times the mean."""
+    assert n % 2 == 0
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, 3)) * L
+    k = int(slab_frac * n)
+    pos[:k, 2] = rng.random(k) * slab_width
+    q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    typ = np.zeros(n, dtype=np.int32)
+    mass = np.ones(n)
+    vel = _maxwell(rng, mass, 1.0, 1.0)
+    return System("slab_ions", L, pos, q, typ, None, mass, vel, alpha_for(r_s), r_c, r_s, p, P,
+                  K_E_REDUCED, (0.0,), (1.0,), 1.0, 0.002, seed)
+
+
 def _random_rotations(rng, n):
     """Uniform random rotation matrices from unit quaternions (Shoemake 1992)."""
     u1, u2, u3 = rng.random(n), rng.random(n), rng.random(n)
