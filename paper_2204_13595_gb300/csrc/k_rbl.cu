@@ -83,12 +83,16 @@ struct __align__(16) RowInfo {
 };
 static_assert(sizeof(RowInfo) == 64, "RowInfo layout");
 
-// Candidate ranges of one pass of 32 stencil rows: at most two per row.
+// Candidate ranges of one pass of 32 stencil rows: at most two per row.  A
+// pass whose concatenated ranges hold more than RBL_MAX_PACKED candidates is
+// walked range by range instead.
 constexpr int RBL_MAX_RANGES = 64;
+constexpr int RBL_MAX_PACKED = 2048;
 
 // Shared-memory layout of k_rbl; every section starts on a 16-byte boundary.
-// Per warp: the range table of the current pass [RBL_MAX_RANGES] int4, the
-// Philox words [ga][p_pad], the core and shell lists and the batch ordinals.
+// Per warp: the range table of the current pass [RBL_MAX_RANGES] int2 and the
+// bitmap of range starts [RBL_MAX_PACKED / 32] words, the Philox words
+// [ga][p_pad], the core and shell lists and the batch ordinals.
 struct SmemLayout {
     size_t rows, cellpos, lj, warps, wbytes, total;
     int ga;                // atoms whose Philox words are made in one warp pass
@@ -110,7 +114,7 @@ __host__ __device__ inline SmemLayout smem_layout(const RblGeom& g, int nt2, int
     L.lj = o;
     o = up16(o + sizeof(double) * 12 * (size_t)nt2);
     L.warps = o;
-    L.wbytes = sizeof(int4) * RBL_MAX_RANGES +
+    L.wbytes = sizeof(int2) * RBL_MAX_RANGES + sizeof(unsigned) * (RBL_MAX_PACKED / 32) +
                up16(sizeof(uint64_t) * (size_t)p_pad * L.ga + sizeof(int) * (size_t)(core_cap + shell_cap + p_pad));
     L.total = o + L.wbytes * WARPS;
     return L;
@@ -287,36 +291,41 @@ __device__ __forceinline__ void exact_class(const RblArgs& a, int i, uint4 si, i
 }
 
 // Classification of the concatenated candidate ranges of one pass of stencil
-// rows.  The ranges are listed in canonical order in the warp's table, entry
-// k = (end position, staged index - position, global index - position) over
-// virtual positions [0, T); lane l of a 32-wide chunk takes position v0 + l
-// and finds its range by advancing its own cursor (positions only grow), so
-// every chunk but the last is full whatever the lengths of the ranges.  The
-// staged positions carry their image shifts, so every candidate is compared
-// with atom i's position (xi, yi, zi).  Two chunks per iteration, appended in
-// order, as in the per-range walk.
-__device__ __forceinline__ void classify_packed(const float4* __restrict__ stage, const int4* __restrict__ ranges,
-                                                int T, float xi, float yi, float zi, const RblArgs& a, int i, uint4 si,
-                                                int lane, unsigned lt_mask, int* core_buf, int* shell_buf, int& ncore,
+// rows, virtual positions [0, T).  Range k of the warp's table holds (staged
+// index - position, global index - position); bit v of the start bitmap is
+// set where a range begins.  Lane l of a 32-wide chunk takes position
+// v = v0 + l (v0 a multiple of 32) and its range index is the number of range
+// starts at or below v, less one: the starts below v0 are counted as the
+// chunks go, the rest from the chunk's bitmap word, so every chunk but the
+// last is full whatever the lengths of the ranges.  The staged positions
+// carry their image shifts, so every candidate is compared with atom i's
+// position (xi, yi, zi).  Two chunks per iteration, appended in order, as in
+// the per-range walk.
+__device__ __forceinline__ void classify_packed(const float4* __restrict__ stage, const int2* __restrict__ ranges,
+                                                const unsigned* __restrict__ rstart, int T, float xi, float yi,
+                                                float zi, const RblArgs& a, int i, uint4 si, int lane,
+                                                unsigned lt_mask, int* core_buf, int* shell_buf, int& ncore,
                                                 int& nshell, bool& overlap)
 {
     const RblGeom& g = a.g;
     const unsigned FULL = 0xffffffffu;
-    int ka = 0, kb = 0;
-    int4 ra = ranges[0], rb = ra;
+    const unsigned le_mask = lt_mask | (1u << lane);
+    int before = 0;                       // range starts below v0
     int v0 = 0;
     for (; T - v0 > 32; v0 += 64) {
+        const unsigned wa = rstart[v0 >> 5], wb = rstart[(v0 >> 5) + 1];
+        const int na = __popc(wa);
+        const int2 ra = ranges[before + __popc(wa & le_mask) - 1];
+        const int2 rb = ranges[before + na + __popc(wb & le_mask) - 1];
+        before += na + __popc(wb);
         const int va = v0 + lane, vb = va + 32;
         const bool vbok = vb < T;
-        while (va >= ra.x) ra = ranges[++ka];
-        if (vbok)
-            while (vb >= rb.x) rb = ranges[++kb];
-        const float4 pa = stage[va + ra.y];
-        const float4 pb = stage[vbok ? vb + rb.y : va + ra.y];
+        const float4 pa = stage[va + ra.x];
+        const float4 pb = stage[vbok ? vb + rb.x : va + ra.x];
         bool ca, sha, ma, cb, shb, mb;
         dist_class<false>(pa, true, xi, yi, zi, g, 0.f, 0.f, ca, sha, ma);
         dist_class<false>(pb, vbok, xi, yi, zi, g, 0.f, 0.f, cb, shb, mb);
-        const int ga = va + ra.z, gb = vb + rb.z;
+        const int ga = va + ra.y, gb = vb + rb.y;
         if (__any_sync(FULL, ma || mb)) {
             if (ma) exact_class(a, i, si, ga, ca, sha, overlap);
             if (mb) exact_class(a, i, si, gb, cb, shb, overlap);
@@ -334,14 +343,14 @@ __device__ __forceinline__ void classify_packed(const float4* __restrict__ stage
         nshell += nsa + __popc(smb);
     }
     if (v0 < T) {
+        const unsigned wa = rstart[v0 >> 5];
+        const int2 ra = ranges[before + __popc(wa & le_mask) - 1];
         const int va = v0 + lane;
         const bool vaok = va < T;
-        if (vaok)
-            while (va >= ra.x) ra = ranges[++ka];
-        const float4 pa = stage[vaok ? va + ra.y : ranges[0].y];
+        const float4 pa = stage[vaok ? va + ra.x : 0];      // lanes past T: any staged slot, not classified
         bool ca, sha, ma;
         dist_class<false>(pa, vaok, xi, yi, zi, g, 0.f, 0.f, ca, sha, ma);
-        const int ga = va + ra.z;
+        const int ga = va + ra.y;
         if (__any_sync(FULL, ma)) {
             if (ma) exact_class(a, i, si, ga, ca, sha, overlap);
         }
@@ -385,8 +394,9 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     double* s_dsds = s_dsde + nt2;
     double* s_rc2 = s_dsds + nt2;           // squared LJ cutoff per pair type
     double* s_glj = s_rc2 + nt2;            // adjoint: [4][nt2] block accumulators
-    int4* ranges = reinterpret_cast<int4*>(smem + lay.warps + lay.wbytes * wib);          // [RBL_MAX_RANGES]
-    uint64_t* words = reinterpret_cast<uint64_t*>(ranges + RBL_MAX_RANGES);              // [ga][p_pad]
+    int2* ranges = reinterpret_cast<int2*>(smem + lay.warps + lay.wbytes * wib);          // [RBL_MAX_RANGES]
+    unsigned* rstart = reinterpret_cast<unsigned*>(ranges + RBL_MAX_RANGES);              // [RBL_MAX_PACKED / 32]
+    uint64_t* words = reinterpret_cast<uint64_t*>(rstart + RBL_MAX_PACKED / 32);         // [ga][p_pad]
     int* core_buf = reinterpret_cast<int*>(words + (size_t)p_pad * lay.ga);
     int* shell_buf = core_buf + a.core_cap;
     int* sel = shell_buf + a.shell_cap;
@@ -641,18 +651,26 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                         if (lane >= o) incl += t;
                     }
                     const int T = __shfl_sync(FULL, incl, 31) & 0xffff;
-                    int v = (incl - own) & 0xffff, k = (incl - own) >> 16;
-                    if (n1 > 0) {
-                        ranges[k++] = make_int4(v + n1, b1 - v, b1 + o1 - v, 0);
-                        v += n1;
+                    if (T <= RBL_MAX_PACKED) {
+                        for (int w = lane; w < ((T + 31) >> 5); w += 32) rstart[w] = 0u;
+                        __syncwarp();
+                        int v = (incl - own) & 0xffff, k = (incl - own) >> 16;
+                        if (n1 > 0) {
+                            ranges[k++] = make_int2(b1 - v, b1 + o1 - v);
+                            atomicOr(&rstart[v >> 5], 1u << (v & 31));
+                            v += n1;
+                        }
+                        if (n2 > 0) {
+                            ranges[k] = make_int2(b2 - v, b2 + o2 - v);
+                            atomicOr(&rstart[v >> 5], 1u << (v & 31));
+                        }
+                        __syncwarp();
+                        if (T > 0)
+                            classify_packed(stage, ranges, rstart, T, fi4.x, fi4.y, fi4.z, a, i, si, lane, lt_mask,
+                                            core_buf, shell_buf, ncore, nshell, overlap);
+                        __syncwarp();        // the tables are rewritten by the next pass
+                        continue;
                     }
-                    if (n2 > 0) ranges[k] = make_int4(v + n2, b2 - v, b2 + o2 - v, 0);
-                    __syncwarp();
-                    if (T > 0)
-                        classify_packed(stage, ranges, T, fi4.x, fi4.y, fi4.z, a, i, si, lane, lt_mask, core_buf,
-                                        shell_buf, ncore, nshell, overlap);
-                    __syncwarp();            // the table is rewritten by the next pass
-                    continue;
                 }
                 // walk the non-empty segments in canonical order
                 const unsigned m1 = __ballot_sync(FULL, e1 > b1), m2 = __ballot_sync(FULL, e2 > b2);
@@ -1062,6 +1080,29 @@ int rbl_smem_bytes(const rbe_ctx* ctx)
 }
 
 size_t rbl_args_bytes() { return sizeof(RblArgs); }
+
+// Dynamic shared memory per block that leaves room for two resident blocks of
+// every form of the pair kernel on the current device: half the SM's shared
+// memory, less the per-block reservation and the largest static shared
+// memory of the forms (the batched form also keeps its arguments there).
+int rbl_smem_target()
+{
+    static int cached = 0;
+    if (cached > 0) return cached;
+    int dev = 0, per_sm = 0, reserved = 0;
+    cudaFuncAttributes f1, f2;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&f1, k_rbl<true, false, false>) != cudaSuccess ||
+        cudaFuncGetAttributes(&f2, k_rbl_batch<true, true>) != cudaSuccess) {
+        cudaGetLastError();
+        return 110 * 1024;
+    }
+    const size_t st = f1.sharedSizeBytes > f2.sharedSizeBytes ? f1.sharedSizeBytes : f2.sharedSizeBytes;
+    cached = per_sm / 2 - reserved - (int)st;
+    return cached;
+}
 
 void rbl_fill_args(const rbe_ctx* ctx, int n, void* out)
 {

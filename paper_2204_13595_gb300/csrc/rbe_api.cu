@@ -193,9 +193,8 @@ void rbl_geometry(rbe_ctx* ctx, int n)
     double apc = (double)n / ((double)nc * nc * nc);
     int naxis = g.small ? nc : 2 * R + 1;
     g.nrows = naxis * naxis;
-    // shared memory per block: two resident blocks per SM (228 KB per SM, of
-    // which 1 KB per block is reserved and under 1 KB is static)
-    const int target = 112 * 1024;
+    // shared memory per block: two resident blocks per SM
+    const int target = rbl_smem_target();
     const double apu = ctx->tune_apu > 0 ? (double)ctx->tune_apu : 48.0;
     int G = (int)lrint(apu / (apc > 1e-9 ? apc : 1e-9));
     G = G < 1 ? 1 : (G > nc ? nc : G);

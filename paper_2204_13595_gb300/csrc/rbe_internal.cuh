@@ -347,6 +347,7 @@ void launch_langevin_batch(const BatchPlan& bp, const int* mask, cudaStream_t st
 void launch_ke_trace(rbe_ctx* ctx, int n, const double* vel, const double* mass, double accel,
                      double* trace_slot, cudaStream_t st);
 int rbl_smem_bytes(const rbe_ctx* ctx);
+int rbl_smem_target();
 // validation and device set-up of one context for n atoms (rbe_api.cu)
 int ctx_prepare(rbe_ctx* ctx, int n);
 // Langevin force buffer of a context for n atoms (rbe_api.cu)
