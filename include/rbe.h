@@ -308,7 +308,7 @@ int rbe_get_langevin_force(rbe_ctx* ctx, int n, double* FL, uint64_t* step);
 int rbe_set_langevin_force(rbe_ctx* ctx, int n, const double* FL, uint64_t step);
 
 /* Work decomposition of the RBL pair kernel (Sec. 2.3 stencil walk): a work
- * unit is a run of cells along x holding about atoms_per_unit atoms (0: 48;
+ * unit is a run of cells along x holding about atoms_per_unit atoms (0: 64;
  * shared memory caps the width); the kernel's grid has
  * ceil(units / units_per_slot) slots, one block each (0: about three units
  * per slot, and no fewer slots than one wave of resident blocks).  Results do not depend on the unit

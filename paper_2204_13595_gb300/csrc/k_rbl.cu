@@ -394,6 +394,13 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     double* s_dsds = s_dsde + nt2;
     double* s_rc2 = s_dsds + nt2;           // squared LJ cutoff per pair type
     double* s_glj = s_rc2 + nt2;            // adjoint: [4][nt2] block accumulators
+    // mixed forces: FP32 copies of c12, c6, shift and the cutoff, held where
+    // the adjoint keeps eps_ab and sigma_ab (one conversion per block, none
+    // per pair)
+    float* f_c12 = reinterpret_cast<float*>(s_eps);
+    float* f_c6 = f_c12 + nt2;
+    float* f_sh = f_c6 + nt2;
+    float* f_rc2 = f_sh + nt2;
     int2* ranges = reinterpret_cast<int2*>(smem + lay.warps + lay.wbytes * wib);          // [RBL_MAX_RANGES]
     unsigned* rstart = reinterpret_cast<unsigned*>(ranges + RBL_MAX_RANGES);              // [RBL_MAX_PACKED / 32]
     uint64_t* words = reinterpret_cast<uint64_t*>(rstart + RBL_MAX_PACKED / 32);         // [ga][p_pad]
@@ -409,6 +416,12 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
         s_c6[t] = a.lj->c6[ti * RBE_MAXT + tj];
         s_sh[t] = a.lj->shift[ti * RBE_MAXT + tj];
         s_rc2[t] = a.lj->rc2[ti * RBE_MAXT + tj];
+        if (MIXED && !ADJ) {
+            f_c12[t] = (float)s_c12[t];
+            f_c6[t] = (float)s_c6[t];
+            f_sh[t] = (float)s_sh[t];
+            f_rc2[t] = (float)s_rc2[t];
+        }
         if (ADJ) {
             s_eps[t] = a.lj->eps[ti * RBE_MAXT + tj];
             s_sig[t] = a.lj->sig[ti * RBE_MAXT + tj];
@@ -862,12 +875,12 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     const float ucoul = qq * ec * rinv;
                     float s = -qq * (ec * rinv + gauss) * rinv * rinv;
                     const int tt = ti.x * c.ntypes + tj.x;
-                    const bool nolj = ex || !(r2 < (float)s_rc2[tt]);
-                    const float c12 = nolj ? 0.f : (float)s_c12[tt], c6 = nolj ? 0.f : (float)s_c6[tt];
+                    const bool nolj = ex || !(r2 < f_rc2[tt]);
+                    const float c12 = nolj ? 0.f : f_c12[tt], c6 = nolj ? 0.f : f_c6[tt];
                     const float ir2 = rinv * rinv;
                     const float ir6 = ir2 * ir2 * ir2;
                     s -= (12.f * c12 * ir6 - 6.f * c6) * ir6 * ir2;
-                    const float ulj = (c12 * ir6 - c6) * ir6 - (nolj ? 0.f : (float)s_sh[tt]);
+                    const float ulj = (c12 * ir6 - c6) * ir6 - (nolj ? 0.f : f_sh[tt]);
                     const float gx = w * s * dx, gy = w * s * dy, gz = w * s * dz;
                     ff[0] += gx; ff[1] += gy; ff[2] += gz;
                     facc_e[0] += ex ? 0.f : w * ucoul;

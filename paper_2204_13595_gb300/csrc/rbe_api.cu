@@ -195,14 +195,17 @@ void rbl_geometry(rbe_ctx* ctx, int n)
     g.nrows = naxis * naxis;
     // shared memory per block: two resident blocks per SM
     const int target = rbl_smem_target();
-    const double apu = ctx->tune_apu > 0 ? (double)ctx->tune_apu : 48.0;
+    const double apu = ctx->tune_apu > 0 ? (double)ctx->tune_apu : 64.0;
     int G = (int)lrint(apu / (apc > 1e-9 ? apc : 1e-9));
     G = G < 1 ? 1 : (G > nc ? nc : G);
     for (;; --G) {
         g.G = G;
         g.cells_per_row = g.small ? nc : G + 2 * R;
         double region = g.small ? (double)n : (double)g.cells_per_row * g.nrows * apc;
-        int cap = (int)ceil(1.3 * region + 256.0);
+        // the mean region plus eight Poisson standard deviations and a
+        // margin; a unit beyond it reads global memory instead (correct,
+        // slower: only strongly inhomogeneous systems get there)
+        int cap = (int)ceil(region + 8.0 * sqrt(region) + 256.0);
         cap = (cap + 63) / 64 * 64;
         const int maxcap = (96 * 1024) / 16;
         g.cap_stage = cap < maxcap ? cap : maxcap;
