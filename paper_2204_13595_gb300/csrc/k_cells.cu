@@ -23,26 +23,42 @@ __device__ __forceinline__ void quantize_count_body(int bx, int nbx, int n, cons
                                                     double* __restrict__ part_q, int* __restrict__ status)
 {
     double sq2 = 0.0, sq = 0.0, sabs = 0.0;
-    for (int i = bx * TPB + threadIdx.x; i < n; i += nbx * TPB) {
-        double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-        double qi = q[i];
-        if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) {
-            latch_status(status, RBE_ST_NONFINITE);
-            x = y = z = 0.0;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    // block-uniform trip count, so that every lane takes part in the warp
+    // vote below; lanes of a warp that fall in the same cell share one atomic
+    // (the slot order inside a cell is immaterial: the in-cell sort orders
+    // the cell by its keys)
+    for (int b0 = bx * TPB; b0 < n; b0 += nbx * TPB) {
+        const int i = b0 + threadIdx.x;
+        const bool ok = i < n;
+        int cell = -1;
+        if (ok) {
+            double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+            double qi = q[i];
+            if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) {
+                latch_status(status, RBE_ST_NONFINITE);
+                x = y = z = 0.0;
+            }
+            double xw;
+            uint32_t sx, sy, sz;
+            wrap_fixed(x, c.invL, c.L, xw, sx);
+            wrap_fixed(y, c.invL, c.L, xw, sy);
+            wrap_fixed(z, c.invL, c.L, xw, sz);
+            uint32_t cx = cell_of_fixed(sx, c.n_cell), cy = cell_of_fixed(sy, c.n_cell), cz = cell_of_fixed(sz, c.n_cell);
+            cell = (int)(cx + (uint32_t)c.n_cell * (cy + (uint32_t)c.n_cell * cz));
+            cell_of[i] = cell;
+            sx_of[i] = sx;
+            sq2 += qi * qi;
+            sq += qi;
+            sabs += fabs(qi);
         }
-        double xw;
-        uint32_t sx, sy, sz;
-        wrap_fixed(x, c.invL, c.L, xw, sx);
-        wrap_fixed(y, c.invL, c.L, xw, sy);
-        wrap_fixed(z, c.invL, c.L, xw, sz);
-        uint32_t cx = cell_of_fixed(sx, c.n_cell), cy = cell_of_fixed(sy, c.n_cell), cz = cell_of_fixed(sz, c.n_cell);
-        int cell = (int)(cx + (uint32_t)c.n_cell * (cy + (uint32_t)c.n_cell * cz));
-        cell_of[i] = cell;
-        sx_of[i] = sx;
-        slot[i] = atomicAdd(&cell_count[cell], 1);
-        sq2 += qi * qi;
-        sq += qi;
-        sabs += fabs(qi);
+        const unsigned peers = __match_any_sync(FULL, cell);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (ok && lane == leader) base = atomicAdd(&cell_count[cell], __popc(peers));
+        base = __shfl_sync(FULL, base, leader);
+        if (ok) slot[i] = base + __popc(peers & ((1u << lane) - 1u));
     }
     __shared__ double red[3][TPB / 32];
     sq2 = warp_sum(sq2); sq = warp_sum(sq); sabs = warp_sum(sabs);
@@ -215,34 +231,41 @@ __global__ void __launch_bounds__(TPB) k_scatter(int n, const int* __restrict__ 
     scatter_body(blockIdx.x, n, cell_of, slot, sx_of, start, skey);
 }
 
-// Canonical in-cell order: ascending (fixed-point x code, caller index)
-// (insertion sort on the 64-bit key, cells are small).  Sorting by x lets the
-// pair kernel drop, by binary search, the atoms of a stencil row's end cells
-// that lie beyond r_s along x.
-__device__ __forceinline__ void sort_cells_body(int bx, long m, const int* __restrict__ start,
-                                                unsigned long long* __restrict__ skey, int* __restrict__ perm)
+// Canonical in-cell order: ascending (fixed-point x code, caller index).
+// Sorting by x lets the pair kernel drop, by binary search, the atoms of a
+// stencil row's end cells that lie beyond r_s along x.  A warp per cell (cells
+// taken warp-strided): the keys are distinct (the caller index is in the low
+// word), so each key's place is the number of smaller keys of its cell,
+// counted over the warp by shuffles (cells of more than 32 atoms count from
+// memory).
+__device__ __forceinline__ void sort_cells_body(int bx, int nbx, long m, const int* __restrict__ start,
+                                                const unsigned long long* __restrict__ skey, int* __restrict__ perm)
 {
-    long c = (long)bx * TPB + threadIdx.x;
-    if (c >= m) return;
-    int b = start[c], e = start[c + 1];
-    for (int k = b + 1; k < e; ++k) {
-        const unsigned long long kv = skey[k];
-        int t = k - 1;
-        while (t >= b) {
-            const unsigned long long ku = skey[t];
-            if (ku <= kv) break;
-            skey[t + 1] = ku;
-            --t;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long nw = (long)nbx * (TPB / 32);
+    for (long c = (long)bx * (TPB / 32) + (threadIdx.x >> 5); c < m; c += nw) {
+        const int b = start[c], cnt = start[c + 1] - b;
+        if (cnt <= 32) {
+            const unsigned long long key = lane < cnt ? skey[b + lane] : ~0ull;
+            int rank = 0;
+            for (int k = 0; k < cnt; ++k) rank += __shfl_sync(FULL, key, k) < key ? 1 : 0;
+            if (lane < cnt) perm[b + rank] = (int)(unsigned)(key & 0xffffffffull);
+        } else {
+            for (int t = lane; t < cnt; t += 32) {
+                const unsigned long long key = skey[b + t];
+                int rank = 0;
+                for (int k = 0; k < cnt; ++k) rank += skey[b + k] < key ? 1 : 0;
+                perm[b + rank] = (int)(unsigned)(key & 0xffffffffull);
+            }
         }
-        skey[t + 1] = kv;
     }
-    for (int k = b; k < e; ++k) perm[k] = (int)(unsigned)(skey[k] & 0xffffffffull);
 }
 
 __global__ void __launch_bounds__(TPB) k_sort_cells(long m, const int* __restrict__ start,
-                                                    unsigned long long* __restrict__ skey, int* __restrict__ perm)
+                                                    const unsigned long long* __restrict__ skey, int* __restrict__ perm)
 {
-    sort_cells_body(blockIdx.x, m, start, skey, perm);
+    sort_cells_body(blockIdx.x, gridDim.x, m, start, skey, perm);
 }
 
 __device__ __forceinline__ void gather_body(int bx, int n, const int* __restrict__ perm, const double* __restrict__ pos,
@@ -324,7 +347,7 @@ __global__ void __launch_bounds__(TPB) k_sort_cells_b(const RepDev* __restrict__
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    sort_cells_body(bx, d.ncells, d.cell_start, d.skey, d.perm);
+    sort_cells_body(bx, nbx, d.ncells, d.cell_start, d.skey, d.perm);
 }
 
 __global__ void __launch_bounds__(TPB) k_gather_b(const RepDev* __restrict__ R, const int* __restrict__ off, int nrep)
@@ -370,8 +393,9 @@ void launch_scatter_sort_gather(rbe_ctx* ctx, int n, const double* pos, const do
     k_scatter<<<g, TPB, 0, st>>>(n, ctx->cell_of, ctx->slot, ctx->sx_of, ctx->cell_start, ctx->skey);
     prof_end(ctx, RBE_K_SCATTER, st);
     prof_begin(ctx, RBE_K_SORT, st);
-    k_sort_cells<<<(unsigned)((ctx->ncells + TPB - 1) / TPB), TPB, 0, st>>>(ctx->ncells, ctx->cell_start,
-                                                                            ctx->skey, ctx->perm);
+    const long wpb = TPB / 32;        // a warp per cell
+    k_sort_cells<<<(unsigned)((ctx->ncells + wpb - 1) / wpb), TPB, 0, st>>>(ctx->ncells, ctx->cell_start, ctx->skey,
+                                                                            ctx->perm);
     prof_end(ctx, RBE_K_SORT, st);
     prof_begin(ctx, RBE_K_GATHER, st);
     k_gather<<<g, TPB, 0, st>>>(n, ctx->perm, pos, q, type, mol, ctx->c, ctx->s4, ctx->f4, ctx->p4, ctx->tm,

@@ -349,38 +349,54 @@ __device__ double block_sum_col(const double* __restrict__ src, int nrow, int st
     return block_reduce(s, sh);
 }
 
-// Fixed-order block reduction of the rows of a row-major [nrow][NC] table:
-// thread t sums rows t, t + blockDim, ... (each row one contiguous read),
-// then a block reduction, column by column.
-template <int NC>
-__device__ void block_sum_rows(const double* __restrict__ src, int nrow, double* out, double* sh)
-{
-    double acc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-    for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
-        const double* row = src + (size_t)r * NC;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] += row[c];
-    }
-    for (int c = 0; c < NC; ++c) out[c] = block_reduce(acc[c], sh);
-}
-
 // totals: E[0..5], W[6..11], corr[12..14]
+// Each of the 23 sums (the rows of the pair kernel's [grid][12] partials,
+// the columns of the charge and k-term partials, the bond partials) is taken
+// in one fixed order: thread t sums rows t, t + blockDim, ..., then a warp
+// butterfly, then the warp results in warp order (the order of block_sum_col);
+// the sums share one block barrier.
+constexpr int FIN_NV = RBE_NPART_RBL + RBE_NPART_Q + 7 + 1;
 __device__ __forceinline__ void finalize_body(int n, const RbeConsts& c, const double* __restrict__ part_rbl,
                                               int grid_rbl, const double* __restrict__ part_q, int grid_q,
                                               const double* __restrict__ kterms, const double* __restrict__ part_bond,
                                               int grid_bond, double* __restrict__ totals, int* __restrict__ status)
 {
-    __shared__ double sh[FIN_TPB];
-    double r[RBE_NPART_RBL];
-    block_sum_rows<RBE_NPART_RBL>(part_rbl, grid_rbl, r, sh);
-    double qs[RBE_NPART_Q];
-    for (int q = 0; q < RBE_NPART_Q; ++q) qs[q] = block_sum_col(part_q, grid_q, RBE_NPART_Q, q, sh);
-    double kt[7];
-    for (int q = 0; q < 7; ++q) kt[q] = block_sum_col(kterms, c.P, 7, q, sh);
-    double eb = grid_bond > 0 ? block_sum_col(part_bond, grid_bond, 1, 0, sh) : 0.0;
+    __shared__ double sh[FIN_TPB / 32][FIN_NV];
+    double v[FIN_NV];
+#pragma unroll
+    for (int q = 0; q < FIN_NV; ++q) v[q] = 0.0;
+#pragma unroll 4
+    for (int r = threadIdx.x; r < grid_rbl; r += blockDim.x) {
+        const double* row = part_rbl + (size_t)r * RBE_NPART_RBL;
+#pragma unroll
+        for (int q = 0; q < RBE_NPART_RBL; ++q) v[q] += row[q];
+    }
+#pragma unroll 4
+    for (int r = threadIdx.x; r < grid_q; r += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < RBE_NPART_Q; ++q) v[RBE_NPART_RBL + q] += part_q[(size_t)r * RBE_NPART_Q + q];
+    }
+    for (int r = threadIdx.x; r < c.P; r += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) v[RBE_NPART_RBL + RBE_NPART_Q + q] += kterms[(size_t)r * 7 + q];
+    }
+    for (int r = threadIdx.x; r < grid_bond; r += blockDim.x) v[FIN_NV - 1] += part_bond[r];
+#pragma unroll
+    for (int q = 0; q < FIN_NV; ++q) v[q] = warp_sum(v[q]);
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < FIN_NV; ++q) sh[threadIdx.x >> 5][q] = v[q];
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double t[FIN_NV];
+        for (int q = 0; q < FIN_NV; ++q) {
+            double a = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a += sh[k][q];
+            t[q] = a;
+        }
+        const double* r = t;
+        const double* qs = t + RBE_NPART_RBL;
+        const double* kt = qs + RBE_NPART_Q;
+        const double eb = t[FIN_NV - 1];
         totals[0] = 0.5 * r[0];
         totals[1] = kt[0];
         totals[2] = -c.k_e * sqrt(c.alpha / 3.14159265358979323846) * qs[0];
