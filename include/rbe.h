@@ -185,7 +185,10 @@ int rbe_get_kspace(rbe_ctx* ctx, int32_t* m, double* rho, void* cuda_stream);
  * out[5] shell capacity (after the last rbe_forces), out[6] kernel launches
  * of the last rbe_forces, out[7] work units of the last pair-kernel launch
  * whose stencil exceeded the shared-memory staging capacity and was read
- * from global memory (counted with rbe_set_debug on; -1 otherwise). */
+ * from global memory, out[8] (atom, pass of 32 stencil rows) pairs of that
+ * launch whose candidates (more than 2048) were classified range by range
+ * instead of as one concatenated list (both counted with rbe_set_debug on;
+ * -1 otherwise). */
 int rbe_get_info(rbe_ctx* ctx, double* out, int nout);
 
 /* Kernel timing: when on, every launch is bracketed by CUDA events on its

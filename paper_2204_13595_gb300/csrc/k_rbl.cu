@@ -664,6 +664,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                         if (lane >= o) incl += t;
                     }
                     const int T = __shfl_sync(FULL, incl, 31) & 0xffff;
+                    if (a.debug && T > RBL_MAX_PACKED && lane == 0) atomicAdd(a.dbg_unstaged + 1, 1);
                     if (T <= RBL_MAX_PACKED) {
                         for (int w = lane; w < ((T + 31) >> 5); w += 32) rstart[w] = 0u;
                         __syncwarp();
@@ -1148,7 +1149,7 @@ void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st, bool adjoin
     rbl_fill_args(ctx, n, &a);
     a.step = step;
     if (adjoint) a.debug = 0;
-    if (a.debug) cudaMemsetAsync(ctx->dbg_unstaged, 0, sizeof(int), st);
+    if (a.debug) cudaMemsetAsync(ctx->dbg_unstaged, 0, 2 * sizeof(int), st);
     int smem = rbl_smem_bytes(ctx);
     prof_begin(ctx, RBE_K_RBL, st);
     const bool small = ctx->rbl.small;

@@ -373,7 +373,7 @@ int ensure(rbe_ctx* ctx, int n)
         if ((rc = grow(ctx, &ctx->dbg_nshell, &ctx->cap_atoms[14], n))) return rc;
         if ((rc = grow(ctx, &ctx->dbg_core, &ctx->cap_atoms[15], (size_t)n * cc))) return rc;
         if ((rc = grow(ctx, &ctx->dbg_batch, &ctx->cap_atoms[16], (size_t)n * ctx->c.p))) return rc;
-        if ((rc = grow(ctx, &ctx->dbg_unstaged, &ctx->cap_atoms[22], 1))) return rc;
+        if ((rc = grow(ctx, &ctx->dbg_unstaged, &ctx->cap_atoms[22], 2))) return rc;
         ctx->dbg_n_cap = n;
     }
     return RBE_OK;
@@ -858,12 +858,12 @@ int rbe_get_kspace(rbe_ctx* ctx, int32_t* m, double* rho, void* cuda_stream)
 int rbe_get_info(rbe_ctx* ctx, double* out, int nout)
 {
     if (!ctx || !out) return RBE_EINVAL;
-    int unstaged = -1;
+    int dbg[2] = {-1, -1};
     if (nout > 7 && ctx->debug && ctx->dbg_unstaged)
-        CUDA_TRY(ctx, cudaMemcpy(&unstaged, ctx->dbg_unstaged, sizeof(int), cudaMemcpyDeviceToHost));
-    double v[8] = {(double)ctx->c.n_cell, (double)ctx->c.reach, (double)ctx->c.M, ctx->c.S, (double)ctx->core_cap,
-                   (double)ctx->shell_cap, (double)ctx->last_launches, (double)unstaged};
-    for (int k = 0; k < nout && k < 8; ++k) out[k] = v[k];
+        CUDA_TRY(ctx, cudaMemcpy(dbg, ctx->dbg_unstaged, sizeof(dbg), cudaMemcpyDeviceToHost));
+    double v[9] = {(double)ctx->c.n_cell, (double)ctx->c.reach, (double)ctx->c.M, ctx->c.S, (double)ctx->core_cap,
+                   (double)ctx->shell_cap, (double)ctx->last_launches, (double)dbg[0], (double)dbg[1]};
+    for (int k = 0; k < nout && k < 9; ++k) out[k] = v[k];
     return RBE_OK;
 }
 

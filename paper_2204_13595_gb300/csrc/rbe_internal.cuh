@@ -133,7 +133,7 @@ struct rbe_ctx {
     int* dbg_nshell;
     int* dbg_core;
     int* dbg_batch;
-    int* dbg_unstaged;       // debug: pair-kernel units of the last launch read from global memory
+    int* dbg_unstaged;       // debug [2]: pair-kernel units read from global memory, passes walked range by range
     int dbg_n_cap;
     // host staging for host-pointer calls
     double* h_pos; double* h_q; int* h_type; int* h_mol; double* h_F;

@@ -2,9 +2,11 @@
 shared-memory staging capacity is classified from the staged copy (positions
 moved to the unit's periodic images, candidate ranges concatenated into full
 32-wide chunks); a unit that does not fit reads its ranges from global memory
-one range at a time.  Both must give the oracle's lists bit for bit.  An ion
-system with half of its atoms in a slab a tenth of the box thick makes part of
-the units overflow (counted by the library in debug mode)."""
+one range at a time, and so does a pass of stencil rows whose concatenation
+exceeds 2048 candidates.  All must give the oracle's lists bit for bit.  An
+ion system with half of its atoms in a slab a tenth of the box thick makes part
+of the units overflow, a uniform one at 2 ions per sigma^3 part of the passes
+(both counted by the library in debug mode)."""
 import numpy as np
 import pytest
 
@@ -56,3 +58,22 @@ def test_uniform_systems_stage_every_unit():
         assert out["status"] == 0
         assert ctx.info()["unstaged_units"] == 0, s.name
     assert np.isfinite(out["F"]).all()
+
+
+def test_long_passes_walk_range_by_range():
+    s = systems.slab_ions(n=12000, L=18.0, slab_frac=0.0, seed=5)
+    step = 3
+    pr = params(s)
+    ol = oracle.lists(s.pos, pr, step, cap_core=CAP)
+    c = rbe.Context(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, s.seed, k_e=s.k_e, eps=s.eps, sigma=s.sigma)
+    c.set_debug(True, CAP)
+    out = gpu_forces(s, step, ctx=c, debug_cap=CAP)
+    assert out["status"] == 0
+    info = c.info()
+    assert info["unstaged_units"] == 0
+    assert 0 < info["walked_passes"] < s.n, info["walked_passes"]
+    L = out["lists"]
+    assert (L["n_core"] == ol["n_core"]).all() and (L["n_shell"] == ol["n_shell"]).all()
+    assert (L["core"] == ol["core"]).all() and (L["batch"] == ol["batch"]).all()
+    ref = oracle.rbe_forces(s.pos, s.q, s.type, s.mol, pr, step)
+    assert cond_err(out["F"], ref) < 1e-11
