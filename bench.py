@@ -18,7 +18,9 @@ size (1,000 to 50,000 atoms, log-uniform, electrolyte and water, each its own
 box, alpha and P) stepped together for 500 velocity-Verlet steps by the
 batched path (one launch per stage, a persistent pair kernel over all
 replicas, one CUDA graph per step, tiling autotuned), against looping the
-single-system rbe_step over the replicas; aggregate atom-steps/s of both.
+single-system rbe_step over the replicas; aggregate atom-steps/s of both.  A
+"next_rows" object times the adjoint (12,000-atom water), the method variants
+(1.2M atoms) and Langevin dynamics of the paper's 5,120-ion electrolyte.
 
 --impl reference times the plain CPU oracle (the same estimator in FP64 C)
 on the host cores, one full force evaluation of the same system per step.
@@ -287,6 +289,95 @@ def _batch_leg(flush):
     }
 
 
+def _next_rows_leg(flush, big):
+    """Timing of the widened rows beside the headline (each after its own
+    warm-up, CUDA events on the launching stream): the adjoint at frozen draws
+    (row f1) on the 12,000-atom water box of the differentiation workload
+    against the forward call on the same box; the method variants (row f3) on
+    the 1.2M-atom box; Langevin dynamics (row f4) on the paper's 5,120-ion 1:1
+    electrolyte with WCA soft spheres (Sec. 3.1)."""
+    import numpy as np
+    import torch
+
+    from paper_2204_13595_gb300 import rbe, systems
+
+    stream = torch.cuda.current_stream()
+    dev = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device="cuda")
+
+    def events(fn, n):
+        tot = 0.0
+        for k in range(n):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(k)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / n
+
+    out = {}
+    # f1: adjoint (dE/dq, dL/dq, dL/d(eps, sigma) of L = sum gF . F) at frozen draws
+    w = systems.water(4000, seed=4)
+    pos, q, typ, mol = dev(w.pos), dev(w.q), dev(w.type, torch.int32), dev(w.mol, torch.int32)
+    gF = dev(np.random.default_rng(4).normal(size=w.pos.shape))
+    F = torch.empty_like(pos)
+    adj = {"workload": "water-like 12,000 atoms (4,000 molecules, seed 4), r_c=5, r_s=10, p=20, P=200; "
+                       "frozen draws (same step)"}
+    for name, prec in (("mixed", rbe.MIXED), ("fp64", rbe.FP64)):
+        c = rbe.Context.for_system(w, precision=prec)
+        for k in range(3):
+            c.forces(7, pos, q, typ, mol, F)
+            c.adjoint(7, pos, q, typ, mol, gF)
+        f_ms = events(lambda k: c.forces(7, pos, q, typ, mol, F), 10)
+        a_ms = events(lambda k: c.adjoint(7, pos, q, typ, mol, gF), 10)
+        if c.sync_status() != 0:
+            raise RuntimeError("device status error in the adjoint leg")
+        adj[name] = {"forces_ms": f_ms, "adjoint_ms": a_ms, "adjoint_over_forces": a_ms / f_ms}
+        c.close()
+    out["adjoint"] = adj
+
+    # f3: variants of the method on the 1.2M-atom box (mixed)
+    s, bpos, bq, btyp, bmol = big
+    F = torch.empty_like(bpos)
+    var = {"workload": "the headline's 1.2M-atom water box, mixed"}
+    for name, setup in (("shell_with_replacement", lambda c: c.set_shell_sampling(rbe.SHELL_REPLACE)),
+                        ("k_pool_mh_4096", lambda c: c.set_kpool(4096, 64))):
+        c = rbe.Context(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, SEED, k_e=s.k_e, eps=s.eps, sigma=s.sigma,
+                        precision=rbe.MIXED)
+        setup(c)
+        for k in range(3):
+            c.forces(k, bpos, bq, btyp, bmol, F)
+        ms = events(lambda k: c.forces(3 + k, bpos, bq, btyp, bmol, F), 5)
+        if c.sync_status() != 0:
+            raise RuntimeError("device status error in the variants leg")
+        var[name] = {"force_evals_per_s": 1e3 / ms, "ms_per_step": ms}
+        c.close()
+    out["variants"] = var
+
+    # f4: Langevin dynamics of the paper's 1:1 electrolyte (WCA, kT = 1, tau = 1)
+    e = systems.electrolyte(n=5120, L=80.0, seed=21, r_c=5.0, r_s=15.0, p=10, P=100, dt=0.002)
+    c = rbe.Context(e.L, 0.03, e.r_c, e.r_s, e.p, e.P, 21, k_e=e.k_e, eps=e.eps, sigma=e.sigma, shift_lj=True,
+                    precision=rbe.MIXED)
+    c.set_lj_cutoff(2.0 ** (1.0 / 6.0))
+    c.set_langevin(1.0, 1.0)
+    d = dict(pos=dev(e.pos), vel=dev(e.vel), mass=dev(e.mass), q=dev(e.q), typ=dev(e.type, torch.int32),
+             F=torch.zeros((e.n, 3), dtype=torch.float64, device="cuda"))
+    c.forces(0, d["pos"], d["q"], d["typ"], None, d["F"])
+    c.step(0, 50, e.dt, e.accel, d["pos"], d["vel"], d["mass"], d["q"], d["typ"], None, d["F"])
+    nsteps = 500
+    ms = events(lambda k: c.step(50, nsteps, e.dt, e.accel, d["pos"], d["vel"], d["mass"], d["q"], d["typ"], None,
+                                 d["F"]), 1) / nsteps
+    if c.sync_status() != 0:
+        raise RuntimeError("device status error in the Langevin leg")
+    out["langevin"] = {"workload": "1:1 electrolyte, 5,120 ions, L=80 sigma, WCA, r_c=5, r_s=15, p=10, P=100, "
+                                   "alpha=0.03, dt=0.002, kT=1, tau=1, mixed",
+                       "steps_per_s": 1e3 / ms, "ms_per_step": ms, "tau_per_day": 1e3 / ms * e.dt * 86400.0,
+                       "atom_steps_per_s": e.n * 1e3 / ms}
+    c.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -364,6 +455,7 @@ def run_ours(args):
     ms_mixed, prof, launches = timed(mixed, args.steps, args.warmup, profile=True)
     ms_f64, _, _ = timed(f64, max(3, min(args.steps, 10)), max(3, min(args.warmup, 3)))
     batch = _batch_leg(flush) if ws == 1 else None
+    next_rows = _next_rows_leg(flush, (s, pos, q, typ, mol)) if ws == 1 else None
     clocks = _clock_summary(clocks_proc, local) if rank == 0 else None
 
     # end to end through the same C ABI with pinned host buffers
@@ -431,6 +523,7 @@ def run_ours(args):
         "e2e": {"value": replicas.throughput(ws, 1, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks, "gpu_launches": launches * args.steps,
         "batch": batch,
+        "next_rows": next_rows,
     }
     print(json.dumps(line))
     if ws > 1:
