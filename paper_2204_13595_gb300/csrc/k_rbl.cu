@@ -299,8 +299,8 @@ __device__ __forceinline__ void exact_class(const RblArgs& a, int i, uint4 si, i
 // chunks go, the rest from the chunk's bitmap word, so every chunk but the
 // last is full whatever the lengths of the ranges.  The staged positions
 // carry their image shifts, so every candidate is compared with atom i's
-// position (xi, yi, zi).  Two chunks per iteration, appended in order, as in
-// the per-range walk.
+// position (xi, yi, zi).  Four chunks per iteration (then two, then one),
+// appended in order, as in the per-range walk.
 __device__ __forceinline__ void classify_packed(const float4* __restrict__ stage, const int2* __restrict__ ranges,
                                                 const unsigned* __restrict__ rstart, int T, float xi, float yi,
                                                 float zi, const RblArgs& a, int i, uint4 si, int lane,
@@ -312,6 +312,53 @@ __device__ __forceinline__ void classify_packed(const float4* __restrict__ stage
     const unsigned le_mask = lt_mask | (1u << lane);
     int before = 0;                       // range starts below v0
     int v0 = 0;
+    // four chunks per iteration while at least three are full: their loads,
+    // distances and exact checks are independent (more work in flight per
+    // warp against the fixed-latency dependencies); appended in chunk order
+    for (; T - v0 > 96; v0 += 128) {
+        unsigned w[4];
+        int2 r[4];
+        float4 pp[4];
+        bool cc[4], ss[4], mm[4];
+        int gg[4];
+        int bc = before;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) w[c] = rstart[(v0 >> 5) + c];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            r[c] = ranges[bc + __popc(w[c] & le_mask) - 1];
+            bc += __popc(w[c]);
+        }
+        before = bc;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int v = v0 + 32 * c + lane;
+            const bool ok = c < 3 || v < T;
+            pp[c] = stage[ok ? v + r[c].x : v0 + lane + r[0].x];
+            gg[c] = v + r[c].y;
+        }
+        bool any_m = false;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const bool ok = c < 3 || (v0 + 96 + lane) < T;
+            dist_class<false>(pp[c], ok, xi, yi, zi, g, 0.f, 0.f, cc[c], ss[c], mm[c]);
+            any_m |= mm[c];
+        }
+        if (__any_sync(FULL, any_m)) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (mm[c]) exact_class(a, i, si, gg[c], cc[c], ss[c], overlap);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const unsigned cm = __ballot_sync(FULL, cc[c]), sm = __ballot_sync(FULL, ss[c]);
+            const int cp = ncore + __popc(cm & lt_mask), sp = nshell + __popc(sm & lt_mask);
+            if (cc[c] && cp < a.core_cap) core_buf[cp] = gg[c];
+            if (ss[c] && sp < a.shell_cap) shell_buf[sp] = gg[c];
+            ncore += __popc(cm);
+            nshell += __popc(sm);
+        }
+    }
     for (; T - v0 > 32; v0 += 64) {
         const unsigned wa = rstart[v0 >> 5], wb = rstart[(v0 >> 5) + 1];
         const int na = __popc(wa);
