@@ -161,7 +161,10 @@ int rbe_adjoint(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const dou
                 double* dLdeps, double* dLdsig, void* cuda_stream);
 
 /* Waits for cuda_stream, returns the first latched device error (or RBE_OK)
- * and clears the status word. */
+ * and clears the status word.  An evaluation whose input holds a non-finite
+ * position latches RBE_ENONFINITE and its result is undefined; such atoms are
+ * placed on a lattice at the system's density for the rest of that step, so a
+ * run that has blown up costs what a normal step costs until it is stopped. */
 int rbe_sync_status(rbe_ctx* ctx, void* cuda_stream);
 
 /* Debug recording: when on, rbe_forces also records per atom (indexed by the

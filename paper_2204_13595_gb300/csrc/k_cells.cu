@@ -15,6 +15,21 @@ constexpr int TPB = 256;
 // replica's grid explicitly (bx, nbx), so that the single-system kernel and
 // the batched one (one launch over many replicas) run the same code.
 
+// Stand-in position of an atom whose input position is not finite (the step
+// is reported as RBE_ENONFINITE and its result is undefined): the i-th point
+// of a cubic lattice of about n points filling the box, so that such atoms
+// spread over the cells at the system's own density instead of piling into
+// one cell, and the rest of the step costs what a normal step costs.
+__device__ __forceinline__ void nonfinite_stand_in(int i, int n, double L, double& x, double& y, double& z)
+{
+    int m = (int)cbrt((double)n);
+    while ((long)m * m * m < (long)n) ++m;
+    const double a = L / (double)m;
+    x = a * ((double)(i % m) + 0.5);
+    y = a * ((double)((i / m) % m) + 0.5);
+    z = a * ((double)(i / ((long)m * m)) + 0.5);
+}
+
 // Wrap, quantise, bin; latch non-finite input; per-block sums of q^2, q, |q|.
 __device__ __forceinline__ void quantize_count_body(int bx, int nbx, int n, const double* __restrict__ pos,
                                                     const double* __restrict__ q, const RbeConsts& c,
@@ -36,10 +51,9 @@ __device__ __forceinline__ void quantize_count_body(int bx, int nbx, int n, cons
         if (ok) {
             double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
             double qi = q[i];
-            if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) {
-                latch_status(status, RBE_ST_NONFINITE);
-                x = y = z = 0.0;
-            }
+            const bool bad_pos = !isfinite(x) || !isfinite(y) || !isfinite(z);
+            if (bad_pos || !isfinite(qi)) latch_status(status, RBE_ST_NONFINITE);
+            if (bad_pos) nonfinite_stand_in(i, n, c.L, x, y, z);     // the same rule as the gather
             double xw;
             uint32_t sx, sy, sz;
             wrap_fixed(x, c.invL, c.L, xw, sx);
@@ -279,7 +293,7 @@ __device__ __forceinline__ void gather_body(int bx, int n, const int* __restrict
     if (k >= n) return;
     int i = perm[k];
     double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) x = y = z = 0.0;
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) nonfinite_stand_in(i, n, c.L, x, y, z);
     double xw, yw, zw;
     uint32_t sx, sy, sz;
     wrap_fixed(x, c.invL, c.L, xw, sx);

@@ -171,6 +171,22 @@ def test_status_errors_without_faults():
     assert gpu_forces(s, 0)["status"] == rbe.ENONFINITE
 
 
+def test_nonfinite_input_is_reported_and_the_context_recovers():
+    """All positions non-finite: RBE_ENONFINITE is latched and the atoms are
+    placed on a lattice at the system's density for the rest of the step (not
+    piled into one cell); after the status is read, the next step on the same
+    context matches the oracle."""
+    s = systems.water(4000, seed=4)
+    ctx = rbe.Context(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, s.seed, k_e=s.k_e, eps=s.eps, sigma=s.sigma)
+    bad = systems.water(4000, seed=4)
+    bad.pos = np.full_like(s.pos, np.nan)
+    assert gpu_forces(bad, 1, ctx=ctx)["status"] == rbe.ENONFINITE
+    out = gpu_forces(s, 2, ctx=ctx)
+    assert out["status"] == 0
+    ref = oracle.rbe_forces(s.pos, s.q, s.type, s.mol, params(s), 2)
+    assert cond_err(out["F"], ref) < F_TOL
+
+
 def test_lists_exact_at_the_radii():
     """Pairs placed within 1e-9..1e-5 (relative) of r_c and r_s, in large and
     small boxes: the FP32 prefilter of the list kernel must defer to the exact
