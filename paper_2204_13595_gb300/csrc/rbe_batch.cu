@@ -487,8 +487,6 @@ int rbe_batch_autotune(rbe_batch* b, uint64_t step, double* out, int nout, void*
     if (rc) return rc;
     BATCH_TRY(b, cudaStreamSynchronize(st));
 
-    std::vector<int> apu(nr), ups(nr);
-    for (int r = 0; r < nr; ++r) { apu[r] = b->ctx[r]->tune_apu; ups[r] = b->ctx[r]->tune_ups; }
     auto apply = [&](int fam, int a, int u) {
         for (int r = 0; r < nr; ++r)
             if (b->family[r] == fam) rbe_set_rbl_tiling(b->ctx[r], a, u);
@@ -511,13 +509,13 @@ int rbe_batch_autotune(rbe_batch* b, uint64_t step, double* out, int nout, void*
         double best = best_all;
         for (int a : cand_apu) {
             apply(f, a, best_u);
-            double t;
+            double t = 0.0;
             if ((rc = measure(&t))) return rc;
             if (t < best) { best = t; best_a = a; }
         }
         for (int u : cand_ups) {
             apply(f, best_a, u);
-            double t;
+            double t = 0.0;
             if ((rc = measure(&t))) return rc;
             if (t < best) { best = t; best_u = u; }
         }
@@ -531,7 +529,7 @@ int rbe_batch_autotune(rbe_batch* b, uint64_t step, double* out, int nout, void*
     {
         const int cur = b->persistent;
         b->persistent = 1 - cur;
-        double t;
+        double t = 0.0;
         if ((rc = measure(&t))) return rc;
         if (!(t < best_all)) b->persistent = cur;
         else best_all = t;
