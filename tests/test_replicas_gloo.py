@@ -60,3 +60,59 @@ def test_single_process_defaults(monkeypatch):
     assert replicas.world() == (1, 0, 0)
     assert replicas.max_over_ranks(7.5, 1) == 7.5
     assert replicas.throughput(1, 1, 8.0) == pytest.approx(125.0)
+
+
+def _rho_rank_main(rank, world, port, out):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2204_13595_gb300 import systems
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        s = systems.water(1000, seed=8)
+        pr = oracle.make_params(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, s.seed, k_e=s.k_e, eps=s.eps, sigma=s.sigma)
+        m = oracle.sample_k_params(pr, 5)               # drawn on every rank from the same counters
+        own = (np.floor(s.pos[:, 0] / s.L * world).astype(int) % world) == rank   # a slab of the box
+        part = oracle.rho(s.pos[own], s.q[own], s.L, m)
+        t = torch.tensor(np.stack([part.real, part.imag]), dtype=torch.float64)
+        dist.all_reduce(t)                               # the one exchange of the Fourier part
+        mm = torch.tensor(m, dtype=torch.int64)
+        m0 = mm.clone()
+        dist.broadcast(m0, 0)
+        out.put((rank, int(own.sum()), bool(torch.equal(mm, m0)), t.numpy().copy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_sum_rho_partials():
+    """The Fourier part's exchange under a domain decomposition (Sec. 3: one
+    all-reduce of rho per step): each rank sums rho(k) over the atoms of its
+    slab of the box for k samples it draws itself from the shared counters; the
+    all-reduced sum equals rho over all atoms, and the samples agree without
+    being sent."""
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    import oracle
+    from paper_2204_13595_gb300 import systems
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rho_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=120) for _ in procs), key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    s = systems.water(1000, seed=8)
+    pr = oracle.make_params(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, s.seed, k_e=s.k_e, eps=s.eps, sigma=s.sigma)
+    full = oracle.rho(s.pos, s.q, s.L, oracle.sample_k_params(pr, 5))
+    assert res[0][1] + res[1][1] == s.n and min(res[0][1], res[1][1]) > 0
+    assert res[0][2] and res[1][2]
+    for _, _, _, t in res:
+        assert np.allclose(t[0] + 1j * t[1], full, rtol=0, atol=1e-12 * np.abs(s.q).sum())
