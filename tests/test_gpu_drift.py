@@ -85,3 +85,31 @@ def test_nve_drift_against_oracle(state):
           f"{np.max(np.abs(mix[:, 1] - K_o) / K_o):.2e} (max over the segment)")
     assert abs(sK_m - sK_o) < 4 * sdK
     assert abs(sE_m - sE_o) < 4 * sdE
+
+
+@pytest.mark.slow
+def test_water_90k_thousand_fp64_steps_thermostatted():
+    """The 90,000-atom water box (30,000 molecules, seed 2) for 1,000 FP64
+    velocity-Verlet steps of 1 fs.  Unthermostatted, the stochastic forces heat
+    this system until it diverges within that many steps (see the NVE slopes
+    above), so the run uses the Langevin thermostat (100 fs): it must finish
+    with no status error, finite state and a bounded kinetic temperature."""
+    import torch
+    s = systems.water(30000, seed=2)
+    dev = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device="cuda")
+    pos, vel, mass, q = dev(s.pos), dev(s.vel), dev(s.mass), dev(s.q)
+    typ, mol = dev(s.type, torch.int32), dev(s.mol, torch.int32)
+    c = rbe.Context.for_system(s, precision=rbe.FP64)
+    c.set_langevin(systems.KT_WATER, 100.0)
+    F = torch.empty_like(pos)
+    c.forces(0, pos, q, typ, mol, F)
+    nsteps = 1000
+    tr = torch.zeros((nsteps, 2), dtype=torch.float64, device="cuda")
+    c.step(0, nsteps, s.dt, s.accel, pos, vel, mass, q, typ, mol, F, tr)
+    assert c.sync_status() == 0
+    t = tr.cpu().numpy()
+    assert np.isfinite(t).all() and torch.isfinite(pos).all() and torch.isfinite(vel).all()
+    kT_kin = t[:, 1] / (1.5 * s.n)
+    print(f"\n90k water, 1,000 FP64 steps: kinetic kT {kT_kin[0]:.3f} -> {kT_kin[-1]:.3f} kJ/mol "
+          f"(target {systems.KT_WATER})")
+    assert kT_kin.max() < 10 * systems.KT_WATER
