@@ -4,20 +4,23 @@
 // (cells of edge L/floor(L/r_c), the grid of Sec. 2.3).  A block takes units
 // round-robin; for each unit it stages, in shared memory, the FP32 positions
 // of every atom in the union of the unit's stencils: (2R+1)^2 rows of G+2R
-// cells, R = floor(r_s/w)+1 (Sec. 2.3's stencil reach).  Each warp then owns
-// one atom i of the unit at a time:
-//   1. list construction: the warp walks i's stencil rows in canonical order
-//      (ascending wrapped cell index, then fixed-point x, then atom index),
-//      each row cut to the cells that can hold a point within r_s and, by
-//      binary search on the x-sorted end cells, to the atoms within the
-//      row's x half-width; every row is one or two contiguous ranges of the
-//      staged arrays with a fixed periodic image shift.  Candidates are classified into the core C(i) (r <= r_c) and
-//      the shell S(i) (r_c < r <= r_s) by an FP32 distance whose rounding is
-//      bounded on the host; candidates inside that bound of r_c or r_s, and
-//      r ~ 0, are decided by the exact integer squared distance of the 32-bit
-//      fixed-point coordinates, so the sets equal the exact-integer
-//      definition bit for bit.  Members are appended in order to per-warp
-//      shared buffers (ballot + popc ranks).
+// cells, R = floor(r_s/w)+1 (Sec. 2.3's stencil reach), each piece of a row
+// moved to the periodic image adjacent to the unit.  Each warp then owns one
+// atom i of the unit at a time:
+//   1. list construction: the lanes take i's stencil rows (32 per pass) in
+//      canonical order (ascending wrapped cell index, then fixed-point x, then
+//      atom index); each row is cut to the cells that can hold a point within
+//      r_s and, by binary search on the x-sorted end cells, to the atoms
+//      within the row's x half-width, leaving one or two contiguous ranges of
+//      the staged array.  The ranges of a pass are concatenated in canonical
+//      order and classified 32 candidates per lane-chunk, four chunks at a
+//      time, into the core C(i) (r <= r_c) and the shell S(i)
+//      (r_c < r <= r_s) by an FP32 distance whose rounding is bounded on the
+//      host; candidates inside that bound of r_c or r_s, and r ~ 0, are
+//      decided by the exact integer squared distance of the 32-bit fixed-point
+//      coordinates, so the sets equal the exact-integer definition bit for
+//      bit.  Members are appended in order to per-warp shared buffers (ballot
+//      + popc ranks).
 //   2. shell batch: if N_S > p, Floyd's algorithm draws p distinct ordinals
 //      in [0, N_S) from Philox words at counter (i, k/4, step, 1); otherwise
 //      the batch is all of S(i) with weight 1 (Algorithm 1, shell step).
@@ -25,7 +28,9 @@
 //      N_S/p, Eq. (2.11)); same-molecule pairs take the Ewald exclusion
 //      correction instead of erfc + LJ.
 // A unit whose staged region exceeds the shared capacity reads the same
-// ranges from global memory instead (identical results, slower).
+// ranges from global memory one range at a time, and so does a pass whose
+// concatenated ranges hold more than RBL_MAX_PACKED candidates (identical
+// results, slower).
 // Outputs: F_real (core + weighted shell, before the momentum correction of
 // Eq. (2.13)) per sorted atom -- FP64 on the FP64 path, FP32 on the mixed
 // path -- and per-block partial sums of the real-space energies, the virial
