@@ -57,6 +57,50 @@ SM_MAX_MHZ = 2070.0
 HBM_FALLBACK_GBS = 6800.0
 
 
+PROBES = {"ffma": 0, "dfma": 1, "sfu": 2, "alu": 3, "copy": 4}
+PROBE_SRC = os.path.join(ROOT, "bench_probes.cu")
+PROBE_LIB = os.path.join(ROOT, "_build", "libbench_probes.so")
+
+
+def build_probes() -> str:
+    """Compiles bench_probes.cu (the pipe and copy throughput probes, not part
+    of librbe.so) into _build/libbench_probes.so when stale."""
+    if os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    from paper_2204_13595_gb300 import build as b
+    os.makedirs(os.path.dirname(PROBE_LIB), exist_ok=True)
+    tmp = PROBE_LIB + ".tmp"
+    cmd = [b.nvcc()] + b.ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", PROBE_SRC,
+                                 "-o", tmp, "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for bench_probes.cu:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
+_probe_lib = None
+
+
+def peak_probe(kind, stream=None):
+    """Measured throughput of a pipe ('ffma', 'dfma', 'sfu', 'alu': operations
+    per second) or of device memory ('copy': bytes per second), from
+    bench_peak_probe of libbench_probes.so."""
+    import ctypes
+    global _probe_lib
+    if _probe_lib is None:
+        _probe_lib = ctypes.CDLL(build_probes())
+        _probe_lib.bench_peak_probe.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    out = ctypes.c_double()
+    rc = _probe_lib.bench_peak_probe(PROBES[kind], ctypes.byref(out), stream)
+    if rc != 0:
+        raise RuntimeError(f"bench_peak_probe({kind}) failed: {rc}")
+    return out.value
+
+
 def _kernel_roofline(prof, n, P, ncells, peaks_meas):
     """Roofline fraction of every kernel of the mixed step (per-launch CUDA-event
     times from the library's profiler).  Denominators: HBM from MEASURED_PEAKS.json
@@ -448,7 +492,7 @@ def run_ours(args):
     meas = {}
     for kind in ("ffma", "dfma", "sfu", "alu", "copy"):
         try:
-            meas[kind] = rbe.peak_probe(kind)
+            meas[kind] = peak_probe(kind)
         except Exception as e:        # report, do not fail the bench
             meas[kind] = f"unavailable: {e}"
     clocks_proc = _clock_sampler() if rank == 0 else None
@@ -517,7 +561,7 @@ def run_ours(args):
         "measured_pipes": {
             "ffma_per_s": meas.get("ffma"), "dfma_per_s": meas.get("dfma"), "sfu_sin_per_s": meas.get("sfu"),
             "int_ops_per_s": meas.get("alu"), "copy_bytes_per_s": meas.get("copy"),
-            "note": "rbe_peak_probe in this run (best of 3 launches): context for the derived peaks"},
+            "note": "bench_peak_probe in this run (best of 3 launches): context for the derived peaks"},
         "cpu_baseline": {"value": 1.0 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "one full FP64 oracle force evaluation of the same 1.2M-atom system"},
         "e2e": {"value": replicas.throughput(ws, 1, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

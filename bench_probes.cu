@@ -1,11 +1,22 @@
-// k_peaks.cu -- throughput probes of the plain arithmetic pipes and of device
-// memory, the roofline denominators of kernels bound by FP32/integer issue,
-// the special-function unit or HBM (none of the force step is tensor-core
-// work).  Each probe runs independent dependency chains in every thread of a
-// grid that fills the GPU, so the pipe, not latency, limits it; the result is
-// the best of three timed launches after one warm-up (CUDA events on the
-// caller's stream).
-#include "rbe_internal.cuh"
+// bench_probes.cu -- throughput probes of the plain arithmetic pipes and of
+// device memory, used by bench.py as context for the roofline denominators of
+// kernels bound by FP32/integer issue, the special-function unit or HBM (none
+// of the force step is tensor-core work).  Built by bench.py into its own
+// shared object; not part of librbe.so.  Each probe runs independent
+// dependency chains in every thread of a grid that fills the GPU, so the
+// pipe, not latency, limits it; the result is the best of three timed
+// launches after one warm-up (CUDA events on the caller's stream).
+#include <cuda_runtime.h>
+
+#define PROBE_FFMA 0
+#define PROBE_DFMA 1
+#define PROBE_SFU  2
+#define PROBE_ALU  3
+#define PROBE_COPY 4
+#define PROBE_OK      0
+#define PROBE_EINVAL -1
+#define PROBE_ECUDA  -6
+#define PROBE_ENOMEM -7
 
 namespace {
 
@@ -88,38 +99,44 @@ __global__ void __launch_bounds__(PB_THREADS) k_probe_copy(long n, const float4*
 
 }  // namespace
 
-extern "C" int rbe_peak_probe(int kind, double* ops_per_s, void* cuda_stream)
+// kind: PROBE_FFMA (FP32 fused multiply-adds per second, one per lane),
+// PROBE_DFMA (FP64 fused multiply-adds per second), PROBE_SFU (hardware sines
+// per second), PROBE_ALU (32-bit integer shift/xor/add operations per second),
+// PROBE_COPY (device-to-device copy, bytes read + written per second, 2 GiB
+// per launch).  Best of three timed launches after a warm-up on cuda_stream
+// (the call waits).  Allocates and frees a small sink, and 2 GiB for the copy.
+extern "C" int bench_peak_probe(int kind, double* ops_per_s, void* cuda_stream)
 {
-    if (!ops_per_s || kind < RBE_PROBE_FFMA || kind > RBE_PROBE_COPY) return RBE_EINVAL;
+    if (!ops_per_s || kind < PROBE_FFMA || kind > PROBE_COPY) return PROBE_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int dev = 0, nsm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return RBE_ECUDA;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RBE_ECUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PROBE_ECUDA;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PROBE_ECUDA;
     const int blocks = nsm * 8;
     const double threads = (double)blocks * PB_THREADS;
     void* sink = nullptr;
     void* buf = nullptr;
     const long ncopy = 64L << 20;   // float4 elements: 1 GiB read + 1 GiB written
-    if (cudaMalloc(&sink, sizeof(double) * blocks) != cudaSuccess) return RBE_ENOMEM;
-    if (kind == RBE_PROBE_COPY && cudaMalloc(&buf, sizeof(float4) * 2 * (size_t)ncopy) != cudaSuccess) {
+    if (cudaMalloc(&sink, sizeof(double) * blocks) != cudaSuccess) return PROBE_ENOMEM;
+    if (kind == PROBE_COPY && cudaMalloc(&buf, sizeof(float4) * 2 * (size_t)ncopy) != cudaSuccess) {
         cudaFree(sink);
-        return RBE_ENOMEM;
+        return PROBE_ENOMEM;
     }
     int iters = 0;
     double ops = 0.0;
     switch (kind) {
-        case RBE_PROBE_FFMA: iters = 16384; ops = threads * iters * PB_CHAINS; break;
-        case RBE_PROBE_DFMA: iters = 512; ops = threads * iters * PB_CHAINS; break;
-        case RBE_PROBE_SFU: iters = 4096; ops = threads * iters * PB_CHAINS; break;
-        case RBE_PROBE_ALU: iters = 8192; ops = threads * iters * PB_CHAINS * 3.0; break;  // shift, xor, add
+        case PROBE_FFMA: iters = 16384; ops = threads * iters * PB_CHAINS; break;
+        case PROBE_DFMA: iters = 512; ops = threads * iters * PB_CHAINS; break;
+        case PROBE_SFU: iters = 4096; ops = threads * iters * PB_CHAINS; break;
+        case PROBE_ALU: iters = 8192; ops = threads * iters * PB_CHAINS * 3.0; break;  // shift, xor, add
         default: ops = 2.0 * sizeof(float4) * (double)ncopy; break;
     }
     auto launch = [&]() {
         switch (kind) {
-            case RBE_PROBE_FFMA: k_probe_ffma<<<blocks, PB_THREADS, 0, st>>>(iters, 1.0f, (float*)sink); break;
-            case RBE_PROBE_DFMA: k_probe_dfma<<<blocks, PB_THREADS, 0, st>>>(iters, 1.0, (double*)sink); break;
-            case RBE_PROBE_SFU: k_probe_sfu<<<blocks, PB_THREADS, 0, st>>>(iters, 0.25f, (float*)sink); break;
-            case RBE_PROBE_ALU: k_probe_alu<<<blocks, PB_THREADS, 0, st>>>(iters, 7u, (unsigned*)sink); break;
+            case PROBE_FFMA: k_probe_ffma<<<blocks, PB_THREADS, 0, st>>>(iters, 1.0f, (float*)sink); break;
+            case PROBE_DFMA: k_probe_dfma<<<blocks, PB_THREADS, 0, st>>>(iters, 1.0, (double*)sink); break;
+            case PROBE_SFU: k_probe_sfu<<<blocks, PB_THREADS, 0, st>>>(iters, 0.25f, (float*)sink); break;
+            case PROBE_ALU: k_probe_alu<<<blocks, PB_THREADS, 0, st>>>(iters, 7u, (unsigned*)sink); break;
             default:
                 k_probe_copy<<<blocks, PB_THREADS, 0, st>>>(ncopy, (const float4*)buf, (float4*)buf + ncopy);
                 break;
@@ -144,7 +161,7 @@ extern "C" int rbe_peak_probe(int kind, double* ops_per_s, void* cuda_stream)
     cudaEventDestroy(e1);
     cudaFree(sink);
     if (buf) cudaFree(buf);
-    if (e != cudaSuccess || !(best > 0.f)) return RBE_ECUDA;
+    if (e != cudaSuccess || !(best > 0.f)) return PROBE_ECUDA;
     *ops_per_s = ops / (best * 1e-3);
-    return RBE_OK;
+    return PROBE_OK;
 }

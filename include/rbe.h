@@ -220,7 +220,11 @@ const char* rbe_last_error(const rbe_ctx* ctx);
 
 /* Structure factors rho_l = sum_j q_j exp(i k_l . r_j), k_l = 2 pi m_l / box_L,
  * for P given integer vectors m[P][3], from n atoms pos[n][3], q[n]; writes
- * rho[P][2] (re, im).  FP64, the same arithmetic as the FP64 context path.
+ * rho[P][2] (re, im).  FP64: the phase (m . x)/L is reduced to [-1/2, 1/2]
+ * and evaluated with sincospi.  This is the structure factor of the context
+ * path (rbe_get_kspace) by other arithmetic (the context path takes the
+ * phase from 32-bit fixed-point codes): the two agree to about 1e-13 of
+ * sum |q|, not bit for bit.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot let the library allocate device memory (their device memory is
  * owned by another allocator or a fixed budget, or allocation and its
@@ -233,7 +237,11 @@ const char* rbe_last_error(const rbe_ctx* ctx);
  * address with that device current; make that first call before any stream
  * capture.  Calls share the array: calls whose kernels overlap on the GPU
  * race.  Returns RBE_EINVAL for bad arguments, RBE_ELIMIT when P exceeds
- * RBE_NOALLOC_PMAX, RBE_ECUDA when the set-up or a launch fails. */
+ * RBE_NOALLOC_PMAX, RBE_ECUDA when the set-up or a launch fails (a launch
+ * error the caller left pending is also reported, and cleared, here).  The
+ * device address is looked up once per device and not refreshed after
+ * cudaDeviceReset: do not call this entry point on a device after resetting
+ * it. */
 #define RBE_ELIMIT        -8   /* size beyond a compiled maximum                */
 #define RBE_NOALLOC_BLOCKS 256
 #define RBE_NOALLOC_PMAX   512
@@ -243,22 +251,6 @@ int rbe_rho_noalloc(int n, const double* pos, const double* q, double box_L, int
 /* Releases the context and its device memory (after the caller's streams are
  * idle). */
 void rbe_destroy(rbe_ctx* ctx);
-
-/* Throughput probes of the GPU's plain pipes and memory, the roofline
- * denominators of kernels bound by arithmetic issue, the special-function unit
- * or HBM.  kind: RBE_PROBE_FFMA (FP32 fused multiply-adds per second, one per
- * lane), RBE_PROBE_DFMA (FP64 fused multiply-adds per second),
- * RBE_PROBE_SFU (hardware sines per second), RBE_PROBE_ALU (32-bit integer
- * shift/xor/add operations per second), RBE_PROBE_COPY (device-to-device copy
- * bytes read + written per second, 2 GiB per launch).  Each is the best of
- * three timed launches after a warm-up, on cuda_stream (the call waits).
- * Allocates (and frees) a small sink, and 2 GiB for the copy probe. */
-#define RBE_PROBE_FFMA 0
-#define RBE_PROBE_DFMA 1
-#define RBE_PROBE_SFU  2
-#define RBE_PROBE_ALU  3
-#define RBE_PROBE_COPY 4
-int rbe_peak_probe(int kind, double* ops_per_s, void* cuda_stream);
 
 /* Variants of the method (the paper leaves them open; defaults = base method).
  *

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librbe.so")
-SOURCES = ["rbe_api.cu", "k_cells.cu", "k_rbl.cu", "k_kspace.cu", "rbe_noalloc.cu", "rbe_batch.cu", "k_peaks.cu"]
+SOURCES = ["rbe_api.cu", "k_cells.cu", "k_rbl.cu", "k_kspace.cu", "rbe_noalloc.cu", "rbe_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -680,6 +680,10 @@ int rbe_forces(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const doub
         rc = forces_device(ctx, step, n, pos, q, type, mol, F, st);
     } else {
         if (n > ctx->h_cap) {
+            // each dev_alloc frees the old buffer first: a failure part way
+            // leaves the set incomplete, so the capacity is zero until all
+            // five succeed
+            ctx->h_cap = 0;
             if ((rc = dev_alloc(ctx, &ctx->h_pos, 3 * (size_t)n))) return rc;
             if ((rc = dev_alloc(ctx, &ctx->h_q, n))) return rc;
             if ((rc = dev_alloc(ctx, &ctx->h_type, n))) return rc;

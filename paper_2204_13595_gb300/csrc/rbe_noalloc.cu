@@ -5,9 +5,9 @@
 // framework's caching allocator that has already reserved the device, or a
 // service running under a fixed memory budget), or code on a path where an
 // allocation call is not allowed or where cudaFree's implicit device
-// synchronisation is not acceptable.  rbe_rho_noalloc serves them: it is the
-// rho(k) partial-sum kernel of the context path with its per-block scratch
-// moved into a file-scope device array that exists from module load to
+// synchronisation is not acceptable.  rbe_rho_noalloc serves them: it
+// computes the structure factors of the context path with its per-block
+// scratch in a file-scope device array that exists from module load to
 // process exit.  The caller passes every input and output; nothing here calls
 // cudaMalloc, cudaFree or an allocating library routine.
 //
@@ -28,15 +28,22 @@ constexpr int NA_TILE = 256;
 static __device__ __align__(256) double2 g_rho_scratch[RBE_NOALLOC_BLOCKS * RBE_NOALLOC_PMAX];
 
 // Device address of g_rho_scratch per device, looked up once per device with
-// that device current (the host-side symbol is only a stand-in).
+// that device current (the host-side symbol is only a stand-in).  The cached
+// address is not refreshed after cudaDeviceReset: a process that resets a
+// device must not call rbe_rho_noalloc on it again.
 std::mutex g_mu;
 double2* g_scratch_ptr[256];
 bool g_scratch_ok[256];
 
 // Block b sums q_j exp(i k_l . r_j) over atoms [b*chunk, (b+1)*chunk) for
-// every l; thread t owns k_l for l = t, t + blockDim, ...  Same arithmetic as
-// the FP64 context path: the phase t = (m . x_wrapped)/L is reduced to
-// [-1/2, 1/2] and evaluated with sincospi.
+// every l; thread t owns k_l for l = t, t + blockDim, ...  The phase
+// t = (m . x_wrapped)/L is formed in FP64, reduced to [-1/2, 1/2] by rint
+// and evaluated with sincospi; the block partials are summed serially in
+// block order.  This is not the context path's arithmetic (which takes the
+// phase from the 32-bit fixed-point codes and a table with a Taylor series,
+// and sums in another order): the two agree to rounding, about 1e-13 of
+// sum |q|, not bit for bit, and the rounding of the FP64 phase grows with
+// |m . x| / L.
 __global__ void __launch_bounds__(NA_THREADS) k_rho_noalloc(int n, int chunk, double L, double invL, int P,
                                                             const double* __restrict__ pos,
                                                             const double* __restrict__ q,
@@ -125,7 +132,11 @@ extern "C" int rbe_rho_noalloc(int n, const double* pos, const double* q, double
     blocks = blocks < 1 ? 1 : (blocks > RBE_NOALLOC_BLOCKS ? RBE_NOALLOC_BLOCKS : blocks);
     const int chunk = (n + blocks - 1) / blocks;
     const int threads = ((P < NA_THREADS ? P : NA_THREADS) + 31) / 32 * 32;
+    // cudaGetLastError also returns (and clears) an error that an earlier
+    // launch of the caller's left pending; such an error is reported here as
+    // RBE_ECUDA
     k_rho_noalloc<<<blocks, threads, 0, st>>>(n, chunk, box_L, 1.0 / box_L, P, pos, q, m, scratch);
+    if (cudaGetLastError() != cudaSuccess) return RBE_ECUDA;
     k_rho_noalloc_sum<<<(P + NA_THREADS - 1) / NA_THREADS, NA_THREADS, 0, st>>>(blocks, P, scratch, rho);
     if (cudaGetLastError() != cudaSuccess) return RBE_ECUDA;
     return RBE_OK;

@@ -27,9 +27,8 @@ EXPORTS = ["rbe_create", "rbe_set_coulomb", "rbe_set_lj", "rbe_set_precision", "
            "rbe_destroy", "rbe_rho_noalloc", "rbe_adjoint", "rbe_set_rbl_tiling", "rbe_batch_create",
            "rbe_batch_bind", "rbe_batch_forces", "rbe_batch_step", "rbe_batch_autotune", "rbe_batch_info",
            "rbe_batch_sync_status", "rbe_batch_last_error", "rbe_batch_destroy", "rbe_set_shell_sampling",
-           "rbe_set_lj_cutoff", "rbe_set_kpool", "rbe_set_langevin", "rbe_peak_probe", "rbe_get_langevin_force",
+           "rbe_set_lj_cutoff", "rbe_set_kpool", "rbe_set_langevin", "rbe_get_langevin_force",
            "rbe_set_langevin_force"]
-PROBES = {"ffma": 0, "dfma": 1, "sfu": 2, "alu": 3, "copy": 4}
 SHELL_FLOYD, SHELL_REPLACE = 0, 1
 WCA_FACTOR = 2.0 ** (1.0 / 6.0)
 ELIMIT = -8
@@ -73,7 +72,6 @@ def load(path: str = LIB_PATH):
     L.rbe_set_lj_cutoff.argtypes = [vp, d]
     L.rbe_set_kpool.argtypes = [vp, i, i]
     L.rbe_set_langevin.argtypes = [vp, d, d]
-    L.rbe_peak_probe.argtypes = [i, ctypes.POINTER(d), vp]
     L.rbe_get_langevin_force.argtypes = [vp, i, vp, ctypes.POINTER(u64)]
     L.rbe_set_langevin_force.argtypes = [vp, i, vp, u64]
     L.rbe_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
@@ -116,20 +114,39 @@ def _stream(stream):
     return torch.cuda.current_stream().cuda_stream
 
 
-def peak_probe(kind, stream=None):
-    """rbe_peak_probe: measured throughput of a pipe ('ffma', 'dfma', 'sfu',
-    'alu': operations per second) or of device memory ('copy': bytes per
-    second)."""
-    out = ctypes.c_double()
-    rc = lib().rbe_peak_probe(PROBES[kind], ctypes.byref(out), _stream(stream))
-    if rc != OK:
-        raise RbeError(rc, f"rbe_peak_probe({kind}) failed")
-    return out.value
+def _check_noalloc_args(pos, q, m, rho):
+    """Shapes, dtypes and placement that rbe_rho_noalloc reads its raw
+    pointers as: pos float64 [n,3], q float64 [n], m int32 [P,3], rho float64
+    [P,2], all contiguous on the current CUDA device.  Anything else would be
+    read or written as the wrong type or size, so it is refused here."""
+    import torch
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+    want = (("pos", pos, torch.float64, 3), ("q", q, torch.float64, None), ("m", m, torch.int32, 3),
+            ("rho", rho, torch.float64, 2))
+    for name, t, dt, cols in want:
+        if not isinstance(t, torch.Tensor):
+            raise RbeError(EINVAL, f"rho_noalloc: {name} must be a torch tensor")
+        if t.dtype != dt:
+            raise RbeError(EINVAL, f"rho_noalloc: {name} must be {dt}, got {t.dtype}")
+        if cols is None and t.dim() != 1:
+            raise RbeError(EINVAL, f"rho_noalloc: {name} must be 1-D")
+        if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+            raise RbeError(EINVAL, f"rho_noalloc: {name} must have shape [*, {cols}]")
+        if not t.is_contiguous():
+            raise RbeError(EINVAL, f"rho_noalloc: {name} must be contiguous")
+    if q.shape[0] != pos.shape[0]:
+        raise RbeError(EINVAL, "rho_noalloc: q and pos hold different atom counts")
+    if rho.shape[0] != m.shape[0]:
+        raise RbeError(EINVAL, "rho_noalloc: rho must have one row per k vector of m")
+    for name, t, _, _ in want:
+        if not t.is_cuda or t.device.index != dev:
+            raise RbeError(EINVAL, f"rho_noalloc: {name} must be on the current CUDA device")
 
 
 def rho_noalloc(pos, q, box_L, m, rho, stream=None):
     """rbe_rho_noalloc: structure factors into rho[P,2] without any device
     allocation (scratch is a static device array; see include/rbe.h)."""
+    _check_noalloc_args(pos, q, m, rho)
     rc = lib().rbe_rho_noalloc(int(pos.shape[0]), _ptr(pos), _ptr(q), float(box_L), int(m.shape[0]), _ptr(m),
                                _ptr(rho), _stream(stream))
     if rc != OK:

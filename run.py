@@ -1,6 +1,6 @@
 """Command-line driver: runs IRBE force evaluations on a synthetic system.
 
-  python -m paper_2204_13595_gb300.run --system water --n-mol 400000 \\
+  python run.py --system water --n-mol 400000 \\
          --precision mixed --steps 3 [--warmup 1] [--profile]
 
 Prints the mean time per force evaluation (CUDA events on the launching
@@ -11,12 +11,18 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
 
 
 def main(argv=None):
     import torch
 
-    from . import build, rbe, systems
+    from paper_2204_13595_gb300 import build, rbe, systems
     ap = argparse.ArgumentParser()
     ap.add_argument("--system", default="water", choices=["water", "electrolyte"])
     ap.add_argument("--n-mol", type=int, default=400000, help="water molecules (water) or ions (electrolyte)")

@@ -99,7 +99,29 @@ def test_batch_create_validates_contexts(L):
     L.rbe_destroy(h)
 
 
-def test_peak_probe_rejects_bad_arguments(L):
-    out = ctypes.c_double()
-    assert L.rbe_peak_probe(99, ctypes.byref(out), None) == -1
-    assert L.rbe_peak_probe(0, None, None) == -1
+def test_rho_noalloc_binding_rejects_bad_tensors():
+    """The binding refuses, before any call into the library, tensors that
+    rbe_rho_noalloc would read or write as the wrong type or size."""
+    import torch
+
+    from paper_2204_13595_gb300 import rbe
+    n, P = 6, 4
+    good = dict(pos=torch.zeros((n, 3), dtype=torch.float64), q=torch.zeros(n, dtype=torch.float64),
+                m=torch.ones((P, 3), dtype=torch.int32), rho=torch.zeros((P, 2), dtype=torch.float64))
+    bad = [
+        dict(rho=torch.zeros((P, 2), dtype=torch.float32)),       # float32 rho
+        dict(rho=torch.zeros((P - 1, 2), dtype=torch.float64)),   # fewer rows than k vectors
+        dict(m=torch.ones((P, 3), dtype=torch.int64)),            # int64 m (torch.tensor of ints)
+        dict(m=torch.ones((P, 2), dtype=torch.int32)),            # wrong m shape
+        dict(pos=torch.zeros((n, 3), dtype=torch.float32)),       # float32 pos
+        dict(pos=torch.zeros((3, n), dtype=torch.float64).t()),   # non-contiguous pos
+        dict(q=torch.zeros(n - 1, dtype=torch.float64)),          # q and pos differ in length
+        dict(q=torch.zeros((n, 1), dtype=torch.float64)),         # 2-D q
+        dict(pos=[[0.0, 0.0, 0.0]] * n),                          # not a tensor
+        {},                                                       # CPU tensors: not on a CUDA device
+    ]
+    for change in bad:
+        args = dict(good, **change)
+        with pytest.raises(rbe.RbeError) as e:
+            rbe.rho_noalloc(args["pos"], args["q"], 10.0, args["m"], args["rho"])
+        assert e.value.code == rbe.EINVAL, change
