@@ -99,7 +99,17 @@ def test_rbl_reduces_to_truncated_sum_when_p_covers_shell(orc, elec, wat):
         assert np.abs(est["F_real"] - ex["F"]).max() < 1e-12 * scale
         for k in (0, 3, 4):
             assert est["E"][k] == pytest.approx(ex["E"][k], rel=1e-12, abs=1e-12 * np.abs(ex["E"]).max())
-        assert np.abs(est["W"] - est["W"]).max() == 0.0
+        # virial: the estimator's W less its reweighted reciprocal part (the
+        # textbook Ewald reciprocal virial of each drawn k, weight S/P) is the
+        # real-space virial -1/2 sum r_ij (x) f_ij, which must equal the
+        # exact truncated real-space virial of the separate Ewald code
+        k = 2 * np.pi * est["m"] / s.L
+        k2 = (k * k).sum(1)
+        e = 0.5 * (orc.S(s.alpha, s.L) / s.P) * 4 * np.pi * s.k_e / (s.L**3 * k2) * np.abs(est["rho"]) ** 2
+        b = 2 * (1 / k2 + 1 / (4 * s.alpha))
+        Wk = [np.sum(e * ((a == c) - b * k[:, a] * k[:, c])) for a, c in ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))]
+        assert np.sum(e) == pytest.approx(est["E"][1], rel=1e-12)
+        assert np.abs(est["W"] - np.array(Wk) - ex["W"]).max() < 1e-12 * np.abs(ex["W"]).max()
         assert np.abs(est["corr"]).max() < 1e-12 * scale      # Newton's third law
 
 
@@ -244,3 +254,47 @@ def test_fourier_variance_scales_as_one_over_P(orc, wat):
                       for k in range(300)])
         v.append(F.var(0, ddof=1).mean())
     assert v[0] / v[1] == pytest.approx(4.0, rel=0.12)
+
+
+def test_fourier_variance_closed_form(orc):
+    """Exact finite-sample variance of the RBE force (Sec. 2.2, Eq. (2.15)):
+    F^{long,*}_i = (1/P) sum_l X_l with X = S g(k), k ~ e^{-k^2/4 alpha}/S and
+    g(k) = -(4 pi k_e q_i k / (V k^2)) Im(e^{-i k.r_i} rho(k)); hence
+    Var = (S sum_k e^{-k^2/4 alpha} g(k)^2 - (F^long_i)^2) / P with
+    F^long_i = sum_k e^{-k^2/4 alpha} g(k).  The sums run over every k of the
+    box in numpy (independent of the oracle's sampler and Fourier code) and
+    the prediction is compared with the oracle's variance over 2,000 seeds."""
+    s = systems.water(334, seed=6)          # 1,002 atoms, L = 21.5 A
+    P, nseeds = 20, 2000
+    atoms = [0, 1, 517]
+    M = orc.k_table(s.alpha, s.L)[0]
+    ax = np.arange(-M, M + 1)
+    m = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3)
+    m = m[np.any(m != 0, axis=1)]
+    k = 2 * np.pi * m / s.L
+    k2 = (k * k).sum(1)
+    w = np.exp(-k2 / (4 * s.alpha))
+    keep = w > 1e-30 * w.max()
+    k, k2, w = k[keep], k2[keep], w[keep]
+    S = w.sum()                                       # = H^3 - 1 (Eq. (2.6))
+    assert S == pytest.approx(orc.S(s.alpha, s.L), rel=1e-12)
+    rho = (s.q[None, :] * np.exp(1j * (k @ s.pos.T))).sum(1)
+    V = s.L**3
+    pred, mean = [], []
+    for i in atoms:
+        im = np.imag(np.exp(-1j * (k @ s.pos[i])) * rho)
+        g = -(4 * np.pi * s.k_e * s.q[i] / (V * k2) * im)[:, None] * k
+        F = (w[:, None] * g).sum(0)
+        mean.append(F)
+        pred.append((S * (w[:, None] * g * g).sum(0) - F * F) / P)
+    pred, mean = np.array(pred), np.array(mean)
+    samples = np.array([orc.rbe_forces(s.pos, s.q, s.type, s.mol,
+                                       _params(orc, s, P=P, seed=9000 + t), 0)["F_long"][atoms]
+                        for t in range(nseeds)])
+    emp = samples.var(0, ddof=1)
+    # relative sampling error of a variance from 2,000 draws of a 20-sample
+    # mean is a few percent; 15% is several standard errors
+    assert np.allclose(emp, pred, rtol=0.15), (emp / pred)
+    # the mean agrees with the exact k-space force within its standard error
+    z = (samples.mean(0) - mean) / np.sqrt(pred / nseeds)
+    assert np.abs(z).max() < 4.5
