@@ -13,6 +13,10 @@ Parity status of each function (what pins it; tests/test_oracle_*.py):
   floyd             chi^2 over all C(6,3) subsets; uniform inclusion
   lists             brute force == cell stencil; neighbour counts vs 4/3 pi r^3 rho
                     and the paper's ~140 / ~700 (Sec. 2.1, Sec. 3.1)
+  skin_lists,       (reading R15) stored lists: stencil == brute force; a step's
+  lists(pos_b=)     sets from them == the stencil sets at that step while no
+                    atom moved more than skin/2, and the rebuild test decides
+                    that boundary exactly
   ewald_exact       NaCl Madelung constant; alpha invariance; direct lattice
                     sum; central finite differences; virial trace = energy
   rbe_forces        p >= max N_S reduces to the truncated exact sum;
@@ -76,15 +80,18 @@ class Params(ctypes.Structure):
         ("kpool_burn", ctypes.c_int),
         ("lang_kT", ctypes.c_double),
         ("lang_tau", ctypes.c_double),
+        ("skin", ctypes.c_double),
     ]
 
 
 def make_params(L, alpha, r_c, r_s, p, P, seed, k_e=1.0, eps=(0.0,), sigma=(1.0,), shift_lj=0, shell_mode=0,
-                lj_rc_factor=0.0, kpool=0, kpool_burn=0, lang_kT=0.0, lang_tau=0.0):
+                lj_rc_factor=0.0, kpool=0, kpool_burn=0, lang_kT=0.0, lang_tau=0.0, skin=0.0):
     """Parameters of the estimator; shell_mode, lj_rc_factor, kpool and
     kpool_burn select the variants of reading R13, lang_kT and lang_tau the
-    Langevin thermostat of R14 used by vv_run (defaults: the base method)."""
+    Langevin thermostat of R14 used by vv_run, skin the Verlet skin of R15
+    (used with rebuild positions pos_b; defaults: the base method)."""
     pr = Params()
+    pr.skin = float(skin)
     pr.lang_kT, pr.lang_tau = float(lang_kT), float(lang_tau)
     pr.shell_mode, pr.lj_rc_factor = int(shell_mode), float(lj_rc_factor)
     pr.kpool, pr.kpool_burn = int(kpool), int(kpool_burn)
@@ -133,6 +140,14 @@ def lib():
             L.orc_lists.argtypes = [ctypes.c_int, _P(d), _P(Params), u64, ctypes.c_int,
                                     _P(i32), _P(i32), _P(i32), _P(i32), ctypes.c_int,
                                     _P(i32), ctypes.c_int, _P(i32), ctypes.c_int]
+            L.orc_lists_skin.argtypes = [ctypes.c_int, _P(d), _P(d), _P(Params), u64, ctypes.c_int,
+                                         _P(i32), _P(i32), _P(i32), _P(i32), ctypes.c_int,
+                                         _P(i32), ctypes.c_int, _P(i32), ctypes.c_int]
+            L.orc_skin_lists.argtypes = [ctypes.c_int, _P(d), _P(Params), ctypes.c_int, _P(i32), _P(i32),
+                                         ctypes.c_int]
+            L.orc_skin_displaced.argtypes = [ctypes.c_int, _P(d), _P(d), d, d]
+            L.orc_rbe_forces_skin.argtypes = [ctypes.c_int, _P(d), _P(d), _P(d), _P(i32), _P(i32), _P(Params), u64,
+                                              _P(d), _P(d), _P(d), _P(d), _P(d), _P(d), _P(i32), _P(d), _P(d)]
             L.orc_rho.argtypes = [ctypes.c_int, _P(d), _P(d), d, ctypes.c_int, _P(i32), _P(d)]
             L.orc_rbe_forces.argtypes = [ctypes.c_int, _P(d), _P(d), _P(i32), _P(i32), _P(Params), u64,
                                          _P(d), _P(d), _P(d), _P(d), _P(d), _P(d), _P(i32), _P(d), _P(d)]
@@ -235,9 +250,12 @@ def floyd(n, p, words):
     return out
 
 
-def lists(pos, pr, step, brute=False, cap_core=512, cap_shell=0):
-    """Per-atom C(i), S(i) sizes, core ids (canonical order), batch ids."""
+def lists(pos, pr, step, brute=False, cap_core=512, cap_shell=0, pos_b=None):
+    """Per-atom C(i), S(i) sizes, core ids (canonical order), batch ids.
+    With pos_b (and pr.skin > 0) the sets come from the stored lists of the
+    rebuild positions pos_b (reading R15)."""
     pos = _f64(pos)
+    pb = None if pos_b is None else _f64(pos_b)
     n = pos.shape[0]
     n_core = np.zeros(n, dtype=np.int32)
     n_shell = np.zeros(n, dtype=np.int32)
@@ -246,11 +264,34 @@ def lists(pos, pr, step, brute=False, cap_core=512, cap_shell=0):
     cap_b = max(pr.p, 1)
     batch = np.full((n, cap_b), -1, dtype=np.int32)
     shell = np.full((n, cap_shell), -1, dtype=np.int32) if cap_shell else None
-    st = lib().orc_lists(n, _ptr(pos, ctypes.c_double), ctypes.byref(pr), step, int(brute),
-                         _ptr(n_core, ctypes.c_int32), _ptr(n_shell, ctypes.c_int32), _ptr(n_batch, ctypes.c_int32),
-                         _ptr(core, ctypes.c_int32), cap_core, _ptr(batch, ctypes.c_int32), cap_b,
-                         _ptr(shell, ctypes.c_int32), cap_shell)
+    tail = (ctypes.byref(pr), step, int(brute),
+            _ptr(n_core, ctypes.c_int32), _ptr(n_shell, ctypes.c_int32), _ptr(n_batch, ctypes.c_int32),
+            _ptr(core, ctypes.c_int32), cap_core, _ptr(batch, ctypes.c_int32), cap_b,
+            _ptr(shell, ctypes.c_int32), cap_shell)
+    if pb is None:
+        st = lib().orc_lists(n, _ptr(pos, ctypes.c_double), *tail)
+    else:
+        st = lib().orc_lists_skin(n, _ptr(pos, ctypes.c_double), _ptr(pb, ctypes.c_double), *tail)
     return dict(status=st, n_core=n_core, n_shell=n_shell, n_batch=n_batch, core=core, batch=batch, shell=shell)
+
+
+def skin_lists(pos_b, pr, brute=False, cap=2048):
+    """The stored lists V(i) of reading R15 built at positions pos_b:
+    (counts[n], ids[n, cap] in the order of V(i), status)."""
+    pb = _f64(pos_b)
+    n = pb.shape[0]
+    counts = np.zeros(n, dtype=np.int32)
+    ids = np.full((n, cap), -1, dtype=np.int32)
+    st = lib().orc_skin_lists(n, _ptr(pb, ctypes.c_double), ctypes.byref(pr), int(brute),
+                              _ptr(counts, ctypes.c_int32), _ptr(ids, ctypes.c_int32), cap)
+    return counts, ids, st
+
+
+def skin_displaced(pos, pos_b, L, skin):
+    """Reading R15's rebuild test: True when some atom moved by more than
+    skin/2 (fixed-point units) since pos_b."""
+    return bool(lib().orc_skin_displaced(_f64(pos).shape[0], _ptr(_f64(pos), ctypes.c_double),
+                                         _ptr(_f64(pos_b), ctypes.c_double), float(L), float(skin)))
 
 
 def rho(pos, q, L, m):
@@ -262,12 +303,15 @@ def rho(pos, q, L, m):
     return out[:, 0] + 1j * out[:, 1]
 
 
-def rbe_forces(pos, q, typ, mol, pr, step):
+def rbe_forces(pos, q, typ, mol, pr, step, pos_b=None):
     """The IRBE estimator: dict(F, F_real, F_long, F_abs, E[6], W[6], corr, m, rho, status).
 
     F_abs holds, per force component, the sum of the absolute values of all
-    its summands (the componentwise condition scale of the sum)."""
+    its summands (the componentwise condition scale of the sum).  With pos_b
+    (and pr.skin > 0) the sets C(i), S(i) come from the stored lists of the
+    rebuild positions pos_b (reading R15)."""
     pos, q = _f64(pos), _f64(q)
+    pb = None if pos_b is None else _f64(pos_b)
     typ, mol = _i32(typ), _i32(mol)
     n = pos.shape[0]
     F = np.zeros((n, 3)); Fr = np.zeros((n, 3)); Fl = np.zeros((n, 3)); Fa = np.zeros((n, 3))
@@ -275,9 +319,13 @@ def rbe_forces(pos, q, typ, mol, pr, step):
     m = np.zeros((pr.P, 3), dtype=np.int32)
     rh = np.zeros((pr.P, 2))
     c = ctypes.c_double
-    st = lib().orc_rbe_forces(n, _ptr(pos, c), _ptr(q, c), _ptr(typ, ctypes.c_int32), _ptr(mol, ctypes.c_int32),
-                              ctypes.byref(pr), step, _ptr(F, c), _ptr(Fr, c), _ptr(Fl, c), _ptr(E, c), _ptr(W, c),
-                              _ptr(corr, c), _ptr(m, ctypes.c_int32), _ptr(rh, c), _ptr(Fa, c))
+    tail = (_ptr(q, c), _ptr(typ, ctypes.c_int32), _ptr(mol, ctypes.c_int32),
+            ctypes.byref(pr), step, _ptr(F, c), _ptr(Fr, c), _ptr(Fl, c), _ptr(E, c), _ptr(W, c),
+            _ptr(corr, c), _ptr(m, ctypes.c_int32), _ptr(rh, c), _ptr(Fa, c))
+    if pb is None:
+        st = lib().orc_rbe_forces(n, _ptr(pos, c), *tail)
+    else:
+        st = lib().orc_rbe_forces_skin(n, _ptr(pos, c), _ptr(pb, c), *tail)
     return dict(F=F, F_real=Fr, F_long=Fl, F_abs=Fa, E=E, W=W, corr=corr, m=m, rho=rh[:, 0] + 1j * rh[:, 1],
                 status=st)
 

@@ -63,6 +63,18 @@
  *      2^-53 from word a of the Philox block at counter (i, 0, s, 3): a
  *      uniform random force of the variance 2 m kT / (accel tau dt) of the
  *      Euler-Maruyama step; the first half kick of the next step uses it too.
+ *  R15 Verlet skin (Sec. 2.3 remarks that cells slightly larger than r_eta
+ *      spare rebuilding the lists every step; the scheme is not given): with
+ *      skin d > 0, a stored list V(i) = {j != i : r_ij <= r_s + d} is built
+ *      from the positions of a rebuild step t_b, by the exact rule of R2 with
+ *      floor(((r_s + d) 2^32/L)^2), in the canonical order of R3 at t_b.  At
+ *      a later step the sets C(i), S(i) are the members of V(i) classified by
+ *      R2 at the current positions, kept in the order of V(i); the ordinals
+ *      of R3 index S(i) in that order.  A rebuild is due when some atom's
+ *      fixed-point displacement since t_b, sum_a (int32)(s_a - s_a(t_b))^2,
+ *      exceeds floor((d/2 2^32/L)^2): below it every pair within r_s now was
+ *      within r_s + d at t_b (triangle inequality), so C(i) and S(i) equal
+ *      those of the stencil at every step.
  *  R8  Energy estimator: E_real = 1/2 sum_i [sum_C u_ij + w_i sum_B u_ij];
  *      E_k = (S/P) sum_l (2 pi k_e / (V k_l^2)) |rho_l|^2;
  *      E_self = -k_e sqrt(alpha/pi) sum q^2  (Eq. (2.3) terms, reweighted).
@@ -99,6 +111,7 @@ typedef struct orc_params {
     int kpool_burn;          /* R13: burn-in iterations of the MH chains   */
     double lang_kT;          /* R14: thermostat kT (energy units)         */
     double lang_tau;         /* R14: relaxation time; <= 0 thermostat off */
+    double skin;             /* R15: Verlet skin d (0: lists every step)  */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -669,19 +682,122 @@ static void canonical_order(const grid_storage* gs, int n, int32_t* order)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Stored lists of the Verlet-skin variant (R15)                            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    grid_storage gs;   /* grid of the rebuild step t_b */
+    int32_t* order;    /* canonical order at t_b (brute-force enumeration) */
+    int reach;         /* stencil reach for r_s + d */
+    uint64_t Rv2;      /* floor(((r_s + d) 2^32 / L)^2) */
+} skin_grid;
+
+static void skin_grid_build(int n, const double* pos_b, const orc_params* pr, skin_grid* sg)
+{
+    build_grid(n, pos_b, pr, &sg->gs);
+    double rv = pr->r_s + pr->skin;
+    sg->reach = (int)floor(rv * (double)sg->gs.n_cell / pr->L) + 1;
+    sg->Rv2 = orc_radius2_fixed(rv, pr->L);
+    sg->order = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    canonical_order(&sg->gs, n, sg->order);
+}
+
+static void skin_grid_free(skin_grid* sg)
+{
+    free(sg->order);
+    free_grid(&sg->gs);
+}
+
+/* V(i): candidates of the rebuild step in canonical order (the stencil for
+ * r_s + d, or every atom when brute), kept when j != i and their exact
+ * squared distance at t_b is at most Rv2.  tmp holds n ids. */
+static void stored_list(const skin_grid* sg, int n, int i, int brute, int32_t* tmp, cand_list* out)
+{
+    const grid_storage* gs = &sg->gs;
+    const int32_t* cand;
+    int ncand;
+    if (brute) {
+        cand = sg->order;
+        ncand = n;
+    } else {
+        orc_grid gb = {n, gs->s, gs->cell, gs->Rc2, gs->Rs2, gs->n_cell, gs->cell_start, gs->cell_atoms};
+        cand_list c = {0, tmp};
+        candidates_cells(&gb, i, sg->reach, &c);
+        cand = tmp;
+        ncand = c.count;
+    }
+    const uint32_t* si = gs->s + 3 * i;
+    out->count = 0;
+    for (int t = 0; t < ncand; ++t) {
+        int j = cand[t];
+        if (j == i) continue;
+        if (dist2_fixed(si, gs->s + 3 * j) <= sg->Rv2) out->ids[out->count++] = j;
+    }
+}
+
+/* R15 rebuild test: 1 when some atom moved, in fixed-point units, by more
+ * than d/2 since the rebuild positions pos_b (sum of squared wrapped
+ * differences above floor((d/2 2^32/L)^2)), else 0. */
+int orc_skin_displaced(int n, const double* pos, const double* pos_b, double L, double skin)
+{
+    double invL = 1.0 / L;
+    uint64_t D2 = orc_radius2_fixed(0.5 * skin, L);
+    for (int i = 0; i < n; ++i) {
+        uint32_t a[3], b[3];
+        for (int k = 0; k < 3; ++k) {
+            a[k] = fixed_point(pos[3 * i + k], invL);
+            b[k] = fixed_point(pos_b[3 * i + k], invL);
+        }
+        if (dist2_fixed(a, b) > D2) return 1;
+    }
+    return 0;
+}
+
+/* R15 stored lists themselves: counts[i] = |V(i)|, ids (cap per atom) in the
+ * order of V(i); brute = 1 enumerates every atom instead of the stencil.
+ * Returns 1 if some list exceeded cap, else 0. */
+int orc_skin_lists(int n, const double* pos_b, const orc_params* pr, int brute, int32_t* counts, int32_t* ids,
+                   int cap)
+{
+    skin_grid sg;
+    skin_grid_build(n, pos_b, pr, &sg);
+    int status = 0;
+#pragma omp parallel
+    {
+        int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+        cand_list v = {0, (int32_t*)malloc(sizeof(int32_t) * (size_t)n)};
+        int local = 0;
+#pragma omp for schedule(dynamic, 64)
+        for (int i = 0; i < n; ++i) {
+            stored_list(&sg, n, i, brute, tmp, &v);
+            counts[i] = v.count;
+            if (v.count > cap) local = 1;
+            if (ids)
+                for (int t = 0; t < v.count && t < cap; ++t) ids[(size_t)i * cap + t] = v.ids[t];
+        }
+#pragma omp critical
+        status |= local;
+        free(tmp); free(v.ids);
+    }
+    skin_grid_free(&sg);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Lists only (for bit-exact comparisons)                                   */
 /* ------------------------------------------------------------------------ */
 /* For every atom: n_core[i], n_shell[i], core ids (row-major, cap_core per
  * atom, canonical order), batch ids (cap_batch per atom, slot order), and
  * n_batch[i].  brute=1 enumerates all atoms, 0 uses the cell stencil.
  * Returns 0, or 1 if some list exceeded a cap, 2 on an r=0 overlap. */
-int orc_lists(int n, const double* pos, const orc_params* pr, uint64_t step, int brute,
-              int32_t* n_core, int32_t* n_shell, int32_t* n_batch,
-              int32_t* core, int cap_core, int32_t* batch, int cap_batch,
-              int32_t* shell, int cap_shell)
+static int lists_impl(int n, const double* pos, const double* pos_b, const orc_params* pr, uint64_t step, int brute,
+                      int32_t* n_core, int32_t* n_shell, int32_t* n_batch,
+                      int32_t* core, int cap_core, int32_t* batch, int cap_batch,
+                      int32_t* shell, int cap_shell)
 {
     grid_storage gs;
     build_grid(n, pos, pr, &gs);
+    skin_grid sg;
+    if (pos_b) skin_grid_build(n, pos_b, pr, &sg);
     orc_grid g = {n, gs.s, gs.cell, gs.Rc2, gs.Rs2, gs.n_cell, gs.cell_start, gs.cell_atoms};
     int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     canonical_order(&gs, n, order);
@@ -696,11 +812,16 @@ int orc_lists(int n, const double* pos, const orc_params* pr, uint64_t step, int
         uint64_t* words = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(pr->p + 4));
         uint64_t* ord = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(pr->p + 4));
         int local_status = 0;
+        cand_list v = {0, pos_b ? (int32_t*)malloc(sizeof(int32_t) * (size_t)n) : NULL};
 #pragma omp for schedule(dynamic, 64)
         for (int i = 0; i < n; ++i) {
             int ncand;
             const int32_t* cl;
-            if (brute) { cl = order; ncand = n; }
+            if (pos_b) {
+                /* R15: the members of V(i), in its order */
+                stored_list(&sg, n, i, brute, cand, &v);
+                cl = v.ids; ncand = v.count;
+            } else if (brute) { cl = order; ncand = n; }
             else {
                 cand_list c = {0, cand};
                 candidates_cells(&g, i, gs.reach, &c);
@@ -724,11 +845,32 @@ int orc_lists(int n, const double* pos, const orc_params* pr, uint64_t step, int
         }
 #pragma omp critical
         status |= local_status;
-        free(cand); free(al.core); free(al.shell); free(al.batch); free(words); free(ord);
+        free(cand); free(al.core); free(al.shell); free(al.batch); free(words); free(ord); free(v.ids);
     }
     free(order);
     free_grid(&gs);
+    if (pos_b) skin_grid_free(&sg);
     return status;
+}
+
+int orc_lists(int n, const double* pos, const orc_params* pr, uint64_t step, int brute,
+              int32_t* n_core, int32_t* n_shell, int32_t* n_batch,
+              int32_t* core, int cap_core, int32_t* batch, int cap_batch,
+              int32_t* shell, int cap_shell)
+{
+    return lists_impl(n, pos, NULL, pr, step, brute, n_core, n_shell, n_batch, core, cap_core, batch, cap_batch,
+                      shell, cap_shell);
+}
+
+/* R15: the lists of a step classified from the stored lists of the rebuild
+ * positions pos_b (pr->skin > 0); brute = 1 builds V(i) from every atom. */
+int orc_lists_skin(int n, const double* pos, const double* pos_b, const orc_params* pr, uint64_t step, int brute,
+                   int32_t* n_core, int32_t* n_shell, int32_t* n_batch,
+                   int32_t* core, int cap_core, int32_t* batch, int cap_batch,
+                   int32_t* shell, int cap_shell)
+{
+    return lists_impl(n, pos, pos_b, pr, step, brute, n_core, n_shell, n_batch, core, cap_core, batch, cap_batch,
+                      shell, cap_shell);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -810,13 +952,15 @@ static void rbe_fourier(int n, const double* pos, const double* q, const orc_par
  * of each force component (pair terms, the correction, the k terms): the
  * scale that bounds the rounding error of the component.  mol may be NULL
  * (no exclusions); every output pointer may be NULL. */
-int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* type,
-                   const int32_t* mol, const orc_params* pr, uint64_t step,
-                   double* F, double* F_real_out, double* F_long_out, double* E, double* W,
-                   double* corr, int32_t* m_out, double* rho_out, double* F_abs)
+static int rbe_forces_impl(int n, const double* pos, const double* pos_b, const double* q, const int32_t* type,
+                           const int32_t* mol, const orc_params* pr, uint64_t step,
+                           double* F, double* F_real_out, double* F_long_out, double* E, double* W,
+                           double* corr, int32_t* m_out, double* rho_out, double* F_abs)
 {
     grid_storage gs;
     build_grid(n, pos, pr, &gs);
+    skin_grid sg;
+    if (pos_b) skin_grid_build(n, pos_b, pr, &sg);
     orc_grid g = {n, gs.s, gs.cell, gs.Rc2, gs.Rs2, gs.n_cell, gs.cell_start, gs.cell_atoms};
     pair_consts pc;
     make_pair_consts(pr, &pc);
@@ -835,11 +979,18 @@ int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* typ
         uint64_t* words = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(pr->p + 4));
         uint64_t* ord = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(pr->p + 4));
         int local_status = 0;
+        cand_list v = {0, pos_b ? (int32_t*)malloc(sizeof(int32_t) * (size_t)n) : NULL};
 #pragma omp for schedule(dynamic, 64)
         for (int i = 0; i < n; ++i) {
             cand_list c = {0, cand};
-            candidates_cells(&g, i, gs.reach, &c);
-            classify_and_sample(&g, i, cand, c.count, pr->p, pr->shell_mode, pr->seed, step, &al, words, ord);
+            if (pos_b) {
+                /* R15: the members of the stored list V(i), in its order */
+                stored_list(&sg, n, i, 0, cand, &v);
+                classify_and_sample(&g, i, v.ids, v.count, pr->p, pr->shell_mode, pr->seed, step, &al, words, ord);
+            } else {
+                candidates_cells(&g, i, gs.reach, &c);
+                classify_and_sample(&g, i, cand, c.count, pr->p, pr->shell_mode, pr->seed, step, &al, words, ord);
+            }
             if (al.overlap) local_status |= 2;
             double w_shell = (al.n_shell <= pr->p) ? 1.0 : (double)al.n_shell / (double)pr->p;
             double f[3] = {0, 0, 0}, u[3] = {0, 0, 0}, wv[6] = {0, 0, 0, 0, 0, 0}, fa[3] = {0, 0, 0};
@@ -871,8 +1022,9 @@ int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* typ
         }
 #pragma omp critical
         status |= local_status;
-        free(cand); free(al.core); free(al.shell); free(al.batch); free(words); free(ord);
+        free(cand); free(al.core); free(al.shell); free(al.batch); free(words); free(ord); free(v.ids);
     }
+    if (pos_b) skin_grid_free(&sg);
     /* Eq. (2.12): net force of the real-space estimate (compensated sums) */
     double cr[3];
     for (int a = 0; a < 3; ++a) {
@@ -927,6 +1079,26 @@ int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* typ
     free(Freal); free(Eat); free(Wat); free(Aat);
     free_grid(&gs);
     return status;
+}
+
+int orc_rbe_forces(int n, const double* pos, const double* q, const int32_t* type,
+                   const int32_t* mol, const orc_params* pr, uint64_t step,
+                   double* F, double* F_real_out, double* F_long_out, double* E, double* W,
+                   double* corr, int32_t* m_out, double* rho_out, double* F_abs)
+{
+    return rbe_forces_impl(n, pos, NULL, q, type, mol, pr, step, F, F_real_out, F_long_out, E, W, corr, m_out,
+                           rho_out, F_abs);
+}
+
+/* R15: the estimator of a step whose sets C(i), S(i) come from the stored
+ * lists of the rebuild positions pos_b (pr->skin > 0). */
+int orc_rbe_forces_skin(int n, const double* pos, const double* pos_b, const double* q, const int32_t* type,
+                        const int32_t* mol, const orc_params* pr, uint64_t step,
+                        double* F, double* F_real_out, double* F_long_out, double* E, double* W,
+                        double* corr, int32_t* m_out, double* rho_out, double* F_abs)
+{
+    return rbe_forces_impl(n, pos, pos_b, q, type, mol, pr, step, F, F_real_out, F_long_out, E, W, corr, m_out,
+                           rho_out, F_abs);
 }
 
 /* ------------------------------------------------------------------------ */
