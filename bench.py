@@ -333,6 +333,100 @@ def _batch_leg(flush):
     }
 
 
+def _configs_leg(flush):
+    """The other configurations' lines (each after its own warm-up, CUDA
+    events on the launching stream, L2 flushed between timed calls):
+    the 2,000-ion 1:1 electrolyte in FP64 (one force evaluation, then 100
+    velocity-Verlet NVE steps at dt = 0.002 tau, in tau/day) with the force
+    RMS error of the estimator against a converged exact Ewald sum of the
+    oracle; the 90,000-atom water box in FP64 (force evaluations and 100
+    velocity-Verlet steps at 1 fs)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2204_13595_gb300 import rbe, systems
+
+    stream = torch.cuda.current_stream()
+    dev = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device="cuda")
+
+    def timed(fn, n):
+        tot = 0.0
+        for k in range(n):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(k)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / n
+
+    out = {}
+    for key, s, nsteps, unit_day in (("electrolyte_2000_fp64", systems.electrolyte(), 100, "tau_per_day"),
+                                     ("water_90k_fp64", systems.water(30000, seed=2), 100, "ns_per_day")):
+        c = rbe.Context.for_system(s, precision=rbe.FP64)
+        d = dict(pos=dev(s.pos), vel=dev(s.vel), mass=dev(s.mass), q=dev(s.q), typ=dev(s.type, torch.int32),
+                 mol=None if s.mol is None else dev(s.mol, torch.int32))
+        F = torch.empty_like(d["pos"])
+        for k in range(3):
+            c.forces(k, d["pos"], d["q"], d["typ"], d["mol"], F)
+        f_ms = timed(lambda k: c.forces(3 + k, d["pos"], d["q"], d["typ"], d["mol"], F), 10)
+        c.forces(0, d["pos"], d["q"], d["typ"], d["mol"], F)
+        F0 = F.cpu().numpy()
+        s_ms = timed(lambda k: c.step(0, nsteps, s.dt, s.accel, d["pos"], d["vel"], d["mass"], d["q"], d["typ"],
+                                      d["mol"], F), 1) / nsteps
+        if c.sync_status() != 0:
+            raise RuntimeError(f"device status error in the {key} leg")
+        steps_per_s = 1e3 / s_ms
+        row = {"n_atoms": s.n, "force_evals_per_s": 1e3 / f_ms, "force_ms": f_ms, "steps": nsteps,
+               "md_ms_per_step": s_ms, "md_steps_per_s": steps_per_s,
+               unit_day: steps_per_s * s.dt * 86400.0 * (1e-6 if unit_day == "ns_per_day" else 1.0)}
+        if key.startswith("electrolyte"):
+            # the method's own (stochastic) error: the estimator at step 0
+            # against real space to r_s plus the full reciprocal sum
+            pr = oracle.make_params(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, s.seed, k_e=s.k_e, eps=s.eps,
+                                    sigma=s.sigma)
+            kmax = int(np.ceil(np.sqrt(46.0 * s.alpha * s.L ** 2) / np.pi)) + 1
+            t0 = time.perf_counter()
+            ex = oracle.ewald_exact(s.pos, s.q, s.type, s.mol, pr, s.r_s, kmax)["F"]
+            row["exact_ewald_s"] = time.perf_counter() - t0
+            row["force_rms_rel_err_vs_exact_ewald"] = float(np.sqrt(((F0 - ex) ** 2).mean() / (ex ** 2).mean()))
+        out[key] = row
+        c.close()
+    return out
+
+
+def _oracle_timings():
+    """The oracle on one host core (a subprocess with OMP_NUM_THREADS=1): one
+    full FP64 force evaluation of the 1.2M-atom water box; and the exact Ewald
+    sum (real space to r_s, the full reciprocal sum to a 1e-20 tail) of the
+    12,000-atom water box on all host cores."""
+    import numpy as np
+
+    import oracle
+    from paper_2204_13595_gb300 import systems
+    code = ("import sys,time; sys.path.insert(0, %r)\n"
+            "import oracle\nfrom paper_2204_13595_gb300 import systems\n"
+            "s = systems.water(%d, seed=%d)\n"
+            "pr = oracle.make_params(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, %d, k_e=s.k_e, eps=s.eps, sigma=s.sigma)\n"
+            "t0 = time.perf_counter(); oracle.rbe_forces(s.pos, s.q, s.type, s.mol, pr, 0)\n"
+            "print(time.perf_counter() - t0)\n") % (ROOT, N_MOL, SEED, SEED)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    one = float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    w = systems.water(4000, seed=4)
+    pr = oracle.make_params(w.L, w.alpha, w.r_c, w.r_s, w.p, w.P, 4, k_e=w.k_e, eps=w.eps, sigma=w.sigma)
+    kmax = int(np.ceil(np.sqrt(46.0 * w.alpha * w.L ** 2) / np.pi)) + 1
+    t0 = time.perf_counter()
+    oracle.ewald_exact(w.pos, w.q, w.type, w.mol, pr, w.r_s, kmax)
+    ex_s = time.perf_counter() - t0
+    return {"oracle_1core_water_1p2M": {"force_evals_per_s": (1.0 / one) if one else None, "seconds": one,
+                                        "cores": 1},
+            "exact_ewald_water_12k": {"seconds": ex_s, "kmax": kmax,
+                                      "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}}
+
+
 def _next_rows_leg(flush, big):
     """Timing of the widened rows beside the headline (each after its own
     warm-up, CUDA events on the launching stream): the adjoint at frozen draws
@@ -500,6 +594,7 @@ def run_ours(args):
     ms_f64, _, _ = timed(f64, max(3, min(args.steps, 10)), max(3, min(args.warmup, 3)))
     batch = _batch_leg(flush) if ws == 1 else None
     next_rows = _next_rows_leg(flush, (s, pos, q, typ, mol)) if ws == 1 else None
+    configs = _configs_leg(flush) if ws == 1 else None
     clocks = _clock_summary(clocks_proc, local) if rank == 0 else None
 
     # end to end through the same C ABI with pinned host buffers
@@ -541,6 +636,7 @@ def run_ours(args):
     oracle.rbe_forces(s.pos, s.q, s.type, s.mol, pr, 0)
     cpu_s = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    oracle_more = _oracle_timings()
 
     value = replicas.throughput(ws, 1, ms_mixed)
     line = {
@@ -564,10 +660,12 @@ def run_ours(args):
             "note": "bench_peak_probe in this run (best of 3 launches): context for the derived peaks"},
         "cpu_baseline": {"value": 1.0 / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "one full FP64 oracle force evaluation of the same 1.2M-atom system"},
+        "oracle_timings": oracle_more,
         "e2e": {"value": replicas.throughput(ws, 1, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks, "gpu_launches": launches * args.steps,
         "batch": batch,
         "next_rows": next_rows,
+        "configs": configs,
     }
     print(json.dumps(line))
     if ws > 1:

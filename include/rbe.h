@@ -111,7 +111,13 @@ int rbe_set_water_bonds(rbe_ctx* ctx, int n_mol, double k_b, double r0, double k
 
 /* Per-atom list capacities used by the pair kernel (0 = automatic, from the
  * density: roughly twice the mean count plus a margin).  A list longer than its
- * capacity sets RBE_ECAPACITY in the status word. */
+ * capacity sets RBE_ECAPACITY in the status word and records the count met;
+ * the overflowing evaluation's forces are then wrong.  rbe_forces calls that
+ * wait (host pointers or host energy/virial) retry once with capacities that
+ * hold the counts met, rbe_step retries the failing step once the same way,
+ * and rbe_sync_status, when it reports RBE_ECAPACITY, grows the capacities
+ * for the next call.  Capacities that shared memory cannot hold give
+ * RBE_ECAPACITY from the next call. */
 int rbe_set_capacity(rbe_ctx* ctx, int core_cap, int shell_cap);
 
 /* One IRBE force evaluation at MD step `step` (Algorithm 1, force steps):
@@ -126,7 +132,9 @@ int rbe_set_capacity(rbe_ctx* ctx, int core_cap, int shell_cap);
  * be NULL, a host pointer (the call then waits for the stream) or a device
  * pointer.  Positions need not be wrapped into the box.
  * Errors found on the device (overlap, capacity, non-neutral charge,
- * non-finite input) are latched in a status word read by rbe_sync_status(). */
+ * non-finite input) are latched in a status word read by rbe_sync_status();
+ * a call that waits reads it itself and retries a capacity overflow once
+ * (rbe_set_capacity), leaving other errors latched. */
 int rbe_forces(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const double* q,
                const int32_t* type, const int32_t* mol, double* F, double* energy, double* virial,
                void* cuda_stream);
@@ -137,7 +145,18 @@ int rbe_forces(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const doub
  * kJ/mol/A, g/mol, fs).  On entry F must hold the forces at (pos, step0); on
  * exit it holds those at the final positions.  All arrays are device pointers;
  * energy_trace (device, may be NULL) receives per step the potential energy
- * (sum of the RBE_NE components) and the kinetic energy / accel. */
+ * (sum of the RBE_NE components) and the kinetic energy / accel.
+ * The call waits for the stream at its end.  An error latched on the device
+ * stops the integration there: the kicks of that and every later step leave
+ * positions and velocities as they are (a status latched before the call and
+ * not read stops it at its first step).  A capacity overflow in the force
+ * evaluation of a step is retried once: the capacities are grown to the
+ * counts met, that evaluation and the step's second half kick are redone and
+ * the remaining steps run.  Any other error, or a second overflow, is
+ * returned (and stays latched for rbe_sync_status); positions, velocities
+ * and F are then the state at the force evaluation that failed, whose step
+ * rbe_get_info reports (out[9]); the energy_trace entries from that step on
+ * are not meaningful. */
 int rbe_step(rbe_ctx* ctx, uint64_t step0, int nsteps, double dt, double accel, int n,
              double* pos, double* vel, const double* mass, const double* q, const int32_t* type,
              const int32_t* mol, double* F, double* energy_trace, void* cuda_stream);
@@ -161,7 +180,8 @@ int rbe_adjoint(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const dou
                 double* dLdeps, double* dLdsig, void* cuda_stream);
 
 /* Waits for cuda_stream, returns the first latched device error (or RBE_OK)
- * and clears the status word.  An evaluation whose input holds a non-finite
+ * and clears the status word; after RBE_ECAPACITY the next call uses
+ * capacities that hold the counts met.  An evaluation whose input holds a non-finite
  * position latches RBE_ENONFINITE and its result is undefined; such atoms are
  * placed on a lattice at the system's density for the rest of that step, so a
  * run that has blown up costs what a normal step costs until it is stopped. */
@@ -191,7 +211,8 @@ int rbe_get_kspace(rbe_ctx* ctx, int32_t* m, double* rho, void* cuda_stream);
  * from global memory, out[8] (atom, pass of 32 stencil rows) pairs of that
  * launch whose candidates (more than 2048) were classified range by range
  * instead of as one concatenated list (both counted with rbe_set_debug on;
- * -1 otherwise). */
+ * -1 otherwise), out[9] the step whose force evaluation stopped the last
+ * rbe_step (-1 if it ran to the end). */
 int rbe_get_info(rbe_ctx* ctx, double* out, int nout);
 
 /* Kernel timing: when on, every launch is bracketed by CUDA events on its

@@ -537,10 +537,19 @@ __device__ __forceinline__ void vv_body(int bx, int n, double* __restrict__ pos,
     }
 }
 
+// rbe_step's kick: once an error is latched (by the force evaluation it
+// would use, or earlier) it leaves positions and velocities as they are and
+// records its code (2k first half kick and drift of step k, 2k + 1 second
+// half kick) if it is the first to stop
 __global__ void __launch_bounds__(TPB) k_vv(int n, double* __restrict__ pos, double* __restrict__ vel,
                                             const double* __restrict__ mass, const double* __restrict__ F,
-                                            const double* __restrict__ FL, double hdta, double dt, int drift)
+                                            const double* __restrict__ FL, double hdta, double dt, int drift,
+                                            int* __restrict__ status, int code)
 {
+    if (*(volatile int*)status != 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(status + RBE_STW_HALT, -1, code);
+        return;
+    }
     vv_body(blockIdx.x, n, pos, vel, mass, F, FL, hdta, dt, drift);
 }
 
@@ -789,10 +798,11 @@ void launch_kforce(rbe_ctx* ctx, int n, double* F, cudaStream_t st)
 }
 
 void launch_vv_kick_drift(rbe_ctx* ctx, int n, double* pos, double* vel, const double* mass, const double* F,
-                          const double* FL, double dt, double accel, int drift, cudaStream_t st)
+                          const double* FL, double dt, double accel, int drift, int code, cudaStream_t st)
 {
     prof_begin(ctx, RBE_K_VV, st);
-    k_vv<<<(n + TPB - 1) / TPB, TPB, 0, st>>>(n, pos, vel, mass, F, FL, 0.5 * dt * accel, dt, drift);
+    k_vv<<<(n + TPB - 1) / TPB, TPB, 0, st>>>(n, pos, vel, mass, F, FL, 0.5 * dt * accel, dt, drift, ctx->status,
+                                              code);
     prof_end(ctx, RBE_K_VV, st);
 }
 

@@ -93,6 +93,12 @@ static_assert(sizeof(RowInfo) == 64, "RowInfo layout");
 // walked range by range instead.
 constexpr int RBL_MAX_RANGES = 64;
 constexpr int RBL_MAX_PACKED = 2048;
+// Words of the per-warp shell buffer used by the two-atom path beyond B's
+// core list: shell ballot words [2 * 64], their prefix counts for A and B
+// and the range-start prefix [3 * 64], the batches of A and B [2 * 32] and
+// B's slot ordinals [32]
+constexpr int RBL_PAIR_CARVE = 2 * 64 + 3 * 64 + 3 * 32;
+static_assert(RBL_PAIR_CARVE == RBE_RBL_PAIR_CARVE, "carve of the two-atom path");
 
 // Shared-memory layout of k_rbl; every section starts on a 16-byte boundary.
 // Per warp: the range table of the current pass [RBL_MAX_RANGES] int2 and the
@@ -157,13 +163,12 @@ __device__ __forceinline__ unsigned long long d2_exact(uint4 a, uint4 b)
 // bound already used to choose the segment's cells (conservative by
 // construction: every member of C or S has |dx| <= r_s < H - 1e-3 A), so no
 // member is dropped and the exact classification is unchanged.
-__device__ __forceinline__ void trim_segment(const float4* __restrict__ src, int& b, int& e, int cnt_lo, int cnt_hi,
-                                             bool one_cell, float xref, float H)
+__device__ __forceinline__ void trim_range(const float4* __restrict__ src, int& b, int& e, int cnt_lo, int cnt_hi,
+                                           bool one_cell, float lo_x, float hi_x)
 {
-    // the lower cut (first x >= xref - H in the first cell) and the upper cut
-    // (first x > xref + H in the last cell) are independent searches, run
+    // the lower cut (first x >= lo_x in the first cell) and the upper cut
+    // (first x > hi_x in the last cell) are independent searches, run
     // together so that their shared-memory loads overlap
-    const float lo_x = xref - H, hi_x = xref + H;
     int l = b, r = b + cnt_lo;
     int l2 = one_cell ? b : e - cnt_hi, r2 = e;
     while (l < r || l2 < r2) {
@@ -181,6 +186,29 @@ __device__ __forceinline__ void trim_segment(const float4* __restrict__ src, int
     }
     b = l;
     e = l2 < l ? l : l2;
+}
+
+__device__ __forceinline__ void trim_segment(const float4* __restrict__ src, int& b, int& e, int cnt_lo, int cnt_hi,
+                                             bool one_cell, float xref, float H)
+{
+    trim_range(src, b, e, cnt_lo, cnt_hi, one_cell, xref - H, xref + H);
+}
+
+// Position of the r-th set bit (r counted from 0) of m, r < popc(m): a
+// binary search on the population counts of halves.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int r)
+{
+    int base = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (r >= c) {
+            r -= c;
+            m >>= w;
+            base += w;
+        }
+    }
+    return base;
 }
 
 // Classification of one canonical segment [beg, end) of the source array:
@@ -415,6 +443,88 @@ __device__ __forceinline__ void classify_packed(const float4* __restrict__ stage
     }
 }
 
+// Classification of the concatenated candidate ranges of one pass against two
+// atoms A and B of the same cell row at once (the ranges cover the union of
+// their stencils).  The range lookup and the staged load of each candidate
+// are shared; each atom gets its own FP32 distance and exact decision in the
+// rounding bands.  Core members are appended in order to each atom's buffer;
+// the shell membership of chunk k (positions 32k .. 32k+31) is kept as one
+// ballot word per atom, smask[2k] for A and smask[2k+1] for B, so that shell
+// ordinals can later be mapped back to candidates without a shell list.
+// Without B (hasB false) B's sets are empty.  Two chunks per iteration, then
+// one; lanes past T load a fixed staged slot and are not classified.
+__device__ __forceinline__ void classify_pair(const float4* __restrict__ stage, const int2* __restrict__ ranges,
+                                              const unsigned* __restrict__ rstart, int T, float4 pA, float4 pB,
+                                              bool hasB, const RblArgs& a, int iA, int iB, uint4 sA, uint4 sB,
+                                              int lane, unsigned lt_mask, int* coreA, int* coreB,
+                                              unsigned* smask, int& ncA, int& ncB, bool& overlap)
+{
+    const RblGeom& g = a.g;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned le_mask = lt_mask | (1u << lane);
+    int before = 0;
+    int v0 = 0;
+    for (; T - v0 > 32; v0 += 64) {
+        const unsigned wa = rstart[v0 >> 5], wb = rstart[(v0 >> 5) + 1];
+        const int2 ra = ranges[before + __popc(wa & le_mask) - 1];
+        const int2 rb = ranges[before + __popc(wa) + __popc(wb & le_mask) - 1];
+        before += __popc(wa) + __popc(wb);
+        const int va = v0 + lane, vb = va + 32;
+        const bool vbok = vb < T;
+        const float4 qa = stage[va + ra.x];
+        const float4 qb = stage[vbok ? vb + rb.x : va + ra.x];
+        const int ga = va + ra.y, gb = vb + rb.y;
+        bool caA, saA, maA, cbA, sbA, mbA, caB, saB, maB, cbB, sbB, mbB;
+        dist_class<false>(qa, true, pA.x, pA.y, pA.z, g, 0.f, 0.f, caA, saA, maA);
+        dist_class<false>(qb, vbok, pA.x, pA.y, pA.z, g, 0.f, 0.f, cbA, sbA, mbA);
+        dist_class<false>(qa, hasB, pB.x, pB.y, pB.z, g, 0.f, 0.f, caB, saB, maB);
+        dist_class<false>(qb, hasB && vbok, pB.x, pB.y, pB.z, g, 0.f, 0.f, cbB, sbB, mbB);
+        if (__any_sync(FULL, maA || mbA || maB || mbB)) {
+            if (maA) exact_class(a, iA, sA, ga, caA, saA, overlap);
+            if (mbA) exact_class(a, iA, sA, gb, cbA, sbA, overlap);
+            if (maB) exact_class(a, iB, sB, ga, caB, saB, overlap);
+            if (mbB) exact_class(a, iB, sB, gb, cbB, sbB, overlap);
+        }
+        const unsigned cma = __ballot_sync(FULL, caA), cmb = __ballot_sync(FULL, cbA);
+        const unsigned cna = __ballot_sync(FULL, caB), cnb = __ballot_sync(FULL, cbB);
+        const unsigned sma = __ballot_sync(FULL, saA), smb = __ballot_sync(FULL, sbA);
+        const unsigned sna = __ballot_sync(FULL, saB), snb = __ballot_sync(FULL, sbB);
+        const int pa = ncA + __popc(cma & lt_mask), pb = ncA + __popc(cma) + __popc(cmb & lt_mask);
+        const int qa2 = ncB + __popc(cna & lt_mask), qb2 = ncB + __popc(cna) + __popc(cnb & lt_mask);
+        if (caA && pa < a.core_cap) coreA[pa] = ga;
+        if (cbA && pb < a.core_cap) coreA[pb] = gb;
+        if (caB && qa2 < a.core_cap) coreB[qa2] = ga;
+        if (cbB && qb2 < a.core_cap) coreB[qb2] = gb;
+        ncA += __popc(cma) + __popc(cmb);
+        ncB += __popc(cna) + __popc(cnb);
+        if (lane == 0)
+            reinterpret_cast<uint4*>(smask)[v0 >> 6] = make_uint4(sma, sna, smb, snb);
+    }
+    if (v0 < T) {
+        const unsigned wa = rstart[v0 >> 5];
+        const int2 ra = ranges[before + __popc(wa & le_mask) - 1];
+        const int va = v0 + lane;
+        const bool vaok = va < T;
+        const float4 qa = stage[vaok ? va + ra.x : 0];
+        const int ga = va + ra.y;
+        bool caA, saA, maA, caB, saB, maB;
+        dist_class<false>(qa, vaok, pA.x, pA.y, pA.z, g, 0.f, 0.f, caA, saA, maA);
+        dist_class<false>(qa, hasB && vaok, pB.x, pB.y, pB.z, g, 0.f, 0.f, caB, saB, maB);
+        if (__any_sync(FULL, maA || maB)) {
+            if (maA) exact_class(a, iA, sA, ga, caA, saA, overlap);
+            if (maB) exact_class(a, iB, sB, ga, caB, saB, overlap);
+        }
+        const unsigned cma = __ballot_sync(FULL, caA), cna = __ballot_sync(FULL, caB);
+        const unsigned sma = __ballot_sync(FULL, saA), sna = __ballot_sync(FULL, saB);
+        const int pa = ncA + __popc(cma & lt_mask), qa2 = ncB + __popc(cna & lt_mask);
+        if (caA && pa < a.core_cap) coreA[pa] = ga;
+        if (caB && qa2 < a.core_cap) coreB[qa2] = ga;
+        ncA += __popc(cma);
+        ncB += __popc(cna);
+        if (lane == 0) reinterpret_cast<uint2*>(smask)[v0 >> 5] = make_uint2(sma, sna);
+    }
+}
+
 template <bool MIXED, bool SMALL, bool ADJ>
 __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
 {
@@ -497,6 +607,64 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
 
     const int units_per_row = (nc + G - 1) / G;
     const long nunits = (long)nc * nc * units_per_row;
+
+    // Eq. (2.10) in FP32 (mixed path) for atom i (fixed-point si, charge qi,
+    // (type, mol) ti) and partner j (sj, tj) with weight w: the Coulomb factor
+    // erfc (erfc - 1 = -erf for a same-molecule pair, the Ewald exclusion
+    // correction) and LJ; adds the force on i to ff and the weighted
+    // energies and virial to the per-lane sums
+    const float kef = (float)c.k_e, saf = (float)c.sqrt_alpha, tsaf = (float)c.two_sqrt_alpha_over_sqrt_pi;
+    auto mixed_term = [&](const uint4 si, const float qi, const int2 ti, const uint4 sj, const int2 tj, const float w,
+                          float* ff) {
+        const float dx = (float)(int)(sj.x - si.x) * c.Lfix;
+        const float dy = (float)(int)(sj.y - si.y) * c.Lfix;
+        const float dz = (float)(int)(sj.z - si.z) * c.Lfix;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        const float qq = kef * qi * __uint_as_float(sj.w);
+        const float ar = saf * r;
+        const float gauss = tsaf * __expf(-ar * ar);
+        const bool ex = ti.y == tj.y;
+        const float ec = erfcf(ar) - (ex ? 1.0f : 0.0f);
+        const float ucoul = qq * ec * rinv;
+        float sc = -qq * (ec * rinv + gauss) * rinv * rinv;
+        const int tt = ti.x * c.ntypes + tj.x;
+        const bool nolj = ex || !(r2 < f_rc2[tt]);
+        const float c12 = nolj ? 0.f : f_c12[tt], c6 = nolj ? 0.f : f_c6[tt];
+        const float ir2 = rinv * rinv;
+        const float ir6 = ir2 * ir2 * ir2;
+        sc -= (12.f * c12 * ir6 - 6.f * c6) * ir6 * ir2;
+        const float ulj = (c12 * ir6 - c6) * ir6 - (nolj ? 0.f : f_sh[tt]);
+        const float gx = w * sc * dx, gy = w * sc * dy, gz = w * sc * dz;
+        ff[0] += gx; ff[1] += gy; ff[2] += gz;
+        facc_e[0] += ex ? 0.f : w * ucoul;
+        facc_e[1] += w * ulj;
+        facc_e[2] += ex ? w * ucoul : 0.f;
+        facc_w[0] += dx * gx; facc_w[1] += dy * gy; facc_w[2] += dz * gz;
+        facc_w[3] += dx * gy; facc_w[4] += dx * gz; facc_w[5] += dy * gz;
+    };
+    // flush of the FP32 per-lane sums into FP64 every 16 atoms
+    auto flush_sums = [&](int atoms) {
+        fl_count += atoms;
+        if (fl_count >= 16) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) { acc_e[q] += (double)facc_e[q]; facc_e[q] = 0.f; }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) { acc_w[q] += (double)facc_w[q]; facc_w[q] = 0.f; }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) { acc_f[q] += (double)facc_f[q]; facc_f[q] = 0.f; }
+            fl_count = 0;
+        }
+    };
+
+    // Two atoms per warp pass (mixed forward kernel, one pass of at most 32
+    // stencil rows, staged units): the per-warp buffers are carved for A's and
+    // B's core lists, the shell ballot words and their prefix counts, and the
+    // materialised batches (see pair_two below)
+    constexpr bool PAIRS = MIXED && !SMALL && !ADJ;
+    const bool pair_path = PAIRS && nrows <= 32 && lay.ga >= 2 && p <= 32 &&
+                           a.shell_cap >= a.core_cap + RBL_PAIR_CARVE;
 
     for (long unit = slot; unit < nunits; unit += nslots) {
         const int ux = (int)(unit % units_per_row);
@@ -614,26 +782,10 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
         }
         __syncthreads();
 
-        // ---- atoms of the unit, one per warp at a time -----------------------
-        int kloc = 0;
-        for (int i = A0 + wib; i < A1; i += WARPS, ++kloc) {
-            // Philox words of the shell slots, made for lay.ga atoms per pass:
-            // slot k of atom gi uses word k%4 of the block at (gi, k/4, step, 1)
-            const int aslot = kloc % lay.ga;
-            if (aslot == 0) {
-                __syncwarp();
-                for (int t = lane; t < lay.ga * nbk; t += 32) {
-                    const int aa = t / nbk, b = t - aa * nbk;
-                    const int ii = i + WARPS * aa;
-                    if (ii < A1) {
-                        uint64_t w[4];
-                        philox4x64_10((uint64_t)a.perm[ii], (uint64_t)b, a.step, 1ull, c.seed, 0ull, w);
-#pragma unroll
-                        for (int qd = 0; qd < 4; ++qd) words[aa * p_pad + 4 * b + qd] = w[qd];
-                    }
-                }
-                __syncwarp();
-            }
+        // ---- atoms of the unit -------------------------------------------------
+        // one_atom: lists, batch and pair terms of atom i, whose Philox words
+        // are wa_in[0 .. p_pad)
+        auto one_atom = [&](const int i, const uint64_t* wa_in) {
             const uint4 si = a.s4[i];
             const float4 fi4 = a.f4[i];
             const int cx = (int)cell_of_fixed(si.x, nc);
@@ -766,14 +918,18 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                 }
             }
             if (__any_sync(FULL, overlap) && lane == 0) latch_status(a.status, RBE_ST_OVERLAP);
-            if ((ncore > a.core_cap || nshell > a.shell_cap) && lane == 0) latch_status(a.status, RBE_ST_CAPACITY);
+            if ((ncore > a.core_cap || nshell > a.shell_cap) && lane == 0) {
+                latch_status(a.status, RBE_ST_CAPACITY);
+                atomicMax(a.status + RBE_STW_NEED_CORE, ncore);      // what a retry needs
+                atomicMax(a.status + RBE_STW_NEED_SHELL, nshell);
+            }
             const int ncore_c = min(ncore, a.core_cap);
             const int gi = a.perm[i];
 
             // ---- 2. shell batch (Floyd over ordinals) -----------------------
             const bool sample = nshell > p;
             const int nb = sample ? p : nshell;
-            const uint64_t* wa = words + (size_t)aslot * p_pad;
+            const uint64_t* wa = wa_in;
             if (sample && c.shell_mode == 1) {
                 // with replacement: slot k is ordinal floor(u_k N_S / 2^64)
                 for (int k = lane; k < p; k += 32) sel[k] = (int)uniform_below(wa[k], (uint32_t)nshell);
@@ -902,7 +1058,6 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
             } else if (MIXED) {
                 const float wsh = sample ? (float)nshell / (float)p : 1.0f;
                 const float qi = __uint_as_float(si.w);
-                const float kef = (float)c.k_e, saf = (float)c.sqrt_alpha, tsaf = (float)c.two_sqrt_alpha_over_sqrt_pi;
                 float ff[3] = {0.f, 0.f, 0.f};
                 auto pair_of = [&](int t, int& j, float& w) {
                     if (t < ncore_c) { j = core_buf[t]; w = 1.0f; }
@@ -913,35 +1068,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                         w = wsh;
                     }
                 };
-                auto term = [&](const uint4 sj, const int2 tj, const float w) {
-                    const float dx = (float)(int)(sj.x - si.x) * c.Lfix;
-                    const float dy = (float)(int)(sj.y - si.y) * c.Lfix;
-                    const float dz = (float)(int)(sj.z - si.z) * c.Lfix;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    const float rinv = rsqrtf(r2);
-                    const float r = r2 * rinv;
-                    const float qq = kef * qi * __uint_as_float(sj.w);
-                    const float ar = saf * r;
-                    const float gauss = tsaf * __expf(-ar * ar);
-                    const bool ex = ti.y == tj.y;
-                    const float ec = erfcf(ar) - (ex ? 1.0f : 0.0f);
-                    const float ucoul = qq * ec * rinv;
-                    float s = -qq * (ec * rinv + gauss) * rinv * rinv;
-                    const int tt = ti.x * c.ntypes + tj.x;
-                    const bool nolj = ex || !(r2 < f_rc2[tt]);
-                    const float c12 = nolj ? 0.f : f_c12[tt], c6 = nolj ? 0.f : f_c6[tt];
-                    const float ir2 = rinv * rinv;
-                    const float ir6 = ir2 * ir2 * ir2;
-                    s -= (12.f * c12 * ir6 - 6.f * c6) * ir6 * ir2;
-                    const float ulj = (c12 * ir6 - c6) * ir6 - (nolj ? 0.f : f_sh[tt]);
-                    const float gx = w * s * dx, gy = w * s * dy, gz = w * s * dz;
-                    ff[0] += gx; ff[1] += gy; ff[2] += gz;
-                    facc_e[0] += ex ? 0.f : w * ucoul;
-                    facc_e[1] += w * ulj;
-                    facc_e[2] += ex ? w * ucoul : 0.f;
-                    facc_w[0] += dx * gx; facc_w[1] += dy * gy; facc_w[2] += dz * gz;
-                    facc_w[3] += dx * gy; facc_w[4] += dx * gz; facc_w[5] += dy * gz;
-                };
+                auto term = [&](const uint4 sj, const int2 tj, const float w) { mixed_term(si, qi, ti, sj, tj, w, ff); };
                 // two pairs per lane per iteration (t, t + 32: the order of the
                 // one-pair loop), their loads issued together
                 for (int t = lane; t < npairs; t += 64) {
@@ -967,16 +1094,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     Fr[3 * (size_t)i + 2] = ff[2];
                     facc_f[0] += ff[0]; facc_f[1] += ff[1]; facc_f[2] += ff[2];
                 }
-                // flush the FP32 per-lane sums into FP64 every 16 atoms
-                if (++fl_count == 16) {
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) { acc_e[q] += (double)facc_e[q]; facc_e[q] = 0.f; }
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) { acc_w[q] += (double)facc_w[q]; facc_w[q] = 0.f; }
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) { acc_f[q] += (double)facc_f[q]; facc_f[q] = 0.f; }
-                    fl_count = 0;
-                }
+                flush_sums(1);
             } else {
                 const double wsh = sample ? (double)nshell / (double)p : 1.0;
                 const double4_32a pi = a.p4[i];
@@ -1049,6 +1167,322 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                 }
             }
             __syncwarp();
+        };
+        if (PAIRS && pair_path && staged) {
+            // Atoms A = i and B = i + 1 of the unit per warp pass.  Their
+            // stencils are the same 25 rows (one x-row of cells), so each
+            // lane cuts its row to the hull of A's and B's x ranges, and the
+            // concatenated candidates, in canonical order, are classified
+            // against both (classify_pair).  A pass whose concatenation
+            // exceeds RBL_MAX_PACKED falls back to one_atom for A and B.
+            int* coreA = core_buf;
+            int* coreB = shell_buf;
+            unsigned* smask = reinterpret_cast<unsigned*>(shell_buf + a.core_cap);   // [2 * 64]
+            int* pfxA = reinterpret_cast<int*>(smask + 128);                        // [64]
+            int* pfxB = pfxA + 64;                                                   // [64]
+            int* pfxR = pfxB + 64;                                                   // [64]
+            int* jA = pfxR + 64;                                                     // [32]
+            int* jB = jA + 32;                                                       // [32]
+            int* selA = sel;
+            int* selB = jB + 32;                                                     // [32]
+            const int gp = lay.ga >> 1;       // pairs whose Philox words are made in one pass
+            int kp = 0;
+            for (int i = A0 + 2 * wib; i < A1; i += 2 * WARPS, ++kp) {
+                const int pslot = kp % gp;
+                if (pslot == 0) {
+                    __syncwarp();
+                    for (int t = lane; t < 2 * gp * nbk; t += 32) {
+                        const int aa = t / nbk, b = t - aa * nbk;
+                        const int ii = i + 2 * WARPS * (aa >> 1) + (aa & 1);
+                        if (ii < A1) {
+                            uint64_t w[4];
+                            philox4x64_10((uint64_t)a.perm[ii], (uint64_t)b, a.step, 1ull, c.seed, 0ull, w);
+#pragma unroll
+                            for (int qd = 0; qd < 4; ++qd) words[aa * p_pad + 4 * b + qd] = w[qd];
+                        }
+                    }
+                    __syncwarp();
+                }
+                const uint64_t* waA = words + (size_t)(2 * pslot) * p_pad;
+                const uint64_t* waB = waA + p_pad;
+                const bool hasB = i + 1 < A1;
+                const int iA = i, iB = hasB ? i + 1 : i;
+                const uint4 sA = a.s4[iA], sB = a.s4[iB];
+                const float4 pA = a.f4[iA], pB = a.f4[iB];
+                const int cxA = (int)cell_of_fixed(sA.x, nc), cxB = (int)cell_of_fixed(sB.x, nc);
+                const float fxA = (float)sA.x * 2.3283064365386963e-10f, fxB = (float)sB.x * 2.3283064365386963e-10f;
+                const float fyA = (float)sA.y * 2.3283064365386963e-10f, fyB = (float)sB.y * 2.3283064365386963e-10f;
+                const float fzA = (float)sA.z * 2.3283064365386963e-10f, fzB = (float)sB.z * 2.3283064365386963e-10f;
+                if (hasB && cxB - cxA + 2 * R + 1 > nc) {
+                    // the hull of the two stencils would hold a cell twice
+                    // (small boxes with empty cells between A and B)
+                    one_atom(iA, waA);
+                    one_atom(iB, waB);
+                    continue;
+                }
+
+                // ---- 1. rows: segments of the hull of A's and B's x ranges -----
+                int b1 = 0, e1 = 0, b2 = 0, e2 = 0, o1 = 0, o2 = 0;
+                if (lane < nrows) {
+                    const RowInfo& ri = rows[lane];
+                    const int* cp = cellpos + lane * cpr;
+                    const int base = ri.sbase;
+                    const float gzA = fmaxf(0.f, ri.zs * (ri.zb - fzA)), gyA = fmaxf(0.f, ri.ys * (ri.yb - fyA));
+                    const float gzB = fmaxf(0.f, ri.zs * (ri.zb - fzB)), gyB = fmaxf(0.f, ri.ys * (ri.yb - fyB));
+                    const float g2A = gzA * gzA + gyA * gyA, g2B = gzB * gzB + gyB * gyB;
+                    const bool okA = g2A <= c.rs_frac2, okB = hasB && g2B <= c.rs_frac2;
+                    if (okA || okB) {
+                        const float hxA = okA ? sqrtf(c.rs_frac2 - g2A) + 1e-5f : 0.f;
+                        const float hxB = okB ? sqrtf(c.rs_frac2 - g2B) + 1e-5f : 0.f;
+                        const float flo = okA ? (okB ? fminf(fxA - hxA, fxB - hxB) : fxA - hxA) : fxB - hxB;
+                        const float fhi = okA ? (okB ? fmaxf(fxA + hxA, fxB + hxB) : fxA + hxA) : fxB + hxB;
+                        const float xlo = okA ? (okB ? fminf(pA.x - hxA * Lf, pB.x - hxB * Lf) : pA.x - hxA * Lf)
+                                              : pB.x - hxB * Lf;
+                        const float xhi = okA ? (okB ? fmaxf(pA.x + hxA * Lf, pB.x + hxB * Lf) : pA.x + hxA * Lf)
+                                              : pB.x + hxB * Lf;
+                        // unwrapped cells of the hull, within A's and B's
+                        // stencils (both inside the staged range [ul, uh])
+                        const int ua = max(cxA - R, (int)floorf(flo * ncf));
+                        const int ub = min(cxB + R, (int)floorf(fhi * ncf));
+                        int lo1, hi1, lo2 = 1, hi2 = 0;
+                        if (ua < 0) { lo1 = 0; hi1 = ub; lo2 = ua; hi2 = -1; }
+                        else if (ub >= nc) { lo1 = nc; hi1 = ub; lo2 = ua; hi2 = nc - 1; }
+                        else { lo1 = ua; hi1 = ub; }
+                        b1 = base + cp[lo1 - ul];
+                        e1 = base + cp[hi1 - ul + 1];
+                        o1 = ri.goff[lo1 >= nc ? 2 : 1];
+                        trim_range(stage, b1, e1, cp[lo1 - ul + 1] - cp[lo1 - ul], cp[hi1 - ul + 1] - cp[hi1 - ul],
+                                   lo1 == hi1, xlo, xhi);
+                        if (lo2 <= hi2) {
+                            b2 = base + cp[lo2 - ul];
+                            e2 = base + cp[hi2 - ul + 1];
+                            o2 = ri.goff[lo2 < 0 ? 0 : 1];
+                            trim_range(stage, b2, e2, cp[lo2 - ul + 1] - cp[lo2 - ul], cp[hi2 - ul + 1] - cp[hi2 - ul],
+                                       lo2 == hi2, xlo, xhi);
+                        }
+                    }
+                }
+                // concatenation in canonical order (as in one_atom)
+                const int n1 = e1 - b1, n2 = e2 - b2;
+                const int own = n1 + n2 + (((n1 > 0) + (n2 > 0)) << 16);
+                int incl = own;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int T = __shfl_sync(FULL, incl, 31) & 0xffff;
+                if (T >= RBL_MAX_PACKED) {
+                    // (below 2048 candidates every prefix count fits the 11-bit
+                    // fields packed below)
+                    if (a.debug && lane == 0) atomicAdd(a.dbg_unstaged + 1, 1);
+                    one_atom(iA, waA);
+                    if (hasB) one_atom(iB, waB);
+                    continue;
+                }
+                const int nch = (T + 31) >> 5;
+                for (int w = lane; w < nch; w += 32) rstart[w] = 0u;
+                __syncwarp();
+                {
+                    int v = (incl - own) & 0xffff, k = (incl - own) >> 16;
+                    if (n1 > 0) {
+                        ranges[k++] = make_int2(b1 - v, b1 + o1 - v);
+                        atomicOr(&rstart[v >> 5], 1u << (v & 31));
+                        v += n1;
+                    }
+                    if (n2 > 0) {
+                        ranges[k] = make_int2(b2 - v, b2 + o2 - v);
+                        atomicOr(&rstart[v >> 5], 1u << (v & 31));
+                    }
+                }
+                __syncwarp();
+
+                // ---- 2. classification against A and B -----------------------
+                int ncA = 0, ncB = 0;
+                bool overlap = false;
+                if (T > 0)
+                    classify_pair(stage, ranges, rstart, T, pA, pB, hasB, a, iA, iB, sA, sB, lane, lt_mask, coreA,
+                                  coreB, smask, ncA, ncB, overlap);
+                __syncwarp();
+                if (__any_sync(FULL, overlap) && lane == 0) latch_status(a.status, RBE_ST_OVERLAP);
+                if ((ncA > a.core_cap || ncB > a.core_cap) && lane == 0) {
+                    latch_status(a.status, RBE_ST_CAPACITY);
+                    atomicMax(a.status + RBE_STW_NEED_CORE, max(ncA, ncB));
+                }
+                const int ncAc = min(ncA, a.core_cap), ncBc = min(ncB, a.core_cap);
+
+                // exclusive prefix counts over the chunks (two per lane): shell
+                // members of A and B, range starts
+                int nsA, nsB;
+                {
+                    const unsigned wA0 = lane < nch ? smask[2 * lane] : 0u, wB0 = lane < nch ? smask[2 * lane + 1] : 0u;
+                    const unsigned wA1 = lane + 32 < nch ? smask[2 * lane + 64] : 0u;
+                    const unsigned wB1 = lane + 32 < nch ? smask[2 * lane + 65] : 0u;
+                    const unsigned r0 = lane < nch ? rstart[lane] : 0u, r1 = lane + 32 < nch ? rstart[lane + 32] : 0u;
+                    // three counts per word packed in one int: A | B << 11 | R << 22 (each < 2^11)
+                    const int c0 = __popc(wA0) | (__popc(wB0) << 11) | (__popc(r0) << 22);
+                    const int c1 = __popc(wA1) | (__popc(wB1) << 11) | (__popc(r1) << 22);
+                    int s0 = c0, s1 = c1;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t0 = __shfl_up_sync(FULL, s0, o), t1 = __shfl_up_sync(FULL, s1, o);
+                        if (lane >= o) { s0 += t0; s1 += t1; }
+                    }
+                    const int tot0 = __shfl_sync(FULL, s0, 31);
+                    const int ex0 = s0 - c0, ex1 = tot0 + s1 - c1;
+                    if (lane < nch) {
+                        pfxA[lane] = ex0 & 0x7ff; pfxB[lane] = (ex0 >> 11) & 0x7ff; pfxR[lane] = ex0 >> 22;
+                    }
+                    if (lane + 32 < nch) {
+                        pfxA[lane + 32] = ex1 & 0x7ff; pfxB[lane + 32] = (ex1 >> 11) & 0x7ff; pfxR[lane + 32] = ex1 >> 22;
+                    }
+                    const int all = tot0 + __shfl_sync(FULL, s1, 31);
+                    nsA = all & 0x7ff;
+                    nsB = hasB ? (all >> 11) & 0x7ff : 0;
+                }
+                __syncwarp();
+
+                // ---- 3. batches: ordinals (Floyd), then the members they name --
+                const bool sampA = nsA > p, sampB = nsB > p;
+                auto draw = [&](int nshell, const uint64_t* wa, int* out) {
+                    if (c.shell_mode == 1) {
+                        if (lane < p) out[lane] = (int)uniform_below(wa[lane], (uint32_t)nshell);
+                        return;
+                    }
+                    const uint32_t jk = (uint32_t)(nshell - p + lane);
+                    const int tk = lane < p ? (int)uniform_below(wa[lane], jk + 1u) : -1 - lane;
+                    const bool distinct = !__any_sync(FULL, (__match_any_sync(FULL, tk) & lt_mask) != 0u);
+                    int mysel = tk;
+                    if (!distinct) {
+                        mysel = -1;
+                        for (int k = 0; k < p; ++k) {
+                            const int t = __shfl_sync(FULL, tk, k);
+                            const bool dup = __any_sync(FULL, lane < k && mysel == t);
+                            if (lane == k) mysel = dup ? (int)jk : t;
+                        }
+                    }
+                    if (lane < p) out[lane] = mysel;
+                };
+                if (sampA) draw(nsA, waA, selA);
+                if (sampB) draw(nsB, waB, selB);
+                __syncwarp();
+                // member of ordinal t of the shell: chunk c with pfx[c] <= t <
+                // pfx[c + 1] (binary search), the (t - pfx[c])-th set bit of
+                // its ballot word, then the range holding that position
+                auto member = [&](int t, const int* pfx, int which) -> int {
+                    int lo = 0, hi = nch;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (pfx[mid] <= t) lo = mid;
+                        else hi = mid;
+                    }
+                    const int bit = nth_set_bit(smask[2 * lo + which], t - pfx[lo]);
+                    const int v = 32 * lo + bit;
+                    const unsigned upto = bit == 31 ? 0xffffffffu : ((2u << bit) - 1u);
+                    return v + ranges[pfxR[lo] + __popc(rstart[lo] & upto) - 1].y;
+                };
+                const int nbA = sampA ? p : nsA, nbB = sampB ? p : nsB;
+                if (lane < nbA) jA[lane] = member(sampA ? selA[lane] : lane, pfxA, 0);
+                if (lane < nbB) jB[lane] = member(sampB ? selB[lane] : lane, pfxB, 1);
+                __syncwarp();
+
+                // ---- 4. pair terms of A and B on the lanes of the warp ---------
+                const int npA = ncAc + nbA, npB = hasB ? ncBc + nbB : 0, npt = npA + npB;
+                const float wshA = sampA ? (float)nsA / (float)p : 1.0f;
+                const float wshB = sampB ? (float)nsB / (float)p : 1.0f;
+                const int2 tiA = a.tm[iA], tiB = a.tm[iB];
+                const float qiA = __uint_as_float(sA.w), qiB = __uint_as_float(sB.w);
+                float ffA[3] = {0.f, 0.f, 0.f}, ffB[3] = {0.f, 0.f, 0.f};
+                auto pair_of = [&](int t, int& j, float& w) {
+                    const bool isA = t < npA;
+                    const int k = isA ? t : t - npA;
+                    const int ncx = isA ? ncAc : ncBc;
+                    if (k < ncx) { j = isA ? coreA[k] : coreB[k]; w = 1.0f; }
+                    else { j = isA ? jA[k - ncx] : jB[k - ncx]; w = isA ? wshA : wshB; }
+                };
+                // one evaluation per lane whichever atom the pair belongs to
+                // (no divergence where a warp's pairs change from A to B)
+                auto term2 = [&](int t, const uint4 sj, const int2 tj, const float w) {
+                    const bool isA = t < npA;
+                    float g[3] = {0.f, 0.f, 0.f};
+                    mixed_term(isA ? sA : sB, isA ? qiA : qiB, isA ? tiA : tiB, sj, tj, w, g);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        ffA[q] += isA ? g[q] : 0.f;
+                        ffB[q] += isA ? 0.f : g[q];
+                    }
+                };
+                // two pairs per lane per iteration (t, t + 32), loads issued together
+                for (int t = lane; t < npt; t += 64) {
+                    const bool v2 = t + 32 < npt;
+                    int j1, j2;
+                    float w1, w2;
+                    pair_of(t, j1, w1);
+                    if (v2) pair_of(t + 32, j2, w2);
+                    else { j2 = j1; w2 = 0.f; }
+                    const uint4 sj1 = a.s4[j1];
+                    const int2 tj1 = a.tm[j1];
+                    const uint4 sj2 = a.s4[j2];
+                    const int2 tj2 = a.tm[j2];
+                    term2(t, sj1, tj1, w1);
+                    if (v2) term2(t + 32, sj2, tj2, w2);
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) { ffA[q] = warp_sum(ffA[q]); ffB[q] = warp_sum(ffB[q]); }
+                if (lane == 0) {
+                    float* Fr = reinterpret_cast<float*>(a.F_real);
+                    Fr[3 * (size_t)iA + 0] = ffA[0];
+                    Fr[3 * (size_t)iA + 1] = ffA[1];
+                    Fr[3 * (size_t)iA + 2] = ffA[2];
+                    facc_f[0] += ffA[0]; facc_f[1] += ffA[1]; facc_f[2] += ffA[2];
+                    if (hasB) {
+                        Fr[3 * (size_t)iB + 0] = ffB[0];
+                        Fr[3 * (size_t)iB + 1] = ffB[1];
+                        Fr[3 * (size_t)iB + 2] = ffB[2];
+                        facc_f[0] += ffB[0]; facc_f[1] += ffB[1]; facc_f[2] += ffB[2];
+                    }
+                }
+                flush_sums(hasB ? 2 : 1);
+
+                // ---- debug record (caller index order) ---------------------------
+                if (a.debug) {
+                    for (int x = 0; x < (hasB ? 2 : 1); ++x) {
+                        const int ix = x ? iB : iA, gx = a.perm[ix];
+                        const int ncx = x ? ncB : ncA, ncxc = x ? ncBc : ncAc, nsx = x ? nsB : nsA;
+                        const int nbx = x ? nbB : nbA;
+                        const int* cx_ = x ? coreB : coreA;
+                        const int* jx = x ? jB : jA;
+                        if (lane == 0) { a.dbg_ncore[gx] = ncx; a.dbg_nshell[gx] = nsx; }
+                        for (int t = lane; t < a.dbg_cap; t += 32)
+                            a.dbg_core[(size_t)gx * a.dbg_cap + t] = t < ncxc ? a.perm[cx_[t]] : -1;
+                        for (int k = lane; k < p; k += 32)
+                            a.dbg_batch[(size_t)gx * p + k] = k < nbx ? a.perm[jx[k]] : -1;
+                    }
+                }
+                __syncwarp();
+            }
+        } else {
+            int kloc = 0;
+            for (int i = A0 + wib; i < A1; i += WARPS, ++kloc) {
+                // Philox words of the shell slots, made for lay.ga atoms per pass:
+                // slot k of atom gi uses word k%4 of the block at (gi, k/4, step, 1)
+                const int aslot = kloc % lay.ga;
+                if (aslot == 0) {
+                    __syncwarp();
+                    for (int t = lane; t < lay.ga * nbk; t += 32) {
+                        const int aa = t / nbk, b = t - aa * nbk;
+                        const int ii = i + WARPS * aa;
+                        if (ii < A1) {
+                            uint64_t w[4];
+                            philox4x64_10((uint64_t)a.perm[ii], (uint64_t)b, a.step, 1ull, c.seed, 0ull, w);
+#pragma unroll
+                            for (int qd = 0; qd < 4; ++qd) words[aa * p_pad + 4 * b + qd] = w[qd];
+                        }
+                    }
+                    __syncwarp();
+                }
+                one_atom(i, words + (size_t)aslot * p_pad);
+            }
         }
     }
 

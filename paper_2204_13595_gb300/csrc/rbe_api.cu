@@ -165,7 +165,9 @@ int dev_alloc(rbe_ctx* ctx, T** p, size_t count)
 int round32(double x) { return ((int)ceil(x) + 31) / 32 * 32; }
 
 // Capacities of the per-warp core and shell buffers from the density:
-// twice the mean count plus six standard deviations plus a margin.
+// twice the mean count plus six standard deviations plus a margin; the shell
+// buffer also holds what the pair kernel's two-atom path keeps beyond a
+// second core list.
 void auto_caps(rbe_ctx* ctx, int n)
 {
     double rho = (double)n / (ctx->c.L * ctx->c.L * ctx->c.L);
@@ -176,6 +178,8 @@ void auto_caps(rbe_ctx* ctx, int n)
     int sc = ctx->user_shell_cap > 0 ? ctx->user_shell_cap : round32(2.0 * ms + 6.0 * sqrt(ms) + 32.0);
     ctx->core_cap = (cc + 31) / 32 * 32;
     ctx->shell_cap = (sc + 31) / 32 * 32;
+    if (ctx->user_shell_cap <= 0 && ctx->shell_cap < ctx->core_cap + RBE_RBL_PAIR_CARVE)
+        ctx->shell_cap = (ctx->core_cap + RBE_RBL_PAIR_CARVE + 31) / 32 * 32;
 }
 
 // Work-unit geometry of the RBL kernel and the rounding bound of its FP32
@@ -259,8 +263,11 @@ int ensure(rbe_ctx* ctx, int n)
         launch_cis_table(ctx->cis, 0);
         CUDA_TRY(ctx, cudaDeviceSynchronize());
         if ((rc = dev_alloc(ctx, &ctx->totals, 32 + 7 * (size_t)ctx->c.P))) return rc;
-        if ((rc = dev_alloc(ctx, &ctx->status, 1))) return rc;
-        CUDA_TRY(ctx, cudaMemset(ctx->status, 0, sizeof(int)));
+        if ((rc = dev_alloc(ctx, &ctx->status, RBE_STW_WORDS))) return rc;
+        {
+            const int init[RBE_STW_WORDS] = {0, 0, 0, -1};
+            CUDA_TRY(ctx, cudaMemcpy(ctx->status, init, sizeof(init), cudaMemcpyHostToDevice));
+        }
         CUDA_TRY(ctx, cudaMemset(ctx->totals, 0, sizeof(double) * (32 + 7 * (size_t)ctx->c.P)));
         if ((rc = dev_alloc(ctx, &ctx->lj, 1))) return rc;
         if ((rc = dev_alloc(ctx, &ctx->cell_count, ctx->ncells + 1))) return rc;
@@ -452,6 +459,32 @@ int status_code(int bits)
     return RBE_OK;
 }
 
+// Waits for the stream, reads the device status block into w and resets it
+// (bits and needed capacities to 0, halt code to -1).
+int read_status(rbe_ctx* ctx, cudaStream_t st, int w[RBE_STW_WORDS])
+{
+    const int init[RBE_STW_WORDS] = {0, 0, 0, -1};
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    CUDA_TRY(ctx, cudaMemcpy(w, ctx->status, sizeof(int) * RBE_STW_WORDS, cudaMemcpyDeviceToHost));
+    CUDA_TRY(ctx, cudaMemcpy(ctx->status, init, sizeof(init), cudaMemcpyHostToDevice));
+    return RBE_OK;
+}
+
+// After a list overflow: capacities that hold the largest counts met (plus
+// a margin, never smaller than before).  The next ensure() lays out shared
+// memory for them, or fails with RBE_ECAPACITY if they cannot fit.
+void grow_caps(rbe_ctx* ctx, const int w[RBE_STW_WORDS])
+{
+    int cc = w[RBE_STW_NEED_CORE] + 32, sc = w[RBE_STW_NEED_SHELL] + 32;
+    cc = cc > ctx->core_cap ? cc : ctx->core_cap;
+    sc = sc > ctx->shell_cap ? sc : ctx->shell_cap;
+    cc = (cc + 31) / 32 * 32;
+    if (sc < cc + RBE_RBL_PAIR_CARVE) sc = cc + RBE_RBL_PAIR_CARVE;     // room for the two-atom path
+    ctx->user_core_cap = cc;
+    ctx->user_shell_cap = (sc + 31) / 32 * 32;
+    ctx->last_n = -1;           // recompute caps, geometry and grids
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -525,6 +558,7 @@ int rbe_create(rbe_ctx** out, double box_L, double alpha, double r_c, double r_s
     ctx->ncells = ncells;
     ctx->device = -1;
     ctx->last_n = -1;
+    ctx->halt_step = -1;
     ctx->last_precision = -1;
     ctx->precision = RBE_FP64;
     refresh_consts(ctx);
@@ -704,7 +738,21 @@ int rbe_forces(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const doub
     if (rc) return rc;
     if ((rc = copy_out(ctx, energy, ctx->totals, RBE_NE, st, &need_sync))) return rc;
     if ((rc = copy_out(ctx, virial, ctx->totals + 6, RBE_NW, st, &need_sync))) return rc;
-    if (need_sync) CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (need_sync) {
+        // the call waits anyway: a list overflow is retried once with
+        // capacities that hold the counts met (other errors stay latched for
+        // rbe_sync_status)
+        int w[RBE_STW_WORDS];
+        if ((rc = read_status(ctx, st, w))) return rc;
+        if (w[0] == RBE_ST_CAPACITY && !ctx->retrying) {
+            grow_caps(ctx, w);
+            ctx->retrying = 1;
+            rc = rbe_forces(ctx, step, n, pos, q, type, mol, F, energy, virial, cuda_stream);
+            ctx->retrying = 0;
+            return rc;
+        }
+        if (w[0]) CUDA_TRY(ctx, cudaMemcpy(ctx->status, w, sizeof(int), cudaMemcpyHostToDevice));
+    }
     return RBE_OK;
 }
 
@@ -731,21 +779,58 @@ int rbe_step(rbe_ctx* ctx, uint64_t step0, int nsteps, double dt, double accel, 
             launch_langevin(ctx, n, vel, mass, step0, dt, accel, st);
     }
     const double* FL = lang ? ctx->F_lang : nullptr;
-    for (int k = 0; k < nsteps; ++k) {
-        launch_vv_kick_drift(ctx, n, pos, vel, mass, F, FL, dt, accel, 1, st);
-        rc = forces_device(ctx, step0 + (uint64_t)k + 1, n, pos, q, type, mol, F, st);
-        if (rc) return rc;
+    // the second half of step k: forces at step0 + k + 1, thermostat, kick
+    auto finish_step = [&](int k) -> int {
+        int r = forces_device(ctx, step0 + (uint64_t)k + 1, n, pos, q, type, mol, F, st);
+        if (r) return r;
         if (lang) launch_langevin(ctx, n, vel, mass, step0 + (uint64_t)k + 1, dt, accel, st);
-        launch_vv_kick_drift(ctx, n, pos, vel, mass, F, FL, dt, accel, 0, st);
+        launch_vv_kick_drift(ctx, n, pos, vel, mass, F, FL, dt, accel, 0, 2 * k + 1, st);
         if (energy_trace) launch_ke_trace(ctx, n, vel, mass, accel, energy_trace + 2 * (size_t)k, st);
+        return RBE_OK;
+    };
+    auto run = [&](int k0) -> int {
+        for (int k = k0; k < nsteps; ++k) {
+            launch_vv_kick_drift(ctx, n, pos, vel, mass, F, FL, dt, accel, 1, 2 * k, st);
+            int r = finish_step(k);
+            if (r) return r;
+        }
+        return RBE_OK;
+    };
+    ctx->halt_step = -1;
+    if ((rc = run(0))) return rc;
+    // A latched error stops the integration on the device (the kicks leave
+    // positions and velocities as they are).  A list overflow in the force
+    // evaluation of step k is retried once: capacities grown to the counts
+    // met, that evaluation and the second half kick redone, the remaining
+    // steps run.
+    int w[RBE_STW_WORDS];
+    if ((rc = read_status(ctx, st, w))) return rc;
+    if (w[0] == RBE_ST_CAPACITY && w[RBE_STW_HALT] >= 0 && (w[RBE_STW_HALT] & 1)) {
+        const int k = w[RBE_STW_HALT] >> 1;
+        grow_caps(ctx, w);
+        if ((rc = ensure(ctx, n))) return rc;
+        if ((rc = finish_step(k))) return rc;
+        if ((rc = run(k + 1))) return rc;
+        if ((rc = read_status(ctx, st, w))) return rc;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(ctx, RBE_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    if (w[0]) {
+        // stopped: the state is the one after the launch before the stop; the
+        // status stays latched for rbe_sync_status
+        const int h = w[RBE_STW_HALT];
+        ctx->halt_step = h < 0 ? -1 : (long long)(step0 + (uint64_t)(h >> 1) + (uint64_t)(h & 1));
+        ctx->lang_valid = 0;
+        CUDA_TRY(ctx, cudaMemcpy(ctx->status, w, sizeof(int), cudaMemcpyHostToDevice));
+        const int code = status_code(w[0]);
+        return set_err(ctx, code, "integration stopped at the force evaluation of step %lld (status bits 0x%x)",
+                       ctx->halt_step, w[0]);
     }
     if (lang) {
         ctx->lang_step = step0 + (uint64_t)nsteps;
         ctx->lang_valid = 1;
         ctx->lang_n = n;
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_err(ctx, RBE_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     return RBE_OK;
 }
 
@@ -822,12 +907,13 @@ int rbe_sync_status(rbe_ctx* ctx, void* cuda_stream)
     if (!ctx) return RBE_EINVAL;
     if (!ctx->status) return RBE_OK;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    int bits = 0;
-    CUDA_TRY(ctx, cudaStreamSynchronize(st));
-    CUDA_TRY(ctx, cudaMemcpy(&bits, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
-    CUDA_TRY(ctx, cudaMemset(ctx->status, 0, sizeof(int)));
-    int code = status_code(bits);
-    if (code) set_err(ctx, code, "device status bits 0x%x", bits);
+    int w[RBE_STW_WORDS];
+    int rc = read_status(ctx, st, w);
+    if (rc) return rc;
+    // a list overflow sizes the next call's capacities to the counts met
+    if (w[0] & RBE_ST_CAPACITY) grow_caps(ctx, w);
+    int code = status_code(w[0]);
+    if (code) set_err(ctx, code, "device status bits 0x%x", w[0]);
     return code;
 }
 
@@ -865,9 +951,10 @@ int rbe_get_info(rbe_ctx* ctx, double* out, int nout)
     int dbg[2] = {-1, -1};
     if (nout > 7 && ctx->debug && ctx->dbg_unstaged)
         CUDA_TRY(ctx, cudaMemcpy(dbg, ctx->dbg_unstaged, sizeof(dbg), cudaMemcpyDeviceToHost));
-    double v[9] = {(double)ctx->c.n_cell, (double)ctx->c.reach, (double)ctx->c.M, ctx->c.S, (double)ctx->core_cap,
-                   (double)ctx->shell_cap, (double)ctx->last_launches, (double)dbg[0], (double)dbg[1]};
-    for (int k = 0; k < nout && k < 9; ++k) out[k] = v[k];
+    double v[10] = {(double)ctx->c.n_cell, (double)ctx->c.reach, (double)ctx->c.M, ctx->c.S, (double)ctx->core_cap,
+                    (double)ctx->shell_cap, (double)ctx->last_launches, (double)dbg[0], (double)dbg[1],
+                    (double)ctx->halt_step};
+    for (int k = 0; k < nout && k < 10; ++k) out[k] = v[k];
     return RBE_OK;
 }
 

@@ -21,6 +21,18 @@
 #define RBE_WARPS_RBL 8          // warps per block of the pair kernel
 #define RBE_NPART_RBL 12         // Ec, Elj, Ex, W[6], Fsum[3]
 #define RBE_NPART_Q 3            // sum q^2, sum q, sum |q|
+#define RBE_RBL_PAIR_CARVE 416   // words of the per-warp shell buffer the two-atom pair path uses beyond a core list
+
+// Device status block of a context: word 0 holds the status bits below;
+// words 1 and 2 the largest core and shell counts of lists that overflowed
+// their capacity (what a retry needs); word 3 the first velocity-Verlet
+// launch of rbe_step that found a latched error and stopped (2k for the
+// first half kick and drift of step k, 2k + 1 for its second half kick; -1:
+// none)
+#define RBE_STW_NEED_CORE  1
+#define RBE_STW_NEED_SHELL 2
+#define RBE_STW_HALT       3
+#define RBE_STW_WORDS      4
 
 // status bits latched on the device
 #define RBE_ST_OVERLAP   1
@@ -125,7 +137,9 @@ struct rbe_ctx {
     double2* cis;        // [4096] e^{2 pi i j / 4096}: FP64 phase table
     double2* rho;        // [P]
     double* totals;      // [32]: E[6], W[6], corr[3], spare
-    int* status;         // [1]
+    int* status;         // [RBE_STW_WORDS] status bits, needed capacities, halt code
+    long long halt_step; // step whose force evaluation stopped the last rbe_step (-1: none)
+    int retrying;        // rbe_forces is re-running a call after a list overflow
     RbeLJ* lj;           // device copy
     int lj_dirty;
     // debug
@@ -340,7 +354,8 @@ void launch_bonded(rbe_ctx* ctx, int n, const double* pos, cudaStream_t st);
 void launch_finalize(rbe_ctx* ctx, int n, cudaStream_t st);
 void launch_kforce(rbe_ctx* ctx, int n, double* F, cudaStream_t st);
 void launch_vv_kick_drift(rbe_ctx* ctx, int n, double* pos, double* vel, const double* mass,
-                          const double* F, const double* FL, double dt, double accel, int drift, cudaStream_t st);
+                          const double* F, const double* FL, double dt, double accel, int drift, int code,
+                          cudaStream_t st);
 void launch_langevin(rbe_ctx* ctx, int n, const double* vel, const double* mass, uint64_t s, double dt,
                      double accel, cudaStream_t st);
 void launch_langevin_batch(const BatchPlan& bp, const int* mask, cudaStream_t st);

@@ -277,9 +277,10 @@ class Context:
         return m, rho[:, 0] + 1j * rho[:, 1]
 
     def info(self):
-        out = (ctypes.c_double * 9)()
-        self._check(self.L.rbe_get_info(self.h, out, 9))
-        keys = ["n_cell", "reach", "M", "S", "core_cap", "shell_cap", "launches", "unstaged_units", "walked_passes"]
+        keys = ["n_cell", "reach", "M", "S", "core_cap", "shell_cap", "launches", "unstaged_units", "walked_passes",
+                "halt_step"]
+        out = (ctypes.c_double * len(keys))()
+        self._check(self.L.rbe_get_info(self.h, out, len(keys)))
         return {k: out[i] for i, k in enumerate(keys)}
 
     def profile(self, reset=True, stream=None):

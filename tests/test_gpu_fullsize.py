@@ -30,8 +30,10 @@ def test_full_size_water(n_mol, seed):
     for k in (0, 2, 3, 4):
         assert erel[k] < 1e-12, k
     assert ek < 1e-12
-    mix = gpu_forces(s, step, precision=rbe.MIXED)
+    mix = gpu_forces(s, step, precision=rbe.MIXED, debug_cap=160)
     assert mix["status"] == 0
+    for k in ("n_core", "n_shell", "core", "batch"):
+        assert (mix["lists"][k] == ol[k]).all(), k
     em = rms_rel(mix["F"], f64["F"])
     print(f"water {s.n}: mixed force RMS rel err vs FP64 {em:.3e}")
     assert em <= 1e-4

@@ -46,9 +46,13 @@ def case(request):
     return request.param, s, step, ref, ol, cap
 
 
-def test_lists_and_batches_bit_exact(case):
+@pytest.mark.parametrize("precision", [rbe.FP64, rbe.MIXED])
+def test_lists_and_batches_bit_exact(case, precision):
+    """Both precisions decide membership by the exact rule (the mixed pair
+    kernel classifies two atoms per warp pass against the union of their
+    stencil rows, with the shell kept as ballot words)."""
     name, s, step, ref, ol, cap = case
-    out = gpu_forces(s, step, debug_cap=cap)
+    out = gpu_forces(s, step, debug_cap=cap, precision=precision)
     assert out["status"] == 0
     L = out["lists"]
     assert (L["n_core"] == ol["n_core"]).all()
@@ -187,7 +191,8 @@ def test_nonfinite_input_is_reported_and_the_context_recovers():
     assert cond_err(out["F"], ref) < F_TOL
 
 
-def test_lists_exact_at_the_radii():
+@pytest.mark.parametrize("precision", [rbe.FP64, rbe.MIXED])
+def test_lists_exact_at_the_radii(precision):
     """Pairs placed within 1e-9..1e-5 (relative) of r_c and r_s, in large and
     small boxes: the FP32 prefilter of the list kernel must defer to the exact
     fixed-point rule there, so the lists stay bit-exact."""
@@ -209,7 +214,7 @@ def test_lists_exact_at_the_radii():
         s.q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
         s.type = np.zeros(n, np.int32)
         s.mass = np.ones(n)
-        out = gpu_forces(s, 5, debug_cap=128)
+        out = gpu_forces(s, 5, debug_cap=128, precision=precision)
         ol = oracle.lists(s.pos, params(s), 5, cap_core=128)
         assert (out["lists"]["n_core"] == ol["n_core"]).all()
         assert (out["lists"]["n_shell"] == ol["n_shell"]).all()

@@ -17,10 +17,10 @@ pytestmark = pytest.mark.gpu
 CAP = 256
 
 
-def _ctx(s, precision, debug=True):
+def _ctx(s, precision, debug=True, shell_cap=512):
     c = rbe.Context(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, s.seed, k_e=s.k_e, eps=s.eps, sigma=s.sigma,
                     precision=precision)
-    c.set_capacity(128, 512)
+    c.set_capacity(128, shell_cap)
     if debug:
         c.set_debug(True, CAP)
     return c
@@ -46,6 +46,14 @@ def test_overflowing_units_match_oracle(step):
     assert cond_err(out["F"], ref) < 1e-11
     mixed = gpu_forces(s, step, ctx=_ctx(s, rbe.MIXED, debug=False))
     assert mixed["status"] == 0
+    assert rms_rel(mixed["F"], out["F"]) < 1e-4
+    # the mixed kernel with room for its two-atom path (staged units) next to
+    # units read from global memory (one atom at a time): same lists
+    mctx = _ctx(s, rbe.MIXED, shell_cap=640)
+    mixed = gpu_forces(s, step, ctx=mctx, debug_cap=CAP)
+    assert mixed["status"] == 0 and mctx.info()["unstaged_units"] > 0
+    for k in ("n_core", "n_shell", "core", "batch"):
+        assert (mixed["lists"][k] == ol[k]).all(), k
     assert rms_rel(mixed["F"], out["F"]) < 1e-4
 
 
@@ -77,3 +85,13 @@ def test_long_passes_walk_range_by_range():
     assert (L["core"] == ol["core"]).all() and (L["batch"] == ol["batch"]).all()
     ref = oracle.rbe_forces(s.pos, s.q, s.type, s.mol, pr, step)
     assert cond_err(out["F"], ref) < 1e-11
+    # mixed: pairs of atoms whose joint pass exceeds the packed limit fall
+    # back to one atom at a time
+    cm = rbe.Context(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, s.seed, k_e=s.k_e, eps=s.eps, sigma=s.sigma,
+                     precision=rbe.MIXED)
+    cm.set_debug(True, CAP)
+    mixed = gpu_forces(s, step, ctx=cm, debug_cap=CAP)
+    assert mixed["status"] == 0 and cm.info()["walked_passes"] > 0
+    for k in ("n_core", "n_shell", "core", "batch"):
+        assert (mixed["lists"][k] == ol[k]).all(), k
+    assert rms_rel(mixed["F"], out["F"]) < 1e-4
