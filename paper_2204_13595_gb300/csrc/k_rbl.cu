@@ -194,6 +194,20 @@ __device__ __forceinline__ void trim_segment(const float4* __restrict__ src, int
     trim_range(src, b, e, cnt_lo, cnt_hi, one_cell, xref - H, xref + H);
 }
 
+// erfc(x) for x >= 0 in FP32 by Hastings' approximation (Abramowitz & Stegun,
+// Handbook of Mathematical Functions, 7.1.26): erfc x = t (a1 + t (a2 + t (a3
+// + t (a4 + t a5)))) e^{-x^2}, t = 1 / (1 + p x), with absolute error below
+// 1.5e-7 for every x >= 0.  ex2 = e^{-x^2} is passed in: the pair force needs
+// it anyway.  Branch free, unlike a general erfc, whose argument ranges make
+// the lanes of a warp diverge.
+__device__ __forceinline__ float erfc_hastings(float x, float ex2)
+{
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    const float poly = fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                            0.254829592f);
+    return t * poly * ex2;
+}
+
 // Position of the r-th set bit (r counted from 0) of m, r < popc(m): a
 // binary search on the population counts of halves.
 __device__ __forceinline__ int nth_set_bit(unsigned m, int r)
@@ -624,9 +638,10 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
         const float r = r2 * rinv;
         const float qq = kef * qi * __uint_as_float(sj.w);
         const float ar = saf * r;
-        const float gauss = tsaf * __expf(-ar * ar);
+        const float ex2 = __expf(-ar * ar);
+        const float gauss = tsaf * ex2;
         const bool ex = ti.y == tj.y;
-        const float ec = erfcf(ar) - (ex ? 1.0f : 0.0f);
+        const float ec = erfc_hastings(ar, ex2) - (ex ? 1.0f : 0.0f);
         const float ucoul = qq * ec * rinv;
         float sc = -qq * (ec * rinv + gauss) * rinv * rinv;
         const int tt = ti.x * c.ntypes + tj.x;
@@ -665,6 +680,264 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     constexpr bool PAIRS = MIXED && !SMALL && !ADJ;
     const bool pair_path = PAIRS && nrows <= 32 && lay.ga >= 2 && p <= 32 &&
                            a.shell_cap >= a.core_cap + RBL_PAIR_CARVE;
+
+    // Per atom after its sets are known (core_buf[0 .. ncore), shell_buf[0 ..
+    // nshell) in canonical order): the shell batch (Algorithm 1, shell step),
+    // the pair terms of Eq. (2.10) and the debug record; wa_in holds the
+    // atom's Philox words
+    auto finish_atom = [&](const int i, const uint4 si, const int ncore, const int nshell, const bool overlap,
+                           const uint64_t* wa_in) {
+        if (__any_sync(FULL, overlap) && lane == 0) latch_status(a.status, RBE_ST_OVERLAP);
+        if ((ncore > a.core_cap || nshell > a.shell_cap) && lane == 0) {
+            latch_status(a.status, RBE_ST_CAPACITY);
+            atomicMax(a.status + RBE_STW_NEED_CORE, ncore);      // what a retry needs
+            atomicMax(a.status + RBE_STW_NEED_SHELL, nshell);
+        }
+        const int ncore_c = min(ncore, a.core_cap);
+        const int gi = a.perm[i];
+
+        // ---- 2. shell batch (Floyd over ordinals) -----------------------
+        const bool sample = nshell > p;
+        const int nb = sample ? p : nshell;
+        const uint64_t* wa = wa_in;
+        if (sample && c.shell_mode == 1) {
+            // with replacement: slot k is ordinal floor(u_k N_S / 2^64)
+            for (int k = lane; k < p; k += 32) sel[k] = (int)uniform_below(wa[k], (uint32_t)nshell);
+        } else if (sample) {
+            if (p <= 32) {
+                // slot k on lane k; the insertions resolved in slot order
+                const uint32_t jk = (uint32_t)(nshell - p + lane);
+                const int tk = lane < p ? (int)uniform_below(wa[lane], jk + 1u) : -1 - lane;
+                // if the p draws are distinct, no slot is replaced and every
+                // slot keeps its draw (by induction over the slots);
+                // otherwise resolve the slots in order
+                const bool distinct = !__any_sync(FULL, (__match_any_sync(FULL, tk) & lt_mask) != 0u);
+                int mysel = tk;
+                if (!distinct) {
+                    mysel = -1;
+                    for (int k = 0; k < p; ++k) {
+                        const int t = __shfl_sync(FULL, tk, k);
+                        const bool dup = __any_sync(FULL, lane < k && mysel == t);
+                        if (lane == k) mysel = dup ? (int)jk : t;
+                    }
+                }
+                if (lane < p) sel[lane] = mysel;
+            } else {
+                for (int k = 0; k < p; ++k) {
+                    const uint32_t jj = (uint32_t)(nshell - p + k);
+                    const int t = (int)uniform_below(wa[k], jj + 1u);
+                    bool dup = false;
+                    for (int l = lane; l < k; l += 32) dup |= (sel[l] == t);
+                    dup = __any_sync(FULL, dup);
+                    if (lane == 0) sel[k] = dup ? (int)jj : t;
+                    __syncwarp();
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---- 3. pair terms over C(i) and B(i) -----------------------------
+        // Eq. (2.10) with the Coulomb factor erfc (erfc - 1 = -erf for a
+        // same-molecule pair, the Ewald exclusion correction) and LJ.
+        const int npairs = ncore_c + nb;
+        const int2 ti = a.tm[i];
+        if constexpr (ADJ) {
+            // Gradients of E = 1/2 sum w_ij u_ij and of L = sum_i vt_i . F_real_i
+            // (vt = v - mean v, which carries the momentum correction of
+            // Eq. (2.13)) with respect to the charges and the LJ pair
+            // parameters; the part of a pair that belongs to q_j is added
+            // to atom j's slot atomically.
+            const double vtx = a.vs[3 * (size_t)i] - a.vbar[0];
+            const double vty = a.vs[3 * (size_t)i + 1] - a.vbar[1];
+            const double vtz = a.vs[3 * (size_t)i + 2] - a.vbar[2];
+            const double ke = c.k_e;
+            const double4_32a pi = a.p4[i];
+            double gE = 0.0, gL = 0.0;
+            for (int t = lane; t < npairs; t += 32) {
+                int j;
+                double w;
+                if (t < ncore_c) { j = core_buf[t]; w = 1.0; }
+                else {
+                    const int k = t - ncore_c;
+                    const int ord = sample ? sel[k] : k;
+                    j = shell_buf[min(ord, a.shell_cap - 1)];
+                    w = sample ? (double)nshell / (double)p : 1.0;
+                }
+                const int2 tj = a.tm[j];
+                const bool ex = ti.y == tj.y;
+                double dx, dy, dz, qj, phi, h, r2;
+                if (MIXED) {
+                    const uint4 sj = a.s4[j];
+                    const float fdx = (float)(int)(sj.x - si.x) * c.Lfix;
+                    const float fdy = (float)(int)(sj.y - si.y) * c.Lfix;
+                    const float fdz = (float)(int)(sj.z - si.z) * c.Lfix;
+                    const float fr2 = fdx * fdx + fdy * fdy + fdz * fdz;
+                    const float rinv = rsqrtf(fr2);
+                    const float ar = (float)c.sqrt_alpha * fr2 * rinv;
+                    const float gauss = (float)c.two_sqrt_alpha_over_sqrt_pi * __expf(-ar * ar);
+                    const float ec = erfcf(ar) - (ex ? 1.0f : 0.0f);
+                    phi = (double)(ec * rinv);
+                    h = (double)(-(ec * rinv + gauss) * rinv * rinv);
+                    dx = fdx; dy = fdy; dz = fdz; r2 = fr2;
+                    qj = (double)__uint_as_float(sj.w);
+                } else {
+                    const double4_32a pj = a.p4[j];
+                    dx = pj.x - pi.x; dy = pj.y - pi.y; dz = pj.z - pi.z;
+                    dx -= c.L * rint(dx * c.invL);
+                    dy -= c.L * rint(dy * c.invL);
+                    dz -= c.L * rint(dz * c.invL);
+                    r2 = dx * dx + dy * dy + dz * dz;
+                    const double rinv = rsqrt(r2);     // one reciprocal square root, no division
+                    const double rr = r2 * rinv;
+                    const double ar = c.sqrt_alpha * rr;
+                    const double gauss = c.two_sqrt_alpha_over_sqrt_pi * exp(-ar * ar);
+                    const double ec = ex ? -erf(ar) : erfc(ar);
+                    phi = ec * rinv;
+                    h = -(ec * rinv + gauss) * rinv * rinv;
+                    qj = pj.w;
+                }
+                const double qi = MIXED ? (double)__uint_as_float(si.w) : pi.w;
+                const double vd = vtx * dx + vty * dy + vtz * dz;
+                gE += 0.5 * w * ke * qj * phi;
+                gL += w * ke * qj * h * vd;
+                atomicAdd(&a.gq_tr[2 * (size_t)j], 0.5 * w * ke * qi * phi);
+                atomicAdd(&a.gq_tr[2 * (size_t)j + 1], w * ke * qi * h * vd);
+                const int tt = ti.x * c.ntypes + tj.x;
+                if (!ex && r2 < s_rc2[tt]) {
+                    const double e = s_eps[tt], sg = s_sig[tt];
+                    if (e != 0.0) {
+                        const double ir2 = 1.0 / r2;
+                        const double sr2 = sg * sg * ir2, sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
+                        const double du_de = 4.0 * (sr12 - sr6) - s_dsde[tt];
+                        const double du_ds = 4.0 * e * (12.0 * sr12 - 6.0 * sr6) / sg - s_dsds[tt];
+                        const double dh_de = -(48.0 * sr12 - 24.0 * sr6) * ir2;
+                        const double dh_ds = -e * (576.0 * sr12 - 144.0 * sr6) * ir2 / sg;
+                        atomicAdd(&s_glj[0 * nt2 + tt], 0.5 * w * du_de);
+                        atomicAdd(&s_glj[1 * nt2 + tt], 0.5 * w * du_ds);
+                        atomicAdd(&s_glj[2 * nt2 + tt], w * dh_de * vd);
+                        atomicAdd(&s_glj[3 * nt2 + tt], w * dh_ds * vd);
+                    }
+                }
+            }
+            gE = warp_sum(gE);
+            gL = warp_sum(gL);
+            if (lane == 0) {
+                a.gq_own[2 * (size_t)i] = gE;
+                a.gq_own[2 * (size_t)i + 1] = gL;
+            }
+        } else if (MIXED) {
+            const float wsh = sample ? (float)nshell / (float)p : 1.0f;
+            const float qi = __uint_as_float(si.w);
+            float ff[3] = {0.f, 0.f, 0.f};
+            auto pair_of = [&](int t, int& j, float& w) {
+                if (t < ncore_c) { j = core_buf[t]; w = 1.0f; }
+                else {
+                    const int k = t - ncore_c;
+                    const int ord = sample ? sel[k] : k;
+                    j = shell_buf[min(ord, a.shell_cap - 1)];
+                    w = wsh;
+                }
+            };
+            auto term = [&](const uint4 sj, const int2 tj, const float w) { mixed_term(si, qi, ti, sj, tj, w, ff); };
+            // two pairs per lane per iteration (t, t + 32: the order of the
+            // one-pair loop), their loads issued together
+            for (int t = lane; t < npairs; t += 64) {
+                const bool v2 = t + 32 < npairs;
+                int j1, j2;
+                float w1, w2;
+                pair_of(t, j1, w1);
+                if (v2) pair_of(t + 32, j2, w2);
+                else { j2 = j1; w2 = 0.f; }
+                const uint4 sj1 = a.s4[j1];
+                const int2 tj1 = a.tm[j1];
+                const uint4 sj2 = a.s4[j2];
+                const int2 tj2 = a.tm[j2];
+                term(sj1, tj1, w1);
+                if (v2) term(sj2, tj2, w2);
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) ff[q] = warp_sum(ff[q]);
+            if (lane == 0) {
+                float* Fr = reinterpret_cast<float*>(a.F_real);
+                Fr[3 * (size_t)i + 0] = ff[0];
+                Fr[3 * (size_t)i + 1] = ff[1];
+                Fr[3 * (size_t)i + 2] = ff[2];
+                facc_f[0] += ff[0]; facc_f[1] += ff[1]; facc_f[2] += ff[2];
+            }
+            flush_sums(1);
+        } else {
+            const double wsh = sample ? (double)nshell / (double)p : 1.0;
+            const double4_32a pi = a.p4[i];
+            double fi[3] = {0.0, 0.0, 0.0};
+            for (int t = lane; t < npairs; t += 32) {
+                int j;
+                double w;
+                if (t < ncore_c) { j = core_buf[t]; w = 1.0; }
+                else {
+                    const int k = t - ncore_c;
+                    const int ord = sample ? sel[k] : k;
+                    j = shell_buf[min(ord, a.shell_cap - 1)];
+                    w = wsh;
+                }
+                const double4_32a pj = a.p4[j];
+                const int2 tj = a.tm[j];
+                double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                dx -= c.L * rint(dx * c.invL);
+                dy -= c.L * rint(dy * c.invL);
+                dz -= c.L * rint(dz * c.invL);
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                const double rinv = rsqrt(r2);         // one reciprocal square root, no division
+                const double r = r2 * rinv;
+                const double qq = c.k_e * pi.w * pj.w;
+                const double ar = c.sqrt_alpha * r;
+                const double gauss = c.two_sqrt_alpha_over_sqrt_pi * exp(-ar * ar);
+                const bool ex = ti.y == tj.y;
+                // the exclusion term -erf is evaluated directly (not as
+                // erfc - 1) to keep its full FP64 relative accuracy
+                const double ec = ex ? -erf(ar) : erfc(ar);
+                const double ucoul = qq * ec * rinv;
+                double s = -qq * (ec * rinv + gauss) * rinv * rinv;
+                const int tt = ti.x * c.ntypes + tj.x;
+                const bool nolj = ex || !(r2 < s_rc2[tt]);
+                const double c12 = nolj ? 0.0 : s_c12[tt], c6 = nolj ? 0.0 : s_c6[tt];
+                const double ir2 = rinv * rinv;
+                const double ir6 = ir2 * ir2 * ir2;
+                s -= (12.0 * c12 * ir6 - 6.0 * c6) * ir6 * ir2;
+                const double ulj = (c12 * ir6 - c6) * ir6 - (nolj ? 0.0 : s_sh[tt]);
+                const double gx = w * s * dx, gy = w * s * dy, gz = w * s * dz;
+                fi[0] += gx; fi[1] += gy; fi[2] += gz;
+                acc_e[0] += ex ? 0.0 : w * ucoul;
+                acc_e[1] += w * ulj;
+                acc_e[2] += ex ? w * ucoul : 0.0;
+                acc_w[0] += dx * gx; acc_w[1] += dy * gy; acc_w[2] += dz * gz;
+                acc_w[3] += dx * gy; acc_w[4] += dx * gz; acc_w[5] += dy * gz;
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) fi[q] = warp_sum(fi[q]);
+            if (lane == 0) {
+                a.F_real[3 * (size_t)i + 0] = fi[0];
+                a.F_real[3 * (size_t)i + 1] = fi[1];
+                a.F_real[3 * (size_t)i + 2] = fi[2];
+                acc_f[0] += fi[0]; acc_f[1] += fi[1]; acc_f[2] += fi[2];
+            }
+        }
+
+        // ---- debug record (caller index order) ---------------------------
+        if (a.debug) {
+            if (lane == 0) { a.dbg_ncore[gi] = ncore; a.dbg_nshell[gi] = nshell; }
+            for (int t = lane; t < a.dbg_cap; t += 32)
+                a.dbg_core[(size_t)gi * a.dbg_cap + t] = t < ncore_c ? a.perm[core_buf[t]] : -1;
+            for (int k = lane; k < p; k += 32) {
+                int id = -1;
+                if (k < nb) {
+                    const int ord = sample ? sel[k] : k;
+                    id = a.perm[shell_buf[min(ord, a.shell_cap - 1)]];
+                }
+                a.dbg_batch[(size_t)gi * p + k] = id;
+            }
+        }
+        __syncwarp();
+    };
 
     for (long unit = slot; unit < nunits; unit += nslots) {
         const int ux = (int)(unit % units_per_row);
@@ -917,256 +1190,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     }
                 }
             }
-            if (__any_sync(FULL, overlap) && lane == 0) latch_status(a.status, RBE_ST_OVERLAP);
-            if ((ncore > a.core_cap || nshell > a.shell_cap) && lane == 0) {
-                latch_status(a.status, RBE_ST_CAPACITY);
-                atomicMax(a.status + RBE_STW_NEED_CORE, ncore);      // what a retry needs
-                atomicMax(a.status + RBE_STW_NEED_SHELL, nshell);
-            }
-            const int ncore_c = min(ncore, a.core_cap);
-            const int gi = a.perm[i];
-
-            // ---- 2. shell batch (Floyd over ordinals) -----------------------
-            const bool sample = nshell > p;
-            const int nb = sample ? p : nshell;
-            const uint64_t* wa = wa_in;
-            if (sample && c.shell_mode == 1) {
-                // with replacement: slot k is ordinal floor(u_k N_S / 2^64)
-                for (int k = lane; k < p; k += 32) sel[k] = (int)uniform_below(wa[k], (uint32_t)nshell);
-            } else if (sample) {
-                if (p <= 32) {
-                    // slot k on lane k; the insertions resolved in slot order
-                    const uint32_t jk = (uint32_t)(nshell - p + lane);
-                    const int tk = lane < p ? (int)uniform_below(wa[lane], jk + 1u) : -1 - lane;
-                    // if the p draws are distinct, no slot is replaced and every
-                    // slot keeps its draw (by induction over the slots);
-                    // otherwise resolve the slots in order
-                    const bool distinct = !__any_sync(FULL, (__match_any_sync(FULL, tk) & lt_mask) != 0u);
-                    int mysel = tk;
-                    if (!distinct) {
-                        mysel = -1;
-                        for (int k = 0; k < p; ++k) {
-                            const int t = __shfl_sync(FULL, tk, k);
-                            const bool dup = __any_sync(FULL, lane < k && mysel == t);
-                            if (lane == k) mysel = dup ? (int)jk : t;
-                        }
-                    }
-                    if (lane < p) sel[lane] = mysel;
-                } else {
-                    for (int k = 0; k < p; ++k) {
-                        const uint32_t jj = (uint32_t)(nshell - p + k);
-                        const int t = (int)uniform_below(wa[k], jj + 1u);
-                        bool dup = false;
-                        for (int l = lane; l < k; l += 32) dup |= (sel[l] == t);
-                        dup = __any_sync(FULL, dup);
-                        if (lane == 0) sel[k] = dup ? (int)jj : t;
-                        __syncwarp();
-                    }
-                }
-            }
-            __syncwarp();
-
-            // ---- 3. pair terms over C(i) and B(i) -----------------------------
-            // Eq. (2.10) with the Coulomb factor erfc (erfc - 1 = -erf for a
-            // same-molecule pair, the Ewald exclusion correction) and LJ.
-            const int npairs = ncore_c + nb;
-            const int2 ti = a.tm[i];
-            if constexpr (ADJ) {
-                // Gradients of E = 1/2 sum w_ij u_ij and of L = sum_i vt_i . F_real_i
-                // (vt = v - mean v, which carries the momentum correction of
-                // Eq. (2.13)) with respect to the charges and the LJ pair
-                // parameters; the part of a pair that belongs to q_j is added
-                // to atom j's slot atomically.
-                const double vtx = a.vs[3 * (size_t)i] - a.vbar[0];
-                const double vty = a.vs[3 * (size_t)i + 1] - a.vbar[1];
-                const double vtz = a.vs[3 * (size_t)i + 2] - a.vbar[2];
-                const double ke = c.k_e;
-                const double4_32a pi = a.p4[i];
-                double gE = 0.0, gL = 0.0;
-                for (int t = lane; t < npairs; t += 32) {
-                    int j;
-                    double w;
-                    if (t < ncore_c) { j = core_buf[t]; w = 1.0; }
-                    else {
-                        const int k = t - ncore_c;
-                        const int ord = sample ? sel[k] : k;
-                        j = shell_buf[min(ord, a.shell_cap - 1)];
-                        w = sample ? (double)nshell / (double)p : 1.0;
-                    }
-                    const int2 tj = a.tm[j];
-                    const bool ex = ti.y == tj.y;
-                    double dx, dy, dz, qj, phi, h, r2;
-                    if (MIXED) {
-                        const uint4 sj = a.s4[j];
-                        const float fdx = (float)(int)(sj.x - si.x) * c.Lfix;
-                        const float fdy = (float)(int)(sj.y - si.y) * c.Lfix;
-                        const float fdz = (float)(int)(sj.z - si.z) * c.Lfix;
-                        const float fr2 = fdx * fdx + fdy * fdy + fdz * fdz;
-                        const float rinv = rsqrtf(fr2);
-                        const float ar = (float)c.sqrt_alpha * fr2 * rinv;
-                        const float gauss = (float)c.two_sqrt_alpha_over_sqrt_pi * __expf(-ar * ar);
-                        const float ec = erfcf(ar) - (ex ? 1.0f : 0.0f);
-                        phi = (double)(ec * rinv);
-                        h = (double)(-(ec * rinv + gauss) * rinv * rinv);
-                        dx = fdx; dy = fdy; dz = fdz; r2 = fr2;
-                        qj = (double)__uint_as_float(sj.w);
-                    } else {
-                        const double4_32a pj = a.p4[j];
-                        dx = pj.x - pi.x; dy = pj.y - pi.y; dz = pj.z - pi.z;
-                        dx -= c.L * rint(dx * c.invL);
-                        dy -= c.L * rint(dy * c.invL);
-                        dz -= c.L * rint(dz * c.invL);
-                        r2 = dx * dx + dy * dy + dz * dz;
-                        const double rinv = rsqrt(r2);     // one reciprocal square root, no division
-                        const double rr = r2 * rinv;
-                        const double ar = c.sqrt_alpha * rr;
-                        const double gauss = c.two_sqrt_alpha_over_sqrt_pi * exp(-ar * ar);
-                        const double ec = ex ? -erf(ar) : erfc(ar);
-                        phi = ec * rinv;
-                        h = -(ec * rinv + gauss) * rinv * rinv;
-                        qj = pj.w;
-                    }
-                    const double qi = MIXED ? (double)__uint_as_float(si.w) : pi.w;
-                    const double vd = vtx * dx + vty * dy + vtz * dz;
-                    gE += 0.5 * w * ke * qj * phi;
-                    gL += w * ke * qj * h * vd;
-                    atomicAdd(&a.gq_tr[2 * (size_t)j], 0.5 * w * ke * qi * phi);
-                    atomicAdd(&a.gq_tr[2 * (size_t)j + 1], w * ke * qi * h * vd);
-                    const int tt = ti.x * c.ntypes + tj.x;
-                    if (!ex && r2 < s_rc2[tt]) {
-                        const double e = s_eps[tt], sg = s_sig[tt];
-                        if (e != 0.0) {
-                            const double ir2 = 1.0 / r2;
-                            const double sr2 = sg * sg * ir2, sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
-                            const double du_de = 4.0 * (sr12 - sr6) - s_dsde[tt];
-                            const double du_ds = 4.0 * e * (12.0 * sr12 - 6.0 * sr6) / sg - s_dsds[tt];
-                            const double dh_de = -(48.0 * sr12 - 24.0 * sr6) * ir2;
-                            const double dh_ds = -e * (576.0 * sr12 - 144.0 * sr6) * ir2 / sg;
-                            atomicAdd(&s_glj[0 * nt2 + tt], 0.5 * w * du_de);
-                            atomicAdd(&s_glj[1 * nt2 + tt], 0.5 * w * du_ds);
-                            atomicAdd(&s_glj[2 * nt2 + tt], w * dh_de * vd);
-                            atomicAdd(&s_glj[3 * nt2 + tt], w * dh_ds * vd);
-                        }
-                    }
-                }
-                gE = warp_sum(gE);
-                gL = warp_sum(gL);
-                if (lane == 0) {
-                    a.gq_own[2 * (size_t)i] = gE;
-                    a.gq_own[2 * (size_t)i + 1] = gL;
-                }
-            } else if (MIXED) {
-                const float wsh = sample ? (float)nshell / (float)p : 1.0f;
-                const float qi = __uint_as_float(si.w);
-                float ff[3] = {0.f, 0.f, 0.f};
-                auto pair_of = [&](int t, int& j, float& w) {
-                    if (t < ncore_c) { j = core_buf[t]; w = 1.0f; }
-                    else {
-                        const int k = t - ncore_c;
-                        const int ord = sample ? sel[k] : k;
-                        j = shell_buf[min(ord, a.shell_cap - 1)];
-                        w = wsh;
-                    }
-                };
-                auto term = [&](const uint4 sj, const int2 tj, const float w) { mixed_term(si, qi, ti, sj, tj, w, ff); };
-                // two pairs per lane per iteration (t, t + 32: the order of the
-                // one-pair loop), their loads issued together
-                for (int t = lane; t < npairs; t += 64) {
-                    const bool v2 = t + 32 < npairs;
-                    int j1, j2;
-                    float w1, w2;
-                    pair_of(t, j1, w1);
-                    if (v2) pair_of(t + 32, j2, w2);
-                    else { j2 = j1; w2 = 0.f; }
-                    const uint4 sj1 = a.s4[j1];
-                    const int2 tj1 = a.tm[j1];
-                    const uint4 sj2 = a.s4[j2];
-                    const int2 tj2 = a.tm[j2];
-                    term(sj1, tj1, w1);
-                    if (v2) term(sj2, tj2, w2);
-                }
-#pragma unroll
-                for (int q = 0; q < 3; ++q) ff[q] = warp_sum(ff[q]);
-                if (lane == 0) {
-                    float* Fr = reinterpret_cast<float*>(a.F_real);
-                    Fr[3 * (size_t)i + 0] = ff[0];
-                    Fr[3 * (size_t)i + 1] = ff[1];
-                    Fr[3 * (size_t)i + 2] = ff[2];
-                    facc_f[0] += ff[0]; facc_f[1] += ff[1]; facc_f[2] += ff[2];
-                }
-                flush_sums(1);
-            } else {
-                const double wsh = sample ? (double)nshell / (double)p : 1.0;
-                const double4_32a pi = a.p4[i];
-                double fi[3] = {0.0, 0.0, 0.0};
-                for (int t = lane; t < npairs; t += 32) {
-                    int j;
-                    double w;
-                    if (t < ncore_c) { j = core_buf[t]; w = 1.0; }
-                    else {
-                        const int k = t - ncore_c;
-                        const int ord = sample ? sel[k] : k;
-                        j = shell_buf[min(ord, a.shell_cap - 1)];
-                        w = wsh;
-                    }
-                    const double4_32a pj = a.p4[j];
-                    const int2 tj = a.tm[j];
-                    double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                    dx -= c.L * rint(dx * c.invL);
-                    dy -= c.L * rint(dy * c.invL);
-                    dz -= c.L * rint(dz * c.invL);
-                    const double r2 = dx * dx + dy * dy + dz * dz;
-                    const double rinv = rsqrt(r2);         // one reciprocal square root, no division
-                    const double r = r2 * rinv;
-                    const double qq = c.k_e * pi.w * pj.w;
-                    const double ar = c.sqrt_alpha * r;
-                    const double gauss = c.two_sqrt_alpha_over_sqrt_pi * exp(-ar * ar);
-                    const bool ex = ti.y == tj.y;
-                    // the exclusion term -erf is evaluated directly (not as
-                    // erfc - 1) to keep its full FP64 relative accuracy
-                    const double ec = ex ? -erf(ar) : erfc(ar);
-                    const double ucoul = qq * ec * rinv;
-                    double s = -qq * (ec * rinv + gauss) * rinv * rinv;
-                    const int tt = ti.x * c.ntypes + tj.x;
-                    const bool nolj = ex || !(r2 < s_rc2[tt]);
-                    const double c12 = nolj ? 0.0 : s_c12[tt], c6 = nolj ? 0.0 : s_c6[tt];
-                    const double ir2 = rinv * rinv;
-                    const double ir6 = ir2 * ir2 * ir2;
-                    s -= (12.0 * c12 * ir6 - 6.0 * c6) * ir6 * ir2;
-                    const double ulj = (c12 * ir6 - c6) * ir6 - (nolj ? 0.0 : s_sh[tt]);
-                    const double gx = w * s * dx, gy = w * s * dy, gz = w * s * dz;
-                    fi[0] += gx; fi[1] += gy; fi[2] += gz;
-                    acc_e[0] += ex ? 0.0 : w * ucoul;
-                    acc_e[1] += w * ulj;
-                    acc_e[2] += ex ? w * ucoul : 0.0;
-                    acc_w[0] += dx * gx; acc_w[1] += dy * gy; acc_w[2] += dz * gz;
-                    acc_w[3] += dx * gy; acc_w[4] += dx * gz; acc_w[5] += dy * gz;
-                }
-#pragma unroll
-                for (int q = 0; q < 3; ++q) fi[q] = warp_sum(fi[q]);
-                if (lane == 0) {
-                    a.F_real[3 * (size_t)i + 0] = fi[0];
-                    a.F_real[3 * (size_t)i + 1] = fi[1];
-                    a.F_real[3 * (size_t)i + 2] = fi[2];
-                    acc_f[0] += fi[0]; acc_f[1] += fi[1]; acc_f[2] += fi[2];
-                }
-            }
-
-            // ---- debug record (caller index order) ---------------------------
-            if (a.debug) {
-                if (lane == 0) { a.dbg_ncore[gi] = ncore; a.dbg_nshell[gi] = nshell; }
-                for (int t = lane; t < a.dbg_cap; t += 32)
-                    a.dbg_core[(size_t)gi * a.dbg_cap + t] = t < ncore_c ? a.perm[core_buf[t]] : -1;
-                for (int k = lane; k < p; k += 32) {
-                    int id = -1;
-                    if (k < nb) {
-                        const int ord = sample ? sel[k] : k;
-                        id = a.perm[shell_buf[min(ord, a.shell_cap - 1)]];
-                    }
-                    a.dbg_batch[(size_t)gi * p + k] = id;
-                }
-            }
-            __syncwarp();
+            finish_atom(i, si, ncore, nshell, overlap, wa_in);
         };
         if (PAIRS && pair_path && staged) {
             // Atoms A = i and B = i + 1 of the unit per warp pass.  Their

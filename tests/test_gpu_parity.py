@@ -220,3 +220,29 @@ def test_lists_exact_at_the_radii(precision):
         assert (out["lists"]["n_shell"] == ol["n_shell"]).all()
         assert (out["lists"]["core"] == ol["core"]).all()
         assert (out["lists"]["batch"] == ol["batch"]).all()
+
+
+def test_mixed_pair_energy_within_erfc_error_bound():
+    """The mixed pair kernel evaluates erfc by Hastings' approximation
+    (Abramowitz & Stegun 7.1.26, absolute error below 1.5e-7).  One +1/-1
+    pair per system at 64 distances from 0.3 to r_s: the mixed real-space
+    Coulomb energy must equal k_e q_i q_j erfc(sqrt(alpha) r)/r (math.erfc)
+    within k_e |q_i q_j| / r times that bound plus FP32 rounding."""
+    import math
+
+    import torch
+    s0 = systems.electrolyte(n=2, L=20.0, seed=1)
+    worst = 0.0
+    for r in np.linspace(0.3, s0.r_s * 0.999, 64):
+        s = systems.electrolyte(n=2, L=20.0, seed=1)
+        s.pos = np.array([[3.0, 4.0, 5.0], [3.0 + r * 0.6, 4.0 + r * 0.8, 5.0]])
+        s.q = np.array([1.0, -1.0])
+        s.type = np.zeros(2, np.int32)
+        out = gpu_forces(s, 1, precision=rbe.MIXED)
+        assert out["status"] == 0
+        exact = s.k_e * s.q[0] * s.q[1] * math.erfc(math.sqrt(s.alpha) * r) / r
+        bound = s.k_e / r * 1.5e-7 + 4e-7 * abs(exact) + 1e-12
+        err = abs(out["E"][rbe.E_REAL] - exact)
+        worst = max(worst, err / bound)
+        assert err <= bound, (r, err, bound)
+    print(f"mixed pair energy: worst error / bound {worst:.3f}")
