@@ -212,7 +212,8 @@ int rbe_get_kspace(rbe_ctx* ctx, int32_t* m, double* rho, void* cuda_stream);
  * launch whose candidates (more than 2048) were classified range by range
  * instead of as one concatenated list (both counted with rbe_set_debug on;
  * -1 otherwise), out[9] the step whose force evaluation stopped the last
- * rbe_step (-1 if it ran to the end). */
+ * rbe_step (-1 if it ran to the end), out[10] the stored-list rebuilds of the
+ * Verlet skin so far, out[11] the entries per stored list. */
 int rbe_get_info(rbe_ctx* ctx, double* out, int nout);
 
 /* Kernel timing: when on, every launch is bracketed by CUDA events on its
@@ -233,7 +234,8 @@ int rbe_get_info(rbe_ctx* ctx, double* out, int nout);
 #define RBE_K_KFORCE   11
 #define RBE_K_VV       12
 #define RBE_K_MISC     13
-#define RBE_NKERNELS   14
+#define RBE_K_SKIN     14   /* stored-list build and rebuild test of the Verlet skin */
+#define RBE_NKERNELS   15
 int rbe_set_profiling(rbe_ctx* ctx, int on);
 int rbe_get_profile(rbe_ctx* ctx, double* ms, int64_t* launches, int reset, void* cuda_stream);
 
@@ -325,6 +327,26 @@ int rbe_set_langevin(rbe_ctx* ctx, double kT, double tau);
  * restart), so that resuming at that step is exact. */
 int rbe_get_langevin_force(rbe_ctx* ctx, int n, double* FL, uint64_t* step);
 int rbe_set_langevin_force(rbe_ctx* ctx, int n, const double* FL, uint64_t step);
+
+/* Verlet skin (Sec. 2.3 remarks that a cell edge slightly above r_eta spares
+ * rebuilding the lists every step; the scheme is this library's): with
+ * skin > 0 the context keeps, per atom, a stored list V(i) of every atom
+ * within r_s + skin at the positions of the last rebuild, in the canonical
+ * order of that step (ascending cell, fixed-point x, atom index).  Each force
+ * evaluation classifies V(i) by the exact rule at the current positions, so
+ * C(i) and S(i) are those of the stencil walk; the shell ordinals of the
+ * batch follow the order of V(i).  The atoms keep the sorted order of the
+ * rebuild between rebuilds.  A rebuild happens on the first call, when n or
+ * the skin changes, and when some atom has moved more than skin/2 (fixed-
+ * point units, minimum image) since the last one: then every pair within r_s
+ * was within r_s + skin at the rebuild.  That test runs on the device and the
+ * call waits for its answer.  The results therefore depend on the rebuild
+ * history, not only on (positions, step).  Requires r_s + skin <= L/2.
+ * skin = 0 (default) rebuilds every step by the stencil walk.  Not available
+ * in batches or with rbe_adjoint (RBE_EINVAL).  Calling it again with the
+ * same skin makes the next call rebuild.  rbe_get_info reports the rebuilds
+ * (out[10]) and the stored-list capacity (out[11]). */
+int rbe_set_verlet_skin(rbe_ctx* ctx, double skin);
 
 /* Work decomposition of the RBL pair kernel (Sec. 2.3 stencil walk): a work
  * unit is a run of cells along x holding about atoms_per_unit atoms (0: 64;

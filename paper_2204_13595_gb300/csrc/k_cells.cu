@@ -321,6 +321,82 @@ __global__ void __launch_bounds__(TPB) k_gather(int n, const int* __restrict__ p
     gather_body(blockIdx.x, n, perm, pos, q, type, mol, c, s4, f4, p4, tm, status);
 }
 
+// ---- Verlet-skin variant: steps between rebuilds -------------------------
+// Between rebuilds the sorted order of the last rebuild is kept: every atom
+// is wrapped, quantised and written to its slot inv_perm[i] of that order
+// (the arrays of gather_body), no counting sort.  The same block sums of q^2,
+// q, |q| as quantize_count_body (same grid and loop, so the same rounding).
+// An atom whose fixed-point displacement since the rebuild codes sb exceeds
+// D2 (skin/2 squared, fixed-point units) sets *moved: a rebuild is due.
+__global__ void __launch_bounds__(TPB) k_skin_gather(int n, const double* __restrict__ pos,
+                                                     const double* __restrict__ q, const int32_t* __restrict__ type,
+                                                     const int32_t* __restrict__ mol, RbeConsts c,
+                                                     const int* __restrict__ inv_perm, const uint4* __restrict__ sb,
+                                                     uint64_t D2, uint4* __restrict__ s4, float4* __restrict__ f4,
+                                                     double4_32a* __restrict__ p4, int2* __restrict__ tm,
+                                                     double* __restrict__ part_q, int* __restrict__ status,
+                                                     int* __restrict__ moved)
+{
+    double sq2 = 0.0, sq = 0.0, sabs = 0.0;
+    bool far = false;
+    for (int b0 = blockIdx.x * TPB; b0 < n; b0 += gridDim.x * TPB) {
+        const int i = b0 + threadIdx.x;
+        if (i >= n) continue;
+        double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        const double qi = q[i];
+        const bool bad_pos = !isfinite(x) || !isfinite(y) || !isfinite(z);
+        if (bad_pos || !isfinite(qi)) latch_status(status, RBE_ST_NONFINITE);
+        if (bad_pos) nonfinite_stand_in(i, n, c.L, x, y, z);
+        double xw, yw, zw;
+        uint32_t sx, sy, sz;
+        wrap_fixed(x, c.invL, c.L, xw, sx);
+        wrap_fixed(y, c.invL, c.L, yw, sy);
+        wrap_fixed(z, c.invL, c.L, zw, sz);
+        const int k = inv_perm[i];
+        const uint4 b = sb[k];
+        const int dx = (int)(sx - b.x), dy = (int)(sy - b.y), dz = (int)(sz - b.z);
+        const unsigned long long d2 = (unsigned long long)((long long)dx * dx) +
+                                      (unsigned long long)((long long)dy * dy) +
+                                      (unsigned long long)((long long)dz * dz);
+        far |= d2 > D2;
+        const float qf = (float)qi;
+        s4[k] = make_uint4(sx, sy, sz, __float_as_uint(qf));
+        f4[k] = make_float4((float)xw, (float)yw, (float)zw, qf);
+        p4[k] = make_double4_32a(xw, yw, zw, qi);
+        int t = type ? type[i] : 0;
+        if (t < 0 || t >= c.ntypes) {
+            latch_status(status, RBE_ST_BADTYPE);
+            t = 0;
+        }
+        tm[k] = make_int2(t, mol ? mol[i] : -(i + 1));
+        sq2 += qi * qi;
+        sq += qi;
+        sabs += fabs(qi);
+    }
+    if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) *moved = 1;
+    __shared__ double red[3][TPB / 32];
+    sq2 = warp_sum(sq2); sq = warp_sum(sq); sabs = warp_sum(sabs);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { red[0][w] = sq2; red[1][w] = sq; red[2][w] = sabs; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double acc = 0.0;
+        for (int kk = 0; kk < TPB / 32; ++kk) acc += red[threadIdx.x][kk];
+        part_q[blockIdx.x * RBE_NPART_Q + threadIdx.x] = acc;
+    }
+}
+
+// At a rebuild: the inverse of the new sorted order and the fixed-point codes
+// the displacements of later steps are measured from.
+__global__ void __launch_bounds__(TPB) k_skin_mark(int n, const int* __restrict__ perm, const uint4* __restrict__ s4,
+                                                   int* __restrict__ inv_perm, uint4* __restrict__ sb)
+{
+    const int k = blockIdx.x * TPB + threadIdx.x;
+    if (k >= n) return;
+    inv_perm[perm[k]] = k;
+    sb[k] = s4[k];
+}
+
 // ---- batched forms: one launch over all replicas of a plan -----------------
 // Block grids per replica: BK_CELLS = ceil((ncells + 1) / TPB), BK_ATOMS =
 // ceil(n / TPB), BK_Q = grid_q, BK_REP = 1.
@@ -372,6 +448,23 @@ __global__ void __launch_bounds__(TPB) k_gather_b(const RepDev* __restrict__ R, 
 }
 
 }  // namespace
+
+void launch_skin_gather(rbe_ctx* ctx, int n, const double* pos, const double* q, const int32_t* type,
+                        const int32_t* mol, cudaStream_t st)
+{
+    prof_begin(ctx, RBE_K_SKIN, st);
+    k_skin_gather<<<ctx->grid_q, TPB, 0, st>>>(n, pos, q, type, mol, ctx->c, ctx->inv_perm, ctx->sb, ctx->skin_D2,
+                                               ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->part_q, ctx->status,
+                                               ctx->skin_moved);
+    prof_end(ctx, RBE_K_SKIN, st);
+}
+
+void launch_skin_mark(rbe_ctx* ctx, int n, cudaStream_t st)
+{
+    prof_begin(ctx, RBE_K_SKIN, st);
+    k_skin_mark<<<(n + TPB - 1) / TPB, TPB, 0, st>>>(n, ctx->perm, ctx->s4, ctx->inv_perm, ctx->sb);
+    prof_end(ctx, RBE_K_SKIN, st);
+}
 
 void launch_quantize_count(rbe_ctx* ctx, int n, const double* pos, const double* q, cudaStream_t st)
 {

@@ -73,7 +73,20 @@ struct RblArgs {
     int* __restrict__ dbg_core;
     int* __restrict__ dbg_batch;
     int* __restrict__ dbg_unstaged;
+    // Verlet skin (stored lists): V(i) of sorted atom i at vlist[i * vcap ..],
+    // its length at vcnt[i]
+    int* __restrict__ vlist;
+    int* __restrict__ vcnt;
+    int vcap;
 };
+
+// Modes of the pair kernel: the stencil walk of every step; the stencil walk
+// at r_s + skin that writes the stored lists V(i) of the Verlet-skin variant
+// (no batches, no pair terms); the classification of the stored lists at
+// the current positions followed by the batches and pair terms.
+constexpr int RBL_STENCIL = 0;
+constexpr int RBL_BUILD = 1;
+constexpr int RBL_STORED = 2;
 
 // Per-row description of the staged region of the current unit (64 bytes).
 struct __align__(16) RowInfo {
@@ -105,7 +118,7 @@ static_assert(RBL_PAIR_CARVE == RBE_RBL_PAIR_CARVE, "carve of the two-atom path"
 // bitmap of range starts [RBL_MAX_PACKED / 32] words, the Philox words
 // [ga][p_pad], the core and shell lists and the batch ordinals.
 struct SmemLayout {
-    size_t rows, cellpos, lj, warps, wbytes, total;
+    size_t rows, cellpos, cellabs, lj, warps, wbytes, total;
     int ga;                // atoms whose Philox words are made in one warp pass
 };
 
@@ -121,6 +134,8 @@ __host__ __device__ inline SmemLayout smem_layout(const RblGeom& g, int nt2, int
     L.rows = o;
     o = up16(o + sizeof(RowInfo) * (size_t)g.nrows);
     L.cellpos = o;
+    o = up16(o + sizeof(int) * (size_t)g.nrows * (size_t)(g.cells_per_row + 1));
+    L.cellabs = o;
     o = up16(o + sizeof(int) * (size_t)g.nrows * (size_t)(g.cells_per_row + 1));
     L.lj = o;
     o = up16(o + sizeof(double) * 12 * (size_t)nt2);
@@ -539,7 +554,38 @@ __device__ __forceinline__ void classify_pair(const float4* __restrict__ stage, 
     }
 }
 
-template <bool MIXED, bool SMALL, bool ADJ>
+// Classification of atom i's stored list V(i) (Verlet-skin variant) at the
+// current positions: the exact rule on the fixed-point codes (minimum image
+// by the 32-bit wrap), members appended in the order of V(i) to the core and
+// shell buffers.  Two chunks of 32 entries per iteration; V(i) never holds i.
+__device__ __forceinline__ void classify_stored(const RblArgs& a, int i, uint4 si, int lane, unsigned lt_mask,
+                                                int* core_buf, int* shell_buf, int& ncore, int& nshell, bool& overlap)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int nv = min(a.vcnt[i], a.vcap);
+    const int* __restrict__ V = a.vlist + (size_t)i * a.vcap;
+    for (int t0 = 0; t0 < nv; t0 += 64) {
+        const int ta = t0 + lane, tb = ta + 32;
+        const bool va = ta < nv, vb = tb < nv;
+        const int ja = va ? V[ta] : i, jb = vb ? V[tb] : i;
+        const unsigned long long da = d2_exact(si, a.s4[ja]), db = d2_exact(si, a.s4[jb]);
+        const bool ca = va && da <= a.c.Rc2, cb = vb && db <= a.c.Rc2;
+        const bool sa = va && da > a.c.Rc2 && da <= a.c.Rs2, sb = vb && db > a.c.Rc2 && db <= a.c.Rs2;
+        overlap |= (va && da == 0ull) || (vb && db == 0ull);
+        const unsigned cma = __ballot_sync(FULL, ca), cmb = __ballot_sync(FULL, cb);
+        const unsigned sma = __ballot_sync(FULL, sa), smb = __ballot_sync(FULL, sb);
+        const int cpa = ncore + __popc(cma & lt_mask), cpb = ncore + __popc(cma) + __popc(cmb & lt_mask);
+        const int spa = nshell + __popc(sma & lt_mask), spb = nshell + __popc(sma) + __popc(smb & lt_mask);
+        if (ca && cpa < a.core_cap) core_buf[cpa] = ja;
+        if (cb && cpb < a.core_cap) core_buf[cpb] = jb;
+        if (sa && spa < a.shell_cap) shell_buf[spa] = ja;
+        if (sb && spb < a.shell_cap) shell_buf[spb] = jb;
+        ncore += __popc(cma) + __popc(cmb);
+        nshell += __popc(sma) + __popc(smb);
+    }
+}
+
+template <bool MIXED, bool SMALL, bool ADJ, int LMODE = RBL_STENCIL>
 __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -560,6 +606,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     float4* stage = reinterpret_cast<float4*>(smem);                              // [cap_stage]
     RowInfo* rows = reinterpret_cast<RowInfo*>(smem + lay.rows);                   // [nrows]
     int* cellpos = reinterpret_cast<int*>(smem + lay.cellpos);                     // [nrows * cpr]
+    int* cellabs = reinterpret_cast<int*>(smem + lay.cellabs);                     // [nrows * cpr]
     const int cpr = g.cells_per_row + 1;
     double* s_c12 = reinterpret_cast<double*>(smem + lay.lj);
     double* s_c6 = s_c12 + nt2;
@@ -677,7 +724,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     // stencil rows, staged units): the per-warp buffers are carved for A's and
     // B's core lists, the shell ballot words and their prefix counts, and the
     // materialised batches (see pair_two below)
-    constexpr bool PAIRS = MIXED && !SMALL && !ADJ;
+    constexpr bool PAIRS = MIXED && !SMALL && !ADJ && LMODE == RBL_STENCIL;
     const bool pair_path = PAIRS && nrows <= 32 && lay.ga >= 2 && p <= 32 &&
                            a.shell_cap >= a.core_cap + RBL_PAIR_CARVE;
 
@@ -939,7 +986,35 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
         __syncwarp();
     };
 
-    for (long unit = slot; unit < nunits; unit += nslots) {
+    if constexpr (LMODE == RBL_STORED) {
+        // atoms in sorted order, one per warp at a time, over the whole grid
+        const int stride = nslots * WARPS;
+        int kloc = 0;
+        for (int i = slot * WARPS + wib; i < a.n; i += stride, ++kloc) {
+            const int aslot = kloc % lay.ga;
+            if (aslot == 0) {
+                __syncwarp();
+                for (int t = lane; t < lay.ga * nbk; t += 32) {
+                    const int aa = t / nbk, b = t - aa * nbk;
+                    const int ii = i + stride * aa;
+                    if (ii < a.n) {
+                        uint64_t w[4];
+                        philox4x64_10((uint64_t)a.perm[ii], (uint64_t)b, a.step, 1ull, c.seed, 0ull, w);
+#pragma unroll
+                        for (int qd = 0; qd < 4; ++qd) words[aa * p_pad + 4 * b + qd] = w[qd];
+                    }
+                }
+                __syncwarp();
+            }
+            const uint4 si = a.s4[i];
+            int ncore = 0, nshell = 0;
+            bool overlap = false;
+            classify_stored(a, i, si, lane, lt_mask, core_buf, shell_buf, ncore, nshell, overlap);
+            __syncwarp();
+            finish_atom(i, si, ncore, nshell, overlap, words + (size_t)aslot * p_pad);
+        }
+    }
+    for (long unit = LMODE == RBL_STORED ? nunits : slot; unit < nunits; unit += nslots) {
         const int ux = (int)(unit % units_per_row);
         const int uy = (int)((unit / units_per_row) % nc);
         const int uz = (int)(unit / ((long)units_per_row * nc));
@@ -963,7 +1038,9 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
             const int zc = wrapc(zu, nc), yc = wrapc(yu, nc);
             const int rb = nc * (yc + nc * zc);
             const int w = wrapc(ul + k, nc);
-            cellpos[r * cpr + k] = a.cell_start[rb + w + 1] - a.cell_start[rb + w];
+            const int c0 = a.cell_start[rb + w];
+            cellpos[r * cpr + k] = a.cell_start[rb + w + 1] - c0;
+            cellabs[r * cpr + k] = c0;           // global start of the cell, for (d) and (e)
             if (k == 0) {
                 RowInfo ri;
                 ri.zc = zc;
@@ -1022,10 +1099,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
             const int* cp = cellpos + r * cpr;
             const int ufirst = pc == 0 ? ul : (pc == 1 ? max(ul, 0) : max(ul, nc));
             int off = 0;
-            if (staged && ufirst <= uh && (pc != 0 || ufirst < 0) && (pc != 1 || ufirst < nc)) {
-                const int rb = nc * (ri.yc + nc * ri.zc);
-                off = a.cell_start[rb + wrapc(ufirst, nc)] - (ri.sbase + cp[ufirst - ul]);
-            }
+            if (staged && ufirst <= uh && (pc != 0 || ufirst < 0) && (pc != 1 || ufirst < nc))
+                off = cellabs[r * cpr + (ufirst - ul)] - (ri.sbase + cp[ufirst - ul]);
             rows[r].goff[pc] = off;
         }
         // (e) stage the FP32 positions row by row, each piece moved to the
@@ -1034,16 +1109,15 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
         // is compared with atom i's own position
         if (staged) {
             for (int r = wib; r < nrows; r += WARPS) {
-                const int zc = rows[r].zc, yc = rows[r].yc, sb = rows[r].sbase;
+                const int sb = rows[r].sbase;
                 const float shy = rows[r].shy, shz = rows[r].shz;
-                const int rb = nc * (yc + nc * zc);
                 const int* cp = cellpos + r * cpr;
                 for (int pc = 0; pc < 3; ++pc) {
                     const int u0 = pc == 0 ? ul : (pc == 1 ? max(ul, 0) : max(ul, nc));
                     const int u1 = pc == 0 ? min(uh, -1) : (pc == 1 ? min(uh, nc - 1) : uh);
                     if (u0 > u1) continue;
                     const float shx = pc == 0 ? -Lf : (pc == 2 ? Lf : 0.f);
-                    const int gs = a.cell_start[rb + wrapc(u0, nc)];
+                    const int gs = cellabs[r * cpr + (u0 - ul)];
                     const int len = cp[u1 - ul + 1] - cp[u0 - ul];
                     const int ss = sb + cp[u0 - ul];
                     for (int k = lane; k < len; k += 32) {
@@ -1190,7 +1264,21 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     }
                 }
             }
-            finish_atom(i, si, ncore, nshell, overlap, wa_in);
+            if constexpr (LMODE == RBL_BUILD) {
+                // the stored list V(i): every member within r_s + skin (the
+                // "core" of this launch's radii), canonical order
+                if (__any_sync(FULL, overlap) && lane == 0) latch_status(a.status, RBE_ST_OVERLAP);
+                if (ncore > a.vcap && lane == 0) {
+                    latch_status(a.status, RBE_ST_CAPACITY);
+                    atomicMax(a.status + RBE_STW_NEED_LIST, ncore);
+                }
+                const int nv = min(ncore, a.vcap);
+                for (int t = lane; t < nv; t += 32) a.vlist[(size_t)i * a.vcap + t] = core_buf[t];
+                if (lane == 0) a.vcnt[i] = nv;
+                __syncwarp();
+            } else {
+                finish_atom(i, si, ncore, nshell, overlap, wa_in);
+            }
         };
         if (PAIRS && pair_path && staged) {
             // Atoms A = i and B = i + 1 of the unit per warp pass.  Their
@@ -1393,21 +1481,40 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                 // member of ordinal t of the shell: chunk c with pfx[c] <= t <
                 // pfx[c + 1] (binary search), the (t - pfx[c])-th set bit of
                 // its ballot word, then the range holding that position
-                auto member = [&](int t, const int* pfx, int which) -> int {
-                    int lo = 0, hi = nch;
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (pfx[mid] <= t) lo = mid;
-                        else hi = mid;
-                    }
-                    const int bit = nth_set_bit(smask[2 * lo + which], t - pfx[lo]);
-                    const int v = 32 * lo + bit;
-                    const unsigned upto = bit == 31 ? 0xffffffffu : ((2u << bit) - 1u);
-                    return v + ranges[pfxR[lo] + __popc(rstart[lo] & upto) - 1].y;
-                };
+                // (A's and B's searches interleaved: two independent chains)
                 const int nbA = sampA ? p : nsA, nbB = sampB ? p : nsB;
-                if (lane < nbA) jA[lane] = member(sampA ? selA[lane] : lane, pfxA, 0);
-                if (lane < nbB) jB[lane] = member(sampB ? selB[lane] : lane, pfxB, 1);
+                if (lane < nbA || lane < nbB) {
+                    const bool doA = lane < nbA, doB = lane < nbB;
+                    const int tA = doA ? (sampA ? selA[lane] : lane) : 0;
+                    const int tB = doB ? (sampB ? selB[lane] : lane) : 0;
+                    // (the two intervals can differ in length by one after
+                    // the same number of halvings: each search stops on its own)
+                    int loA = 0, hiA = nch, loB = 0, hiB = nch;
+                    while (hiA - loA > 1 || hiB - loB > 1) {
+                        const int mA = (loA + hiA) >> 1, mB = (loB + hiB) >> 1;
+                        const int pa = pfxA[mA], pb = pfxB[mB];
+                        if (hiA - loA > 1) {
+                            if (pa <= tA) loA = mA;
+                            else hiA = mA;
+                        }
+                        if (hiB - loB > 1) {
+                            if (pb <= tB) loB = mB;
+                            else hiB = mB;
+                        }
+                    }
+                    const int bitA = nth_set_bit(smask[2 * loA], tA - pfxA[loA]);
+                    const int bitB = nth_set_bit(smask[2 * loB + 1], tB - pfxB[loB]);
+                    const unsigned uptoA = bitA == 31 ? 0xffffffffu : ((2u << bitA) - 1u);
+                    const unsigned uptoB = bitB == 31 ? 0xffffffffu : ((2u << bitB) - 1u);
+                    // (a lane without an ordinal for A or B searched for ordinal
+                    // 0 there; its index is clamped and its result unused)
+                    const int rA = max(pfxR[loA] + __popc(rstart[loA] & uptoA) - 1, 0);
+                    const int rB = max(pfxR[loB] + __popc(rstart[loB] & uptoB) - 1, 0);
+                    const int jA_ = 32 * loA + bitA + ranges[rA].y;
+                    const int jB_ = 32 * loB + bitB + ranges[rB].y;
+                    if (doA) jA[lane] = jA_;
+                    if (doB) jB[lane] = jB_;
+                }
                 __syncwarp();
 
                 // ---- 4. pair terms of A and B on the lanes of the warp ---------
@@ -1511,6 +1618,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     }
 
     // ---- deterministic block partials ---------------------------------------
+    if constexpr (LMODE == RBL_BUILD) return;        // no pair terms in the list build
     if (MIXED) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) acc_e[q] += (double)facc_e[q];
@@ -1541,6 +1649,21 @@ template <bool MIXED, bool SMALL, bool ADJ>
 __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
 {
     rbl_body<MIXED, SMALL, ADJ>(a, blockIdx.x, gridDim.x);
+}
+
+// Verlet-skin variant: the stored lists from the stencil walk at r_s + skin
+// (a.c and a.g hold that radius and its geometry), and the per-step kernel
+// over the stored lists.
+template <bool SMALL>
+__global__ void __launch_bounds__(WARPS * 32, 2) k_rbl_build(RblArgs a)
+{
+    rbl_body<false, SMALL, false, RBL_BUILD>(a, blockIdx.x, gridDim.x);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(WARPS * 32, 2) k_rbl_stored(RblArgs a)
+{
+    rbl_body<MIXED, false, false, RBL_STORED>(a, blockIdx.x, gridDim.x);
 }
 
 // Pair kernel over many systems.  PERSIST: a grid of resident blocks, each
@@ -1670,6 +1793,66 @@ void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st, bool adjoin
     } else {
         if (mixed) { if (small) launch_t<true, true, false>(ctx, a, smem, st); else launch_t<true, false, false>(ctx, a, smem, st); }
         else { if (small) launch_t<false, true, false>(ctx, a, smem, st); else launch_t<false, false, false>(ctx, a, smem, st); }
+    }
+    prof_end(ctx, RBE_K_RBL, st);
+}
+
+int rbl_build_smem_bytes(const rbe_ctx* ctx)
+{
+    return (int)smem_layout(ctx->skin_g, ctx->c.ntypes * ctx->c.ntypes, ctx->c.p, ctx->skin_vcap, 32).total;
+}
+
+long rbl_build_units(const rbe_ctx* ctx)
+{
+    const int nc = ctx->c.n_cell, G = ctx->skin_g.G;
+    return (long)nc * nc * ((nc + G - 1) / G);
+}
+
+// Stored lists V(i) of the Verlet-skin variant from the sorted arrays of the
+// rebuild step: the stencil walk with both radii set to r_s + skin.
+void launch_rbl_build(rbe_ctx* ctx, int n, cudaStream_t st)
+{
+    RblArgs a;
+    rbl_fill_args(ctx, n, &a);
+    a.c = ctx->skin_c;
+    a.g = ctx->skin_g;
+    a.core_cap = ctx->skin_vcap;
+    a.shell_cap = 32;
+    a.vlist = ctx->vlist; a.vcnt = ctx->vcnt; a.vcap = ctx->skin_vcap;
+    a.debug = 0;
+    a.nslots = ctx->skin_grid_build;
+    const int smem = rbl_build_smem_bytes(ctx);
+    prof_begin(ctx, RBE_K_SKIN, st);
+    if (ctx->skin_g.small) {
+        cudaFuncSetAttribute(k_rbl_build<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_rbl_build<true><<<ctx->skin_grid_build, WARPS * 32, smem, st>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_rbl_build<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_rbl_build<false><<<ctx->skin_grid_build, WARPS * 32, smem, st>>>(a);
+    }
+    prof_end(ctx, RBE_K_SKIN, st);
+}
+
+// Lists, batches and pair terms of one step from the stored lists (same
+// grid and block partials as the stencil launch, so finalisation is shared).
+void launch_rbl_stored(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st)
+{
+    RblArgs a;
+    rbl_fill_args(ctx, n, &a);
+    a.step = step;
+    RblGeom g = ctx->rbl;
+    g.G = 1; g.nrows = 0; g.cap_stage = 0; g.cells_per_row = 0; g.small = 0;
+    a.g = g;
+    a.vlist = ctx->vlist; a.vcnt = ctx->vcnt; a.vcap = ctx->skin_vcap;
+    const int smem = (int)smem_layout(g, ctx->c.ntypes * ctx->c.ntypes, ctx->c.p, ctx->core_cap, ctx->shell_cap).total;
+    if (a.debug) cudaMemsetAsync(ctx->dbg_unstaged, 0, 2 * sizeof(int), st);
+    prof_begin(ctx, RBE_K_RBL, st);
+    if (ctx->precision == RBE_MIXED) {
+        cudaFuncSetAttribute(k_rbl_stored<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_rbl_stored<true><<<ctx->grid_rbl, WARPS * 32, smem, st>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_rbl_stored<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_rbl_stored<false><<<ctx->grid_rbl, WARPS * 32, smem, st>>>(a);
     }
     prof_end(ctx, RBE_K_RBL, st);
 }

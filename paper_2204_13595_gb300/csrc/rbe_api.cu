@@ -129,9 +129,12 @@ void free_dev(rbe_ctx* ctx)
                     ctx->rho_part, ctx->rho, ctx->totals, ctx->status, ctx->lj, ctx->dbg_ncore, ctx->dbg_nshell,
                     ctx->dbg_core, ctx->dbg_batch, ctx->dbg_unstaged, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
                     ctx->ke_part, ctx->vs, ctx->gq_own, ctx->gq_tr, ctx->part_lj, ctx->part_v, ctx->tau_part,
-                    ctx->tau};
+                    ctx->tau, ctx->vlist, ctx->vcnt, ctx->sb, ctx->inv_perm, ctx->skin_moved};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    ctx->vlist = nullptr; ctx->vcnt = nullptr; ctx->sb = nullptr; ctx->inv_perm = nullptr; ctx->skin_moved = nullptr;
+    for (int k = 0; k < 5; ++k) ctx->skin_cap[k] = 0;
+    ctx->skin_valid = 0;
     ctx->s4 = nullptr; ctx->f4 = nullptr; ctx->p4 = nullptr; ctx->tm = nullptr; ctx->perm = nullptr; ctx->cell_of = nullptr;
     ctx->slot = nullptr; ctx->cell_count = nullptr; ctx->cell_start = nullptr; ctx->F_real = nullptr;
     ctx->F_bond = nullptr; ctx->part_rbl = nullptr; ctx->part_q = nullptr; ctx->part_bond = nullptr;
@@ -188,10 +191,13 @@ void auto_caps(rbe_ctx* ctx, int n)
 // so each displacement component is off by at most da = 3 L 2^-23 + r 2^-24
 // and r^2 by at most 2 sqrt(3) r da + 3 da^2 + 3 r^2 2^-23; the bands are four
 // times that bound wide, and inside them the exact integer test decides.
-void rbl_geometry(rbe_ctx* ctx, int n)
+// Work units of one form of the pair kernel (g, with the stencil reach of c)
+// for n atoms: G cells per unit, staging capacity, bands of the FP32
+// prefilter around the squared radii rc and rs; smem_of gives the form's
+// shared memory for the current g.
+void unit_geometry(rbe_ctx* ctx, int n, const RbeConsts& c, double rc, double rs, RblGeom& g,
+                   int (*smem_of)(const rbe_ctx*))
 {
-    RblGeom& g = ctx->rbl;
-    const RbeConsts& c = ctx->c;
     const int nc = c.n_cell, R = c.reach;
     g.small = (2 * R + 1 >= nc) ? 1 : 0;
     double apc = (double)n / ((double)nc * nc * nc);
@@ -213,20 +219,53 @@ void rbl_geometry(rbe_ctx* ctx, int n)
         cap = (cap + 63) / 64 * 64;
         const int maxcap = (96 * 1024) / 16;
         g.cap_stage = cap < maxcap ? cap : maxcap;
-        if (G == 1 || rbl_smem_bytes(ctx) <= target) break;
+        if (G == 1 || smem_of(ctx) <= target) break;
     }
     auto bound = [&](double r) {
         double da = 3.0 * c.L * 1.1920928955078125e-07 + r * 5.9604644775390625e-08;
         return 4.0 * (2.0 * sqrt(3.0) * r * da + 3.0 * da * da + 3.0 * r * r * 1.1920928955078125e-07);
     };
-    double rc2 = c.r_c * c.r_c, rs2 = c.r_s * c.r_s;
+    double rc2 = rc * rc, rs2 = rs * rs;
     // thresholds rounded outward: the FP32 value of a band's lower edge is
     // at most, and of its upper edge at least, the exact edge
-    g.rc2_lo = nextafterf((float)(rc2 - bound(c.r_c)), 0.0f);
-    g.rc2_hi = nextafterf((float)(rc2 + bound(c.r_c)), 3.0e38f);
-    g.rs2_lo = nextafterf((float)(rs2 - bound(c.r_s)), 0.0f);
-    g.rs2_hi = nextafterf((float)(rs2 + bound(c.r_s)), 3.0e38f);
-    g.tiny2 = nextafterf((float)(1e-6 * rc2 + bound(0.0)), 3.0e38f);
+    g.rc2_lo = nextafterf((float)(rc2 - bound(rc)), 0.0f);
+    g.rc2_hi = nextafterf((float)(rc2 + bound(rc)), 3.0e38f);
+    g.rs2_lo = nextafterf((float)(rs2 - bound(rs)), 0.0f);
+    g.rs2_hi = nextafterf((float)(rs2 + bound(rs)), 3.0e38f);
+    g.tiny2 = nextafterf((float)(1e-6 * c.r_c * c.r_c + bound(0.0)), 3.0e38f);
+}
+
+void rbl_geometry(rbe_ctx* ctx, int n)
+{
+    unit_geometry(ctx, n, ctx->c, ctx->c.r_c, ctx->c.r_s, ctx->rbl, rbl_smem_bytes);
+}
+
+// Verlet skin: constants, geometry and capacity of the list build (both
+// radii r_v = r_s + skin: every member of the stored list counts as "core"),
+// and the rebuild threshold floor((skin/2 2^32/L)^2).
+void skin_geometry(rbe_ctx* ctx, int n)
+{
+    const double rv = ctx->c.r_s + ctx->skin;
+    RbeConsts& b = ctx->skin_c;
+    b = ctx->c;
+    b.r_s = rv;
+    b.Rc2 = b.Rs2 = radius2_fixed(rv, ctx->c.L);
+    b.reach = (int)floor(rv * (double)ctx->c.n_cell / ctx->c.L) + 1;
+    b.rs_frac2 = (float)((rv / ctx->c.L) * (rv / ctx->c.L) * (1.0 + 1e-5));
+    ctx->skin_D2 = radius2_fixed(0.5 * ctx->skin, ctx->c.L);
+    const double rho = (double)n / (ctx->c.L * ctx->c.L * ctx->c.L);
+    const double mv = 4.0 / 3.0 * PI * rv * rv * rv * rho;
+    ctx->skin_vcap = round32(1.25 * mv + 8.0 * sqrt(mv) + 64.0);
+    if (ctx->skin_vcap < ctx->skin_vcap_min) ctx->skin_vcap = (ctx->skin_vcap_min + 31) / 32 * 32;
+    unit_geometry(ctx, n, b, rv, rv, ctx->skin_g, rbl_build_smem_bytes);
+    // no shell in the build: the shell band is the core band's upper edge
+    ctx->skin_g.rs2_lo = ctx->skin_g.rs2_hi = ctx->skin_g.rc2_hi;
+    const long units = rbl_build_units(ctx);
+    long gb = (units + 2) / 3;
+    const long wave = 2L * ctx->n_sm;
+    if (gb < wave) gb = wave;
+    if (gb > units) gb = units;
+    ctx->skin_grid_build = (int)(gb < 1 ? 1 : gb);
 }
 
 // Reallocates *p only when `count` exceeds the recorded capacity *cap.
@@ -265,7 +304,7 @@ int ensure(rbe_ctx* ctx, int n)
         if ((rc = dev_alloc(ctx, &ctx->totals, 32 + 7 * (size_t)ctx->c.P))) return rc;
         if ((rc = dev_alloc(ctx, &ctx->status, RBE_STW_WORDS))) return rc;
         {
-            const int init[RBE_STW_WORDS] = {0, 0, 0, -1};
+            const int init[RBE_STW_WORDS] = {0, 0, 0, -1, 0};
             CUDA_TRY(ctx, cudaMemcpy(ctx->status, init, sizeof(init), cudaMemcpyHostToDevice));
         }
         CUDA_TRY(ctx, cudaMemset(ctx->totals, 0, sizeof(double) * (32 + 7 * (size_t)ctx->c.P)));
@@ -352,8 +391,21 @@ int ensure(rbe_ctx* ctx, int n)
         ctx->grid_rbl = (int)(g < 1 ? 1 : g);
         int gr = (n + 255) / 256;
         ctx->grid_rho = gr < 2 * nsm ? gr : 2 * nsm;
+        if (ctx->skin > 0.0) {
+            skin_geometry(ctx, n);
+            if (rbl_build_smem_bytes(ctx) > 220 * 1024)
+                return set_err(ctx, RBE_ECAPACITY, "stored-list capacity %d exceeds shared memory", ctx->skin_vcap);
+            ctx->skin_valid = 0;
+        }
         ctx->last_n = n;
         ctx->last_precision = ctx->precision;
+    }
+    if (ctx->skin > 0.0) {
+        if ((rc = grow(ctx, &ctx->vlist, &ctx->skin_cap[0], (size_t)n * ctx->skin_vcap))) return rc;
+        if ((rc = grow(ctx, &ctx->vcnt, &ctx->skin_cap[1], n))) return rc;
+        if ((rc = grow(ctx, &ctx->sb, &ctx->skin_cap[2], n))) return rc;
+        if ((rc = grow(ctx, &ctx->inv_perm, &ctx->skin_cap[3], n))) return rc;
+        if ((rc = grow(ctx, &ctx->skin_moved, &ctx->skin_cap[4], 1))) return rc;
     }
     int gb = ctx->n_wmol > 0 ? (ctx->n_wmol + 255) / 256 : 0;
     ctx->grid_bond = gb < 4 * ctx->n_sm ? gb : 4 * ctx->n_sm;
@@ -418,16 +470,54 @@ int ctx_grow_lang(rbe_ctx* ctx, int n)
 
 namespace {
 
+// Verlet skin (reading R15): between rebuilds the atoms keep the sorted
+// order of the last rebuild and the pair kernel classifies each atom's stored
+// list V(i); a rebuild (counting sort, then the stencil walk at r_s + skin
+// writing V) happens on the first call, after n or the skin changed, and
+// when some atom has moved more than skin/2 since the last rebuild -- a test
+// on the device whose answer the host reads (one wait per call).
+int skin_prepare(rbe_ctx* ctx, int n, const double* pos, const double* q, const int32_t* type, const int32_t* mol,
+                 cudaStream_t st)
+{
+    bool rebuild = !ctx->skin_valid || ctx->skin_n != n;
+    if (!rebuild) {
+        int moved = 0;
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->skin_moved, 0, sizeof(int), st));
+        launch_skin_gather(ctx, n, pos, q, type, mol, st);
+        CUDA_TRY(ctx, cudaMemcpyAsync(&moved, ctx->skin_moved, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        rebuild = moved != 0;
+    }
+    if (rebuild) {
+        launch_quantize_count(ctx, n, pos, q, st);
+        launch_scan(ctx, st);
+        launch_scatter_sort_gather(ctx, n, pos, q, type, mol, st);
+        launch_skin_mark(ctx, n, st);
+        launch_rbl_build(ctx, n, st);
+        ctx->skin_valid = 1;
+        ctx->skin_n = n;
+        ctx->skin_rebuilds++;
+    }
+    return RBE_OK;
+}
+
 int forces_device(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const double* q, const int32_t* type,
                   const int32_t* mol, double* F, cudaStream_t st)
 {
     ctx->last_launches = 0;
-    launch_quantize_count(ctx, n, pos, q, st);
-    launch_scan(ctx, st);
-    launch_scatter_sort_gather(ctx, n, pos, q, type, mol, st);
+    const bool skin = ctx->skin > 0.0;
+    if (skin) {
+        int rc = skin_prepare(ctx, n, pos, q, type, mol, st);
+        if (rc) return rc;
+    } else {
+        launch_quantize_count(ctx, n, pos, q, st);
+        launch_scan(ctx, st);
+        launch_scatter_sort_gather(ctx, n, pos, q, type, mol, st);
+    }
     launch_ksample(ctx, step, st);
     launch_rho(ctx, n, st);
-    launch_rbl(ctx, n, step, st);
+    if (skin) launch_rbl_stored(ctx, n, step, st);
+    else launch_rbl(ctx, n, step, st);
     if (ctx->n_wmol > 0) launch_bonded(ctx, n, pos, st);
     launch_finalize(ctx, n, st);
     launch_kforce(ctx, n, F, st);
@@ -463,7 +553,7 @@ int status_code(int bits)
 // (bits and needed capacities to 0, halt code to -1).
 int read_status(rbe_ctx* ctx, cudaStream_t st, int w[RBE_STW_WORDS])
 {
-    const int init[RBE_STW_WORDS] = {0, 0, 0, -1};
+    const int init[RBE_STW_WORDS] = {0, 0, 0, -1, 0};
     CUDA_TRY(ctx, cudaStreamSynchronize(st));
     CUDA_TRY(ctx, cudaMemcpy(w, ctx->status, sizeof(int) * RBE_STW_WORDS, cudaMemcpyDeviceToHost));
     CUDA_TRY(ctx, cudaMemcpy(ctx->status, init, sizeof(init), cudaMemcpyHostToDevice));
@@ -481,6 +571,7 @@ void grow_caps(rbe_ctx* ctx, const int w[RBE_STW_WORDS])
     cc = (cc + 31) / 32 * 32;
     if (sc < cc + RBE_RBL_PAIR_CARVE) sc = cc + RBE_RBL_PAIR_CARVE;     // room for the two-atom path
     ctx->user_core_cap = cc;
+    if (w[RBE_STW_NEED_LIST] > 0) ctx->skin_vcap_min = w[RBE_STW_NEED_LIST] + 64;
     ctx->user_shell_cap = (sc + 31) / 32 * 32;
     ctx->last_n = -1;           // recompute caps, geometry and grids
 }
@@ -491,7 +582,8 @@ void grow_caps(rbe_ctx* ctx, const int w[RBE_STW_WORDS])
 // profiling helpers
 // ---------------------------------------------------------------------------
 const char* const KERNEL_NAMES[RBE_NKERNELS] = {"quantize", "scan", "scatter", "sort", "gather", "ksample", "rho",
-                                                "rhosum", "rbl", "bonded", "finalize", "kforce", "vv", "misc"};
+                                                "rhosum", "rbl", "bonded", "finalize", "kforce", "vv", "misc",
+                                                "skin"};
 
 // With profiling on, every launch is bracketed by CUDA events (timing) and an
 // NVTX range named after the kernel (for timeline tools).
@@ -670,6 +762,20 @@ int rbe_set_langevin_force(rbe_ctx* ctx, int n, const double* FL, uint64_t step)
     return RBE_OK;
 }
 
+int rbe_set_verlet_skin(rbe_ctx* ctx, double skin)
+{
+    if (!ctx) return RBE_EINVAL;
+    if (!(skin >= 0.0) || (skin > 0.0 && ctx->c.r_s + skin > 0.5 * ctx->c.L))
+        return set_err(ctx, RBE_EINVAL, "skin must be >= 0 with r_s + skin <= L/2");
+    ctx->skin_valid = 0;        // the next call rebuilds
+    if (skin != ctx->skin) {
+        ctx->skin = skin;
+        ctx->skin_vcap_min = 0;
+        ctx->last_n = -1;       // recompute the geometry (and the list build's) at the next call
+    }
+    return RBE_OK;
+}
+
 int rbe_set_rbl_tiling(rbe_ctx* ctx, int atoms_per_unit, int units_per_slot)
 {
     if (!ctx || atoms_per_unit < 0 || units_per_slot < 0 || atoms_per_unit > 4096) return RBE_EINVAL;
@@ -839,6 +945,8 @@ int rbe_adjoint(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const dou
                 double* dLdeps, double* dLdsig, void* cuda_stream)
 {
     if (!ctx) return RBE_EINVAL;
+    if (ctx->skin > 0.0)
+        return set_err(ctx, RBE_EINVAL, "rbe_adjoint differentiates the stencil lists: turn the Verlet skin off");
     if (n < 1 || !pos || !q) return set_err(ctx, RBE_EINVAL, "n >= 1 and pos, q are required");
     if (!is_device_ptr(pos) || !is_device_ptr(q) || (type && !is_device_ptr(type)) || (mol && !is_device_ptr(mol)) ||
         (gF && !is_device_ptr(gF)) || (dEdq && !is_device_ptr(dEdq)) || (dLdq && !is_device_ptr(dLdq)))
@@ -951,10 +1059,10 @@ int rbe_get_info(rbe_ctx* ctx, double* out, int nout)
     int dbg[2] = {-1, -1};
     if (nout > 7 && ctx->debug && ctx->dbg_unstaged)
         CUDA_TRY(ctx, cudaMemcpy(dbg, ctx->dbg_unstaged, sizeof(dbg), cudaMemcpyDeviceToHost));
-    double v[10] = {(double)ctx->c.n_cell, (double)ctx->c.reach, (double)ctx->c.M, ctx->c.S, (double)ctx->core_cap,
+    double v[12] = {(double)ctx->c.n_cell, (double)ctx->c.reach, (double)ctx->c.M, ctx->c.S, (double)ctx->core_cap,
                     (double)ctx->shell_cap, (double)ctx->last_launches, (double)dbg[0], (double)dbg[1],
-                    (double)ctx->halt_step};
-    for (int k = 0; k < nout && k < 10; ++k) out[k] = v[k];
+                    (double)ctx->halt_step, (double)ctx->skin_rebuilds, (double)ctx->skin_vcap};
+    for (int k = 0; k < nout && k < 12; ++k) out[k] = v[k];
     return RBE_OK;
 }
 

@@ -138,6 +138,7 @@ int build_plan(rbe_batch* b)
         rbe_ctx* ctx = b->ctx[r];
         if (ctx->precision != prec) return berr(b, RBE_EINVAL, "replica %d: all replicas need one precision mode", r);
         if (ctx->debug) return berr(b, RBE_EINVAL, "replica %d: debug recording must be off in a batch", r);
+        if (ctx->skin > 0.0) return berr(b, RBE_EINVAL, "replica %d: the Verlet skin is not batched", r);
         int rc = ctx_prepare(ctx, b->n[r]);
         if (rc) return berr(b, rc, "replica %d: %s", r, ctx->err);
     }

@@ -28,11 +28,12 @@
 // their capacity (what a retry needs); word 3 the first velocity-Verlet
 // launch of rbe_step that found a latched error and stopped (2k for the
 // first half kick and drift of step k, 2k + 1 for its second half kick; -1:
-// none)
+// none); word 4 the largest stored list (Verlet skin) that overflowed
 #define RBE_STW_NEED_CORE  1
 #define RBE_STW_NEED_SHELL 2
 #define RBE_STW_HALT       3
-#define RBE_STW_WORDS      4
+#define RBE_STW_NEED_LIST  4
+#define RBE_STW_WORDS      5
 
 // status bits latched on the device
 #define RBE_ST_OVERLAP   1
@@ -170,6 +171,22 @@ struct rbe_ctx {
     int tune_apu;        // target atoms per RBL work unit (0: 48)
     int tune_ups;        // RBL units per slot (0: about 3, at least one wave of resident blocks)
     RblGeom rbl;
+    // Verlet skin (stored lists; skin <= 0: off)
+    double skin;
+    RbeConsts skin_c;     // constants of the list build: both radii r_s + skin, its stencil reach
+    RblGeom skin_g;       // work-unit geometry of the list build
+    int skin_vcap;        // entries per stored list
+    int skin_vcap_min;    // lower bound after an overflow
+    int skin_grid_build;  // slots of the list build
+    int skin_valid, skin_n;
+    long long skin_rebuilds;
+    uint64_t skin_D2;     // floor((skin/2 2^32/L)^2): the rebuild threshold
+    int* vlist;           // [n * skin_vcap] stored lists (sorted indices of the rebuild)
+    int* vcnt;            // [n]
+    uint4* sb;            // [n] fixed-point codes at the rebuild, sorted order
+    int* inv_perm;        // [n] caller index -> sorted index of the rebuild
+    int* skin_moved;      // [1] set when an atom moved more than skin/2 since the rebuild
+    size_t skin_cap[5];
     size_t cap_atoms[24];
     size_t cap_adj[8];
 };
@@ -382,3 +399,11 @@ void rbl_fill_args(const rbe_ctx* ctx, int n, void* out);
 int rbl_max_blocks_per_sm(int precision, int smem);
 long rbl_units(const rbe_ctx* ctx);
 int rbl_blocks_per_sm(const rbe_ctx* ctx);
+// Verlet-skin variant (stored lists)
+void launch_skin_gather(rbe_ctx* ctx, int n, const double* pos, const double* q, const int32_t* type,
+                        const int32_t* mol, cudaStream_t st);
+void launch_skin_mark(rbe_ctx* ctx, int n, cudaStream_t st);
+void launch_rbl_build(rbe_ctx* ctx, int n, cudaStream_t st);
+void launch_rbl_stored(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st);
+int rbl_build_smem_bytes(const rbe_ctx* ctx);
+long rbl_build_units(const rbe_ctx* ctx);

@@ -20,14 +20,14 @@ FP64, MIXED = 0, 1
 NE, NW = 6, 6
 E_REAL, E_KSPACE, E_SELF, E_LJ, E_EXCL, E_BOND = range(6)
 KERNELS = ["quantize", "scan", "scatter", "sort", "gather", "ksample", "rho", "rhosum", "rbl", "bonded",
-           "finalize", "kforce", "vv", "misc"]
+           "finalize", "kforce", "vv", "misc", "skin"]
 EXPORTS = ["rbe_create", "rbe_set_coulomb", "rbe_set_lj", "rbe_set_precision", "rbe_set_water_bonds",
            "rbe_set_capacity", "rbe_forces", "rbe_step", "rbe_sync_status", "rbe_set_debug", "rbe_get_lists",
            "rbe_get_kspace", "rbe_get_info", "rbe_set_profiling", "rbe_get_profile", "rbe_last_error",
            "rbe_destroy", "rbe_rho_noalloc", "rbe_adjoint", "rbe_set_rbl_tiling", "rbe_batch_create",
            "rbe_batch_bind", "rbe_batch_forces", "rbe_batch_step", "rbe_batch_autotune", "rbe_batch_info",
            "rbe_batch_sync_status", "rbe_batch_last_error", "rbe_batch_destroy", "rbe_set_shell_sampling",
-           "rbe_set_lj_cutoff", "rbe_set_kpool", "rbe_set_langevin", "rbe_get_langevin_force",
+           "rbe_set_lj_cutoff", "rbe_set_kpool", "rbe_set_langevin", "rbe_get_langevin_force", "rbe_set_verlet_skin",
            "rbe_set_langevin_force"]
 SHELL_FLOYD, SHELL_REPLACE = 0, 1
 WCA_FACTOR = 2.0 ** (1.0 / 6.0)
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH):
     L.rbe_set_lj_cutoff.argtypes = [vp, d]
     L.rbe_set_kpool.argtypes = [vp, i, i]
     L.rbe_set_langevin.argtypes = [vp, d, d]
+    L.rbe_set_verlet_skin.argtypes = [vp, d]
     L.rbe_get_langevin_force.argtypes = [vp, i, vp, ctypes.POINTER(u64)]
     L.rbe_set_langevin_force.argtypes = [vp, i, vp, u64]
     L.rbe_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
@@ -218,6 +219,11 @@ class Context:
         FL = np.ascontiguousarray(FL, dtype=np.float64)
         self._check(self.L.rbe_set_langevin_force(self.h, int(FL.shape[0]), _ptr(FL), int(step)))
 
+    def set_verlet_skin(self, skin):
+        """rbe_set_verlet_skin: stored lists within r_s + skin, rebuilt when an
+        atom has moved more than skin/2 (0: lists every step)."""
+        self._check(self.L.rbe_set_verlet_skin(self.h, float(skin)))
+
     def set_rbl_tiling(self, atoms_per_unit=0, units_per_slot=0):
         self._check(self.L.rbe_set_rbl_tiling(self.h, int(atoms_per_unit), int(units_per_slot)))
 
@@ -278,7 +284,7 @@ class Context:
 
     def info(self):
         keys = ["n_cell", "reach", "M", "S", "core_cap", "shell_cap", "launches", "unstaged_units", "walked_passes",
-                "halt_step"]
+                "halt_step", "skin_rebuilds", "skin_vcap"]
         out = (ctypes.c_double * len(keys))()
         self._check(self.L.rbe_get_info(self.h, out, len(keys)))
         return {k: out[i] for i, k in enumerate(keys)}

@@ -165,6 +165,23 @@ def electrolyte(n: int = 2000, L: float = 20.0, seed: int = 1, r_c: float = 2.5,
                   K_E_REDUCED, (1.0,), (1.0,), 1.0, dt, seed)
 
 
+def electrolyte_2to1(n_cations: int = 1280, L: float = 80.0, seed: int = 1, r_c: float = 5.0, r_s: float = 15.0,
+                     p: int = 10, P: int = 100, dt: float = 0.002) -> System:
+    """2:1 primitive electrolyte (Sec. 3.1): n_cations divalent cations (+2)
+    and 2 n_cations monovalent anions (-1), equal soft spheres (sigma = eps =
+    1), random sequential insertion at minimum distance 1 sigma; the charges
+    repeat +2, -1, -1 along the atom index."""
+    n = 3 * n_cations
+    rng = np.random.default_rng(seed)
+    pos = _rsa(rng, n, L, 1.0)
+    q = np.where(np.arange(n) % 3 == 0, 2.0, -1.0)
+    typ = np.zeros(n, dtype=np.int32)
+    mass = np.ones(n)
+    vel = _maxwell(rng, mass, 1.0, 1.0)
+    return System("electrolyte_2to1", L, pos, q, typ, None, mass, vel, alpha_for(r_s), r_c, r_s, p, P,
+                  K_E_REDUCED, (1.0,), (1.0,), 1.0, dt, seed)
+
+
 def slab_ions(n: int = 8000, L: float = 32.0, slab_frac: float = 0.5, slab_width: float = 3.0, seed: int = 11,
               r_c: float = 2.5, r_s: float = 5.0, p: int = 10, P: int = 100) -> System:
     """A strongly inhomogeneous charged system (an edge case, not a paper

@@ -59,6 +59,22 @@ def cond_err(F, ref):
     return float(np.max(np.abs(F - ref["F"]) / ref["F_abs"]))
 
 
+def literal_stats(F, ref):
+    """How the FP64 forces fare against a plain per-component relative bar:
+    quantiles (50, 90, 99, 99.9 %, max) of |F - F_ref| / |F_ref| and of the
+    condition number A / |F_ref| (A: the sum of |summands|), and the fraction
+    of components within 1e-11 relative."""
+    d = np.abs(F - ref["F"]).ravel()
+    f = np.abs(ref["F"]).ravel()
+    a = ref["F_abs"].ravel()
+    rel = d / np.maximum(f, 1e-300)
+    cond = a / np.maximum(f, 1e-300)
+    qs = (50, 90, 99, 99.9, 100)
+    return {"rel_q": [float(np.percentile(rel, q)) for q in qs],
+            "cond_q": [float(np.percentile(cond, q)) for q in qs],
+            "frac_within_1e-11": float(np.mean(rel <= 1e-11))}
+
+
 def ek_scale(s, ref, P=None):
     """Condition scale of E_k = sum_l c_l/2 |rho_l|^2 under perturbations of
     rho_l bounded by the sum of |q_j|: sum_l c_l |rho_l| sum_j |q_j|."""
@@ -73,8 +89,8 @@ def rms_rel(a, ref):
     return float(np.sqrt(np.mean((a - ref) ** 2)) / np.sqrt(np.mean(ref ** 2)))
 
 
-__all__ = ["params", "to_dev", "gpu_forces", "rel_err_components", "rms_rel", "cond_err", "ek_scale", "systems",
-           "oracle", "rbe"]
+__all__ = ["params", "to_dev", "gpu_forces", "rel_err_components", "rms_rel", "cond_err", "ek_scale", "literal_stats",
+           "systems", "oracle", "rbe"]
 
 
 def type_grads(g_eps, g_sig, eps, sigma):

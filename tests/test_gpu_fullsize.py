@@ -3,7 +3,7 @@ configuration bench.py times, against the oracle run in full on the host cores."
 import numpy as np
 import pytest
 
-from gpu_util import cond_err, ek_scale, gpu_forces, oracle, params, rbe, rms_rel, systems
+from gpu_util import cond_err, ek_scale, gpu_forces, literal_stats, oracle, params, rbe, rms_rel, systems
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +25,11 @@ def test_full_size_water(n_mol, seed):
     ef = cond_err(f64["F"], ref)
     erel = np.abs(f64["E"] - ref["E"])[:5] / np.abs(ref["E"][:5])
     ek = abs(f64["E"][1] - ref["E"][1]) / ek_scale(s, ref)
-    print(f"water {s.n}: FP64 force cond err {ef:.3e}; energy rel err {erel}; E_k cond err {ek:.3e}")
+    print(f"water {s.n}: FP64 force cond err {ef:.3e}; energy rel err {erel}; E_k cond err {ek:.3e}; "
+          f"E_k plain rel err {abs(f64['E'][1] - ref['E'][1]) / abs(ref['E'][1]):.3e}")
+    st = literal_stats(f64["F"], ref)
+    print(f"water {s.n}: plain |dF|/|F| quantiles 50/90/99/99.9/max {st['rel_q']}; A/|F| quantiles "
+          f"{st['cond_q']}; fraction within 1e-11 {st['frac_within_1e-11']:.6f}")
     assert ef < 1e-11
     for k in (0, 2, 3, 4):
         assert erel[k] < 1e-12, k

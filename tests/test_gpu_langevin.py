@@ -108,6 +108,12 @@ def _paper_electrolyte(seed=21):
     return systems.electrolyte(n=5120, L=80.0, seed=seed, r_c=5.0, r_s=15.0, p=10, P=100, dt=0.002)
 
 
+def _paper_electrolyte_2to1(seed=22):
+    """Sec. 3.1's 2:1 system: 1,280 divalent cations and 2,560 monovalent
+    anions, L = 80 sigma."""
+    return systems.electrolyte_2to1(n_cations=1280, L=80.0, seed=seed, r_c=5.0, r_s=15.0, p=10, P=100, dt=0.002)
+
+
 def _langevin_run(s, p, P, nsteps, nequil, seed, kT=1.0, tau=1.0, every=100):
     """Potential energy per atom and the kinetic temperature 2 KE / (3 N),
     sampled every `every` steps after `nequil` steps."""
@@ -153,6 +159,30 @@ def test_energy_per_atom_irbe_against_large_batches():
     mi, si = _mean_se(e_irbe)
     mr, sr = _mean_se(e_ref)
     print(f"\nU/N IRBE {mi:.5f} +- {si:.5f} (std {e_irbe.std():.5f}); "
+          f"large batches {mr:.5f} +- {sr:.5f} (std {e_ref.std():.5f})")
+    assert abs(mi - mr) < 4 * math.hypot(si, sr) + 1e-3 * abs(mr)
+    assert mi < 0 and mr < 0
+
+
+def test_equipartition_paper_electrolyte_2to1():
+    """The same relaxation of the kinetic temperature for the 2:1 system."""
+    s = _paper_electrolyte_2to1()
+    _, t_kin = _langevin_run(s, 10, 100, nsteps=6000, nequil=4000, seed=4, every=20)
+    m, se = _mean_se(t_kin)
+    assert abs(m - 1.0) < max(4 * se, 0.01), (m, se)
+
+
+@pytest.mark.slow
+def test_energy_per_atom_2to1_irbe_against_large_batches():
+    """Table 1's 2:1 row: mean potential energy per atom under Langevin
+    dynamics with the IRBE batches (10, 100) against batches large enough to
+    be nearly exact (every shell atom, 2,000 k vectors)."""
+    s = _paper_electrolyte_2to1()
+    e_irbe, _ = _langevin_run(s, 10, 100, nsteps=60000, nequil=20000, seed=7)
+    e_ref, _ = _langevin_run(s, 512, 2000, nsteps=60000, nequil=20000, seed=8)
+    mi, si = _mean_se(e_irbe)
+    mr, sr = _mean_se(e_ref)
+    print(f"\n2:1 U/N IRBE {mi:.5f} +- {si:.5f} (std {e_irbe.std():.5f}); "
           f"large batches {mr:.5f} +- {sr:.5f} (std {e_ref.std():.5f})")
     assert abs(mi - mr) < 4 * math.hypot(si, sr) + 1e-3 * abs(mr)
     assert mi < 0 and mr < 0

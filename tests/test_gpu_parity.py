@@ -12,7 +12,7 @@ the mixed path's force RMS error against the FP64 path at most 1e-4 relative.
 import numpy as np
 import pytest
 
-from gpu_util import cond_err, ek_scale, gpu_forces, oracle, params, rbe, rms_rel, systems, to_dev
+from gpu_util import cond_err, ek_scale, gpu_forces, literal_stats, oracle, params, rbe, rms_rel, systems, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -76,7 +76,11 @@ def test_fp64_forces_energy_virial(case):
     ef = cond_err(out["F"], ref)
     erel = np.abs(out["E"] - ref["E"])[:5] / np.maximum(np.abs(ref["E"][:5]), 1e-300)
     ek = abs(out["E"][1] - ref["E"][1]) / ek_scale(s, ref)
-    print(f"{name}: FP64 force cond err {ef:.3e}; energy rel err {erel}; E_k cond err {ek:.3e}")
+    print(f"{name}: FP64 force cond err {ef:.3e}; energy rel err {erel}; E_k cond err {ek:.3e}; "
+          f"E_k plain rel err {abs(out['E'][1] - ref['E'][1]) / abs(ref['E'][1]):.3e}")
+    st = literal_stats(out["F"], ref)
+    print(f"{name}: plain |dF|/|F| quantiles 50/90/99/99.9/max {st['rel_q']}; A/|F| quantiles {st['cond_q']}; "
+          f"fraction within 1e-11 {st['frac_within_1e-11']:.6f}")
     assert ef < F_TOL
     for k in (0, 2, 3, 4):
         assert erel[k] < E_TOL, k

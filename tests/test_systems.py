@@ -36,3 +36,15 @@ def test_slab_ions_fraction_and_extent():
     assert s.eps == (0.0,) and s.mol is None
     u = systems.slab_ions(n=1000, L=10.0, slab_frac=0.0, seed=1)
     assert abs(u.pos[:, 2].mean() - 5.0) < 0.5
+
+
+def test_electrolyte_2to1_is_neutral_and_spaced():
+    from paper_2204_13595_gb300 import systems
+    s = systems.electrolyte_2to1(n_cations=60, L=12.0, seed=3)
+    assert s.n == 180 and abs(s.q.sum()) == 0.0
+    assert (s.q == 2.0).sum() == 60 and (s.q == -1.0).sum() == 120
+    d = s.pos[:, None, :] - s.pos[None, :, :]
+    d -= s.L * np.round(d / s.L)
+    r = np.sqrt((d * d).sum(-1)) + np.eye(s.n) * 1e9
+    assert r.min() >= 1.0
+    assert systems.electrolyte_2to1(n_cations=60, L=12.0, seed=3).pos.tobytes() == s.pos.tobytes()
