@@ -491,17 +491,27 @@ def _next_rows_leg(flush, big):
             raise RuntimeError("device status error in the variants leg")
         var[name] = {"force_evals_per_s": 1e3 / ms, "ms_per_step": ms}
         c.close()
-    # Verlet skin: velocity-Verlet steps (bonded water, NVE, 1 fs) of the same
-    # box, rebuilds included, against the same steps with lists every step
-    skin = {"workload": "the headline's 1.2M-atom water box, mixed, NVE velocity Verlet at 1 fs with bonds, "
-                        "after 5 warm-up steps; stored lists rebuilt when an atom moved more than skin/2"}
+    # Verlet skin (row f3): the cost of a force evaluation from valid stored
+    # lists (static positions), of one that rebuilds them, and of
+    # velocity-Verlet steps (bonded water, NVE, 1 fs, rebuilds as they come),
+    # each against the same with lists every step
+    skin = {"workload": "the headline's 1.2M-atom water box, mixed; MD: NVE velocity Verlet at 1 fs with bonds after "
+                        "5 warm-up steps, stored lists rebuilt when an atom moved more than skin/2"}
     nmd = 40
     for sk in (0.0, 1.0, 2.0):
         c = rbe.Context.for_system(s, precision=rbe.MIXED)
         if sk > 0:
             c.set_verlet_skin(sk)
+        for k in range(3):
+            c.forces(k, bpos, bq, btyp, bmol, F)
+        static_ms = events(lambda k: c.forces(3 + k, bpos, bq, btyp, bmol, F), 5)
+        row = {"static_force_ms": static_ms}
+        if sk > 0:
+            def rebuild(k):
+                c.set_verlet_skin(sk)            # the next call rebuilds
+                c.forces(20 + k, bpos, bq, btyp, bmol, F)
+            row["rebuild_force_ms"] = events(rebuild, 3)
         d = dict(pos=bpos.clone(), vel=dev(s.vel), mass=dev(s.mass))
-        F = torch.empty_like(bpos)
         c.forces(0, d["pos"], bq, btyp, bmol, F)
         c.step(0, 5, s.dt, s.accel, d["pos"], d["vel"], d["mass"], bq, btyp, bmol, F)
         r0 = c.info()["skin_rebuilds"]
@@ -510,10 +520,16 @@ def _next_rows_leg(flush, big):
         if c.sync_status() != 0:
             raise RuntimeError("device status error in the Verlet-skin leg")
         info = c.info()
-        skin[f"skin_{sk:g}A"] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "ns_per_day": 0.0864 * 1e3 / ms * s.dt,
-                                 "rebuilds": int(info["skin_rebuilds"] - r0), "steps": nmd,
-                                 "stored_list_entries": int(info["skin_vcap"]) if sk > 0 else 0}
+        row.update({"md_ms_per_step": ms, "md_ns_per_day": 0.0864 * 1e3 / ms * s.dt,
+                    "md_rebuilds": int(info["skin_rebuilds"] - r0), "md_steps": nmd,
+                    "stored_list_entries": int(info["skin_vcap"]) if sk > 0 else 0})
+        skin[f"skin_{sk:g}A"] = row
         c.close()
+    base = skin["skin_0A"]["static_force_ms"]
+    for sk in (1.0, 2.0):
+        r = skin[f"skin_{sk:g}A"]
+        gain = base - r["static_force_ms"]
+        r["break_even_steps_between_rebuilds"] = (r["rebuild_force_ms"] - r["static_force_ms"]) / gain if gain > 0 else None
     var["verlet_skin"] = skin
     out["variants"] = var
 

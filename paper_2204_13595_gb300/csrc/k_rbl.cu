@@ -557,31 +557,40 @@ __device__ __forceinline__ void classify_pair(const float4* __restrict__ stage, 
 // Classification of atom i's stored list V(i) (Verlet-skin variant) at the
 // current positions: the exact rule on the fixed-point codes (minimum image
 // by the 32-bit wrap), members appended in the order of V(i) to the core and
-// shell buffers.  Two chunks of 32 entries per iteration; V(i) never holds i.
+// shell buffers.  Four chunks of 32 entries per iteration (their list and
+// position loads in flight together: the positions are gathered from L2);
+// V(i) never holds i.
 __device__ __forceinline__ void classify_stored(const RblArgs& a, int i, uint4 si, int lane, unsigned lt_mask,
                                                 int* core_buf, int* shell_buf, int& ncore, int& nshell, bool& overlap)
 {
     const unsigned FULL = 0xffffffffu;
     const int nv = min(a.vcnt[i], a.vcap);
     const int* __restrict__ V = a.vlist + (size_t)i * a.vcap;
-    for (int t0 = 0; t0 < nv; t0 += 64) {
-        const int ta = t0 + lane, tb = ta + 32;
-        const bool va = ta < nv, vb = tb < nv;
-        const int ja = va ? V[ta] : i, jb = vb ? V[tb] : i;
-        const unsigned long long da = d2_exact(si, a.s4[ja]), db = d2_exact(si, a.s4[jb]);
-        const bool ca = va && da <= a.c.Rc2, cb = vb && db <= a.c.Rc2;
-        const bool sa = va && da > a.c.Rc2 && da <= a.c.Rs2, sb = vb && db > a.c.Rc2 && db <= a.c.Rs2;
-        overlap |= (va && da == 0ull) || (vb && db == 0ull);
-        const unsigned cma = __ballot_sync(FULL, ca), cmb = __ballot_sync(FULL, cb);
-        const unsigned sma = __ballot_sync(FULL, sa), smb = __ballot_sync(FULL, sb);
-        const int cpa = ncore + __popc(cma & lt_mask), cpb = ncore + __popc(cma) + __popc(cmb & lt_mask);
-        const int spa = nshell + __popc(sma & lt_mask), spb = nshell + __popc(sma) + __popc(smb & lt_mask);
-        if (ca && cpa < a.core_cap) core_buf[cpa] = ja;
-        if (cb && cpb < a.core_cap) core_buf[cpb] = jb;
-        if (sa && spa < a.shell_cap) shell_buf[spa] = ja;
-        if (sb && spb < a.shell_cap) shell_buf[spb] = jb;
-        ncore += __popc(cma) + __popc(cmb);
-        nshell += __popc(sma) + __popc(smb);
+    for (int t0 = 0; t0 < nv; t0 += 128) {
+        int j[4];
+        bool ok[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int t = t0 + 32 * c + lane;
+            ok[c] = t < nv;
+            j[c] = ok[c] ? V[t] : i;
+        }
+        uint4 sj[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sj[c] = a.s4[j[c]];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const unsigned long long d2 = d2_exact(si, sj[c]);
+            const bool cc = ok[c] && d2 <= a.c.Rc2;
+            const bool ss = ok[c] && d2 > a.c.Rc2 && d2 <= a.c.Rs2;
+            overlap |= ok[c] && d2 == 0ull;
+            const unsigned cm = __ballot_sync(FULL, cc), sm = __ballot_sync(FULL, ss);
+            const int cp = ncore + __popc(cm & lt_mask), sp = nshell + __popc(sm & lt_mask);
+            if (cc && cp < a.core_cap) core_buf[cp] = j[c];
+            if (ss && sp < a.shell_cap) shell_buf[sp] = j[c];
+            ncore += __popc(cm);
+            nshell += __popc(sm);
+        }
     }
 }
 
@@ -602,7 +611,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
 
     // ---- shared layout ------------------------------------------------------
     const int nt2 = c.ntypes * c.ntypes;
-    const SmemLayout lay = smem_layout(g, nt2, p, a.core_cap, a.shell_cap);
+    // (the list build keeps no core list here: the same layout as the host's)
+    const SmemLayout lay = smem_layout(g, nt2, p, LMODE == RBL_BUILD ? 0 : a.core_cap, a.shell_cap);
     float4* stage = reinterpret_cast<float4*>(smem);                              // [cap_stage]
     RowInfo* rows = reinterpret_cast<RowInfo*>(smem + lay.rows);                   // [nrows]
     int* cellpos = reinterpret_cast<int*>(smem + lay.cellpos);                     // [nrows * cpr]
@@ -628,7 +638,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     unsigned* rstart = reinterpret_cast<unsigned*>(ranges + RBL_MAX_RANGES);              // [RBL_MAX_PACKED / 32]
     uint64_t* words = reinterpret_cast<uint64_t*>(rstart + RBL_MAX_PACKED / 32);         // [ga][p_pad]
     int* core_buf = reinterpret_cast<int*>(words + (size_t)p_pad * lay.ga);
-    int* shell_buf = core_buf + a.core_cap;
+    int* const core_buf_w = core_buf;
+    int* shell_buf = core_buf + (LMODE == RBL_BUILD ? 0 : a.core_cap);
     int* sel = shell_buf + a.shell_cap;
     __shared__ int s_unit_ok;
     __shared__ double red[WARPS][RBE_NPART_RBL];
@@ -1133,6 +1144,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
         // one_atom: lists, batch and pair terms of atom i, whose Philox words
         // are wa_in[0 .. p_pad)
         auto one_atom = [&](const int i, const uint64_t* wa_in) {
+            int* core_buf = LMODE == RBL_BUILD ? a.vlist + (size_t)i * a.vcap : core_buf_w;
             const uint4 si = a.s4[i];
             const float4 fi4 = a.f4[i];
             const int cx = (int)cell_of_fixed(si.x, nc);
@@ -1266,15 +1278,14 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
             }
             if constexpr (LMODE == RBL_BUILD) {
                 // the stored list V(i): every member within r_s + skin (the
-                // "core" of this launch's radii), canonical order
+                // "core" of this launch's radii), canonical order, written
+                // by the classification straight into the list
                 if (__any_sync(FULL, overlap) && lane == 0) latch_status(a.status, RBE_ST_OVERLAP);
                 if (ncore > a.vcap && lane == 0) {
                     latch_status(a.status, RBE_ST_CAPACITY);
                     atomicMax(a.status + RBE_STW_NEED_LIST, ncore);
                 }
-                const int nv = min(ncore, a.vcap);
-                for (int t = lane; t < nv; t += 32) a.vlist[(size_t)i * a.vcap + t] = core_buf[t];
-                if (lane == 0) a.vcnt[i] = nv;
+                if (lane == 0) a.vcnt[i] = min(ncore, a.vcap);
                 __syncwarp();
             } else {
                 finish_atom(i, si, ncore, nshell, overlap, wa_in);
@@ -1646,7 +1657,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
 }
 
 template <bool MIXED, bool SMALL, bool ADJ>
-__global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
+__global__ void __launch_bounds__(WARPS * 32, RBE_BLOCKS_RBL) k_rbl(RblArgs a)
 {
     rbl_body<MIXED, SMALL, ADJ>(a, blockIdx.x, gridDim.x);
 }
@@ -1655,13 +1666,13 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl(RblArgs a)
 // (a.c and a.g hold that radius and its geometry), and the per-step kernel
 // over the stored lists.
 template <bool SMALL>
-__global__ void __launch_bounds__(WARPS * 32, 2) k_rbl_build(RblArgs a)
+__global__ void __launch_bounds__(WARPS * 32, RBE_BLOCKS_RBL) k_rbl_build(RblArgs a)
 {
     rbl_body<false, SMALL, false, RBL_BUILD>(a, blockIdx.x, gridDim.x);
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(WARPS * 32, 2) k_rbl_stored(RblArgs a)
+__global__ void __launch_bounds__(WARPS * 32, RBE_BLOCKS_RBL) k_rbl_stored(RblArgs a)
 {
     rbl_body<MIXED, false, false, RBL_STORED>(a, blockIdx.x, gridDim.x);
 }
@@ -1675,7 +1686,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_rbl_stored(RblArgs a)
 // every force and energy, equal those of the single-system launch.
 static_assert(sizeof(RblArgs) % 8 == 0, "RblArgs copy");
 template <bool MIXED, bool PERSIST>
-__global__ void __launch_bounds__(WARPS * 32, 2) k_rbl_batch(const RblArgs* __restrict__ args,
+__global__ void __launch_bounds__(WARPS * 32, RBE_BLOCKS_RBL) k_rbl_batch(const RblArgs* __restrict__ args,
                                                              const int2* __restrict__ tasks, int ntasks,
                                                              BatchCtl* __restrict__ ctl)
 {
@@ -1728,10 +1739,11 @@ int rbl_smem_bytes(const rbe_ctx* ctx)
 
 size_t rbl_args_bytes() { return sizeof(RblArgs); }
 
-// Dynamic shared memory per block that leaves room for two resident blocks of
-// every form of the pair kernel on the current device: half the SM's shared
-// memory, less the per-block reservation and the largest static shared
-// memory of the forms (the batched form also keeps its arguments there).
+// Dynamic shared memory per block that leaves room for RBE_BLOCKS_RBL resident
+// blocks of every form of the pair kernel on the current device: that share
+// of the SM's shared memory, less the per-block reservation and the largest
+// static shared memory of the forms (the batched form also keeps its
+// arguments there).
 int rbl_smem_target()
 {
     static int cached = 0;
@@ -1747,7 +1759,7 @@ int rbl_smem_target()
         return 110 * 1024;
     }
     const size_t st = f1.sharedSizeBytes > f2.sharedSizeBytes ? f1.sharedSizeBytes : f2.sharedSizeBytes;
-    cached = per_sm / 2 - reserved - (int)st;
+    cached = per_sm / RBE_BLOCKS_RBL - reserved - (int)st;
     return cached;
 }
 
@@ -1797,9 +1809,11 @@ void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st, bool adjoin
     prof_end(ctx, RBE_K_RBL, st);
 }
 
+// (the list build keeps no core list in shared memory: members go straight
+// to the stored lists)
 int rbl_build_smem_bytes(const rbe_ctx* ctx)
 {
-    return (int)smem_layout(ctx->skin_g, ctx->c.ntypes * ctx->c.ntypes, ctx->c.p, ctx->skin_vcap, 32).total;
+    return (int)smem_layout(ctx->skin_g, ctx->c.ntypes * ctx->c.ntypes, ctx->c.p, 0, 32).total;
 }
 
 long rbl_build_units(const rbe_ctx* ctx)

@@ -18,7 +18,12 @@
 #include "../../include/rbe.h"
 
 #define RBE_MAXT 16
+#ifndef RBE_WARPS_RBL
 #define RBE_WARPS_RBL 8          // warps per block of the pair kernel
+#endif
+#ifndef RBE_BLOCKS_RBL
+#define RBE_BLOCKS_RBL 2         // resident blocks per SM the pair kernel is sized for
+#endif
 #define RBE_NPART_RBL 12         // Ec, Elj, Ex, W[6], Fsum[3]
 #define RBE_NPART_Q 3            // sum q^2, sum q, sum |q|
 #define RBE_RBL_PAIR_CARVE 416   // words of the per-warp shell buffer the two-atom pair path uses beyond a core list
