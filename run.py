@@ -1,7 +1,7 @@
 """Command-line driver: runs IRBE force evaluations on a synthetic system.
 
   python run.py --system water --n-mol 400000 \\
-         --precision mixed --steps 3 [--warmup 1] [--profile]
+         --precision mixed --steps 3 [--warmup 1] [--profile] [--skin 1.0]
 
 Prints the mean time per force evaluation (CUDA events on the launching
 stream) and, with --profile, the per-kernel launch times the library records.
@@ -31,6 +31,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--profile", action="store_true")
+    ap.add_argument("--skin", type=float, default=0.0,
+                    help="Verlet skin in length units (0: lists every step); the first call builds the stored lists")
     a = ap.parse_args(argv)
     build.build()
     if a.system == "water":
@@ -40,6 +42,8 @@ def main(argv=None):
         s = systems.electrolyte(n=a.n_mol, L=L, seed=a.seed)
     ctx = rbe.Context(s.L, s.alpha, s.r_c, s.r_s, s.p, s.P, a.seed, k_e=s.k_e, eps=s.eps, sigma=s.sigma,
                       precision=rbe.MIXED if a.precision == "mixed" else rbe.FP64)
+    if a.skin > 0:
+        ctx.set_verlet_skin(a.skin)
     dev = lambda x, dt=torch.float64: torch.tensor(x, dtype=dt, device="cuda")
     pos, q, typ = dev(s.pos), dev(s.q), dev(s.type, torch.int32)
     mol = None if s.mol is None else dev(s.mol, torch.int32)
