@@ -298,3 +298,37 @@ def test_fourier_variance_closed_form(orc):
     # the mean agrees with the exact k-space force within its standard error
     z = (samples.mean(0) - mean) / np.sqrt(pred / nseeds)
     assert np.abs(z).max() < 4.5
+
+
+def test_nve_heating_rate_equals_force_variance(orc, wat):
+    """An unbiased stochastic force F = F_true + xi, with xi drawn afresh at
+    each evaluation (variance sigma^2 per component), heats velocity-Verlet
+    NVE dynamics by 1/2 dt^2 accel sum_i sum_c sigma_ic^2 / m_i per step: the
+    velocity picks up dt accel xi / m per step (the two half kicks that use
+    one evaluation add coherently), the cross terms vanish because xi has zero
+    mean given the state (Sec. 2.2's unbiasedness), and the kinetic energy is
+    m v^2 / (2 accel).  The variance comes from 300 seeds of the estimator at
+    the start configuration; the heating is the mean slope of the total
+    energy over 14 seeded NVE runs of 50 steps (flexible water, bonded terms
+    deterministic).  Re-drawing the force for the first half kick of a step
+    (instead of reusing the last one) would halve the heating; dropping the
+    Fourier or the real-space noise would lower it by that part's share."""
+    s = wat
+    nvar, nrun, nsteps = 300, 14, 50
+    F = np.array([orc.rbe_forces(s.pos, s.q, s.type, s.mol, _params(orc, s, seed=500 + k), 0)["F"]
+                  for k in range(nvar)])
+    var = F.var(0, ddof=1)
+    pred = 0.5 * s.dt**2 * s.accel * (var / s.mass[:, None]).sum()
+    bonded = orc.water_bonded(s.pos, s.L, s.n_water_mol, *s.bonds)[1]
+    t = np.arange(nsteps, dtype=np.float64)
+    slopes = []
+    for k in range(nrun):
+        pr = _params(orc, s, seed=2000 + k)
+        F0 = orc.rbe_forces(s.pos, s.q, s.type, s.mol, pr, 0)["F"] + bonded
+        out = orc.vv_run(s.pos, s.vel, s.mass, s.q, s.type, s.mol, pr, 0, nsteps, s.dt, s.accel, F0,
+                         water=(s.n_water_mol, *s.bonds))
+        assert out["status"] == 0
+        slopes.append(np.polyfit(t, out["trace"].sum(1), 1)[0])
+    slopes = np.array(slopes)
+    se = slopes.std(ddof=1) / math.sqrt(nrun)
+    assert abs(slopes.mean() - pred) < 4 * se + 0.06 * pred, (slopes.mean(), se, pred)
