@@ -240,6 +240,35 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r)
     return base;
 }
 
+// Floyd's algorithm over the ordinals [0, N_S), one slot per lane (p <= 32):
+// slot k draws t_k uniform in [0, N_S - p + k] and inserts t_k, or N_S - p + k
+// if t_k is already in the set.  Slot k's draw is in the set of slots 0..k-1
+// exactly when an earlier slot drew the same value (that value is in the set
+// whether or not that slot was replaced) or when t_k = N_S - p + m for an
+// earlier slot m that was replaced.  The first test is one match over the
+// warp; the second only chains through replaced slots of smaller index, so
+// iterating it from the first test's result reaches the sequential
+// algorithm's answer in at most p rounds (one round when no draw falls among
+// the top p ordinals).  Returns lane k's inserted ordinal (lanes >= p: -1).
+__device__ __forceinline__ int floyd_slot(const uint64_t* wa, int nshell, int p, int lane, unsigned lt_mask)
+{
+    const unsigned FULL = 0xffffffffu;
+    const uint32_t jk = (uint32_t)(nshell - p + lane);
+    const int tk = lane < p ? (int)uniform_below(wa[lane], jk + 1u) : -1 - lane;
+    const bool d1 = (__match_any_sync(FULL, tk) & lt_mask) != 0u;
+    const int m = tk - (nshell - p);
+    const bool link = lane < p && m >= 0 && m < lane;
+    unsigned dup = __ballot_sync(FULL, d1);
+    if (__any_sync(FULL, link)) {
+        for (int it = 0; it < p; ++it) {
+            const unsigned nd = __ballot_sync(FULL, d1 || (link && ((dup >> (link ? m : 0)) & 1u)));
+            if (nd == dup) break;
+            dup = nd;
+        }
+    }
+    return lane < p ? (((dup >> lane) & 1u) ? (int)jk : tk) : -1;
+}
+
 // Classification of one canonical segment [beg, end) of the source array:
 // FP32 distance with exact integer decision inside the rounding bands.
 template <bool SMALL>
@@ -763,22 +792,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
             for (int k = lane; k < p; k += 32) sel[k] = (int)uniform_below(wa[k], (uint32_t)nshell);
         } else if (sample) {
             if (p <= 32) {
-                // slot k on lane k; the insertions resolved in slot order
-                const uint32_t jk = (uint32_t)(nshell - p + lane);
-                const int tk = lane < p ? (int)uniform_below(wa[lane], jk + 1u) : -1 - lane;
-                // if the p draws are distinct, no slot is replaced and every
-                // slot keeps its draw (by induction over the slots);
-                // otherwise resolve the slots in order
-                const bool distinct = !__any_sync(FULL, (__match_any_sync(FULL, tk) & lt_mask) != 0u);
-                int mysel = tk;
-                if (!distinct) {
-                    mysel = -1;
-                    for (int k = 0; k < p; ++k) {
-                        const int t = __shfl_sync(FULL, tk, k);
-                        const bool dup = __any_sync(FULL, lane < k && mysel == t);
-                        if (lane == k) mysel = dup ? (int)jk : t;
-                    }
-                }
+                // slot k on lane k
+                const int mysel = floyd_slot(wa, nshell, p, lane, lt_mask);
                 if (lane < p) sel[lane] = mysel;
             } else {
                 for (int k = 0; k < p; ++k) {
@@ -1472,18 +1487,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                         if (lane < p) out[lane] = (int)uniform_below(wa[lane], (uint32_t)nshell);
                         return;
                     }
-                    const uint32_t jk = (uint32_t)(nshell - p + lane);
-                    const int tk = lane < p ? (int)uniform_below(wa[lane], jk + 1u) : -1 - lane;
-                    const bool distinct = !__any_sync(FULL, (__match_any_sync(FULL, tk) & lt_mask) != 0u);
-                    int mysel = tk;
-                    if (!distinct) {
-                        mysel = -1;
-                        for (int k = 0; k < p; ++k) {
-                            const int t = __shfl_sync(FULL, tk, k);
-                            const bool dup = __any_sync(FULL, lane < k && mysel == t);
-                            if (lane == k) mysel = dup ? (int)jk : t;
-                        }
-                    }
+                    const int mysel = floyd_slot(wa, nshell, p, lane, lt_mask);
                     if (lane < p) out[lane] = mysel;
                 };
                 if (sampA) draw(nsA, waA, selA);
