@@ -269,6 +269,33 @@ __device__ __forceinline__ int floyd_slot(const uint64_t* wa, int nshell, int p,
     return lane < p ? (((dup >> lane) & 1u) ? (int)jk : tk) : -1;
 }
 
+// floyd_slot for two atoms at once (their latency chains overlap): A's
+// slots from waA over [0, nA), B's from waB over [0, nB); both nA, nB > p.
+__device__ __forceinline__ void floyd_slot2(const uint64_t* waA, int nA, const uint64_t* waB, int nB, int p, int lane,
+                                            unsigned lt_mask, int& selA, int& selB)
+{
+    const unsigned FULL = 0xffffffffu;
+    const uint32_t jA = (uint32_t)(nA - p + lane), jB = (uint32_t)(nB - p + lane);
+    const int tA = lane < p ? (int)uniform_below(waA[lane], jA + 1u) : -1 - lane;
+    const int tB = lane < p ? (int)uniform_below(waB[lane], jB + 1u) : -1 - lane;
+    const bool dA = (__match_any_sync(FULL, tA) & lt_mask) != 0u;
+    const bool dB = (__match_any_sync(FULL, tB) & lt_mask) != 0u;
+    const int mA = tA - (nA - p), mB = tB - (nB - p);
+    const bool lA = lane < p && mA >= 0 && mA < lane, lB = lane < p && mB >= 0 && mB < lane;
+    unsigned dupA = __ballot_sync(FULL, dA), dupB = __ballot_sync(FULL, dB);
+    if (__any_sync(FULL, lA || lB)) {
+        for (int it = 0; it < p; ++it) {
+            const unsigned nA2 = __ballot_sync(FULL, dA || (lA && ((dupA >> (lA ? mA : 0)) & 1u)));
+            const unsigned nB2 = __ballot_sync(FULL, dB || (lB && ((dupB >> (lB ? mB : 0)) & 1u)));
+            if (nA2 == dupA && nB2 == dupB) break;
+            dupA = nA2;
+            dupB = nB2;
+        }
+    }
+    selA = lane < p ? (((dupA >> lane) & 1u) ? (int)jA : tA) : -1;
+    selB = lane < p ? (((dupB >> lane) & 1u) ? (int)jB : tB) : -1;
+}
+
 // Classification of one canonical segment [beg, end) of the source array:
 // FP32 distance with exact integer decision inside the rounding bands.
 template <bool SMALL>
@@ -656,13 +683,10 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     double* s_dsds = s_dsde + nt2;
     double* s_rc2 = s_dsds + nt2;           // squared LJ cutoff per pair type
     double* s_glj = s_rc2 + nt2;            // adjoint: [4][nt2] block accumulators
-    // mixed forces: FP32 copies of c12, c6, shift and the cutoff, held where
-    // the adjoint keeps eps_ab and sigma_ab (one conversion per block, none
-    // per pair)
-    float* f_c12 = reinterpret_cast<float*>(s_eps);
-    float* f_c6 = f_c12 + nt2;
-    float* f_sh = f_c6 + nt2;
-    float* f_rc2 = f_sh + nt2;
+    // mixed forces: FP32 copies of (c12, c6, shift, squared cutoff) per type
+    // pair, one 16-byte entry each, held where the adjoint keeps eps_ab and
+    // sigma_ab (one conversion per block, one shared load per pair)
+    float4* f_lj = reinterpret_cast<float4*>(smem + up16(lay.lj + 3 * sizeof(double) * (size_t)nt2));
     int2* ranges = reinterpret_cast<int2*>(smem + lay.warps + lay.wbytes * wib);          // [RBL_MAX_RANGES]
     unsigned* rstart = reinterpret_cast<unsigned*>(ranges + RBL_MAX_RANGES);              // [RBL_MAX_PACKED / 32]
     uint64_t* words = reinterpret_cast<uint64_t*>(rstart + RBL_MAX_PACKED / 32);         // [ga][p_pad]
@@ -671,6 +695,15 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     int* shell_buf = core_buf + (LMODE == RBL_BUILD ? 0 : a.core_cap);
     int* sel = shell_buf + a.shell_cap;
     __shared__ int s_unit_ok;
+    // completion barrier of the staging copies (one phase per staged unit)
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ uint32_t s_phase;        // parity of the barrier's current phase
+    __shared__ int s_stage_total;       // staged atoms of the current unit
+    if (threadIdx.x == 0) {
+        mbar_init(&s_mbar, 1u);
+        s_phase = 0u;
+    }
+    __syncthreads();
     __shared__ double red[WARPS][RBE_NPART_RBL];
 
     for (int t = threadIdx.x; t < nt2; t += blockDim.x) {
@@ -680,10 +713,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
         s_sh[t] = a.lj->shift[ti * RBE_MAXT + tj];
         s_rc2[t] = a.lj->rc2[ti * RBE_MAXT + tj];
         if (MIXED && !ADJ) {
-            f_c12[t] = (float)s_c12[t];
-            f_c6[t] = (float)s_c6[t];
-            f_sh[t] = (float)s_sh[t];
-            f_rc2[t] = (float)s_rc2[t];
+            f_lj[t] = make_float4((float)s_c12[t], (float)s_c6[t], (float)s_sh[t], (float)s_rc2[t]);
         }
         if (ADJ) {
             s_eps[t] = a.lj->eps[ti * RBE_MAXT + tj];
@@ -709,13 +739,13 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     const int units_per_row = (nc + G - 1) / G;
     const long nunits = (long)nc * nc * units_per_row;
 
-    // Eq. (2.10) in FP32 (mixed path) for atom i (fixed-point si, charge qi,
-    // (type, mol) ti) and partner j (sj, tj) with weight w: the Coulomb factor
-    // erfc (erfc - 1 = -erf for a same-molecule pair, the Ewald exclusion
-    // correction) and LJ; adds the force on i to ff and the weighted
-    // energies and virial to the per-lane sums
+    // Eq. (2.10) in FP32 (mixed path) for atom i (fixed-point si, kqi = k_e
+    // q_i, (type, mol) ti) and partner j (sj, tj) with weight w: the Coulomb
+    // factor erfc (erfc - 1 = -erf for a same-molecule pair, the Ewald
+    // exclusion correction) and LJ; adds the force on i to ff and the
+    // weighted energies and virial to the per-lane sums
     const float kef = (float)c.k_e, saf = (float)c.sqrt_alpha, tsaf = (float)c.two_sqrt_alpha_over_sqrt_pi;
-    auto mixed_term = [&](const uint4 si, const float qi, const int2 ti, const uint4 sj, const int2 tj, const float w,
+    auto mixed_term = [&](const uint4 si, const float kqi, const int2 ti, const uint4 sj, const int2 tj, const float w,
                           float* ff) {
         const float dx = (float)(int)(sj.x - si.x) * c.Lfix;
         const float dy = (float)(int)(sj.y - si.y) * c.Lfix;
@@ -723,7 +753,7 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
         const float r2 = dx * dx + dy * dy + dz * dz;
         const float rinv = rsqrtf(r2);
         const float r = r2 * rinv;
-        const float qq = kef * qi * __uint_as_float(sj.w);
+        const float qq = kqi * __uint_as_float(sj.w);
         const float ar = saf * r;
         const float ex2 = __expf(-ar * ar);
         const float gauss = tsaf * ex2;
@@ -731,13 +761,13 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
         const float ec = erfc_hastings(ar, ex2) - (ex ? 1.0f : 0.0f);
         const float ucoul = qq * ec * rinv;
         float sc = -qq * (ec * rinv + gauss) * rinv * rinv;
-        const int tt = ti.x * c.ntypes + tj.x;
-        const bool nolj = ex || !(r2 < f_rc2[tt]);
-        const float c12 = nolj ? 0.f : f_c12[tt], c6 = nolj ? 0.f : f_c6[tt];
+        const float4 lj = f_lj[ti.x * c.ntypes + tj.x];
+        const bool nolj = ex || !(r2 < lj.w);
+        const float c12 = nolj ? 0.f : lj.x, c6 = nolj ? 0.f : lj.y;
         const float ir2 = rinv * rinv;
         const float ir6 = ir2 * ir2 * ir2;
         sc -= (12.f * c12 * ir6 - 6.f * c6) * ir6 * ir2;
-        const float ulj = (c12 * ir6 - c6) * ir6 - (nolj ? 0.f : f_sh[tt]);
+        const float ulj = (c12 * ir6 - c6) * ir6 - (nolj ? 0.f : lj.z);
         const float gx = w * sc * dx, gy = w * sc * dy, gz = w * sc * dz;
         ff[0] += gx; ff[1] += gy; ff[2] += gz;
         facc_e[0] += ex ? 0.f : w * ucoul;
@@ -911,7 +941,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     w = wsh;
                 }
             };
-            auto term = [&](const uint4 sj, const int2 tj, const float w) { mixed_term(si, qi, ti, sj, tj, w, ff); };
+            const float kqi = kef * qi;
+            auto term = [&](const uint4 sj, const int2 tj, const float w) { mixed_term(si, kqi, ti, sj, tj, w, ff); };
             // two pairs per lane per iteration (t, t + 32: the order of the
             // one-pair loop), their loads issued together
             for (int t = lane; t < npairs; t += 64) {
@@ -1113,7 +1144,10 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                 if (r < nrows) rows[r].sbase = carry + incl - v;
                 carry += __shfl_sync(FULL, incl, 31);
             }
-            if (lane == 0) s_unit_ok = carry <= g.cap_stage;
+            if (lane == 0) {
+                s_unit_ok = carry <= g.cap_stage;
+                s_stage_total = carry;
+            }
         }
         __syncthreads();
         const bool staged = s_unit_ok;
@@ -1129,26 +1163,55 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                 off = cellabs[r * cpr + (ufirst - ul)] - (ri.sbase + cp[ufirst - ul]);
             rows[r].goff[pc] = off;
         }
-        // (e) stage the FP32 positions row by row, each piece moved to the
-        // periodic image adjacent to the unit (x: -L below cell 0, +L past
-        // cell nc-1; y, z: the row's shift), so that every staged candidate
-        // is compared with atom i's own position
+        // (e) stage the FP32 positions: one bulk asynchronous copy per
+        // non-empty piece of a row (contiguous in the sorted arrays and in the
+        // staged array), all completing on s_mbar, whose expected byte count
+        // thread 0 posts; then each piece that lies across the box boundary
+        // is moved in place to the periodic image adjacent to the unit (x: -L
+        // below cell 0, +L past cell nc-1; y, z: the row's shift), so that
+        // every staged candidate is compared with atom i's own position.  The
+        // wait is bounded: a copy that never completes latches RBE_ST_STAGE
+        // and the block stops.
         if (staged) {
+            if (threadIdx.x == 0) mbar_arrive_expect_tx(&s_mbar, 16u * (uint32_t)s_stage_total);
+            for (int t = threadIdx.x; t < nrows * 3; t += blockDim.x) {
+                const int r = t / 3, pc = t - 3 * r;
+                const int u0 = pc == 0 ? ul : (pc == 1 ? max(ul, 0) : max(ul, nc));
+                const int u1 = pc == 0 ? min(uh, -1) : (pc == 1 ? min(uh, nc - 1) : uh);
+                if (u0 > u1) continue;
+                const int* cp = cellpos + r * cpr;
+                const int len = cp[u1 - ul + 1] - cp[u0 - ul];
+                if (len <= 0) continue;
+                fence_proxy_async_smem();
+                bulk_copy_g2s(stage + rows[r].sbase + cp[u0 - ul], a.f4 + cellabs[r * cpr + (u0 - ul)],
+                              16u * (uint32_t)len, &s_mbar);
+            }
+            const uint32_t parity = s_phase;
+            const bool done = mbar_wait_bounded(&s_mbar, parity, 1 << 22);
+            if (__syncthreads_or(!done)) {
+                if (threadIdx.x == 0) latch_status(a.status, RBE_ST_STAGE);
+                mbar_wait_bounded(&s_mbar, parity, 1 << 22);     // copies still in flight
+                return;
+            }
+            if (threadIdx.x == 0) s_phase = parity ^ 1u;     // read again after the unit's next barriers
             for (int r = wib; r < nrows; r += WARPS) {
                 const int sb = rows[r].sbase;
                 const float shy = rows[r].shy, shz = rows[r].shz;
                 const int* cp = cellpos + r * cpr;
                 for (int pc = 0; pc < 3; ++pc) {
+                    const float shx = pc == 0 ? -Lf : (pc == 2 ? Lf : 0.f);
+                    if (shx == 0.f && shy == 0.f && shz == 0.f) continue;
                     const int u0 = pc == 0 ? ul : (pc == 1 ? max(ul, 0) : max(ul, nc));
                     const int u1 = pc == 0 ? min(uh, -1) : (pc == 1 ? min(uh, nc - 1) : uh);
                     if (u0 > u1) continue;
-                    const float shx = pc == 0 ? -Lf : (pc == 2 ? Lf : 0.f);
-                    const int gs = cellabs[r * cpr + (u0 - ul)];
                     const int len = cp[u1 - ul + 1] - cp[u0 - ul];
                     const int ss = sb + cp[u0 - ul];
                     for (int k = lane; k < len; k += 32) {
-                        const float4 q4 = a.f4[gs + k];
-                        stage[ss + k] = make_float4(q4.x + shx, q4.y + shy, q4.z + shz, q4.w);
+                        float4 q4 = stage[ss + k];
+                        q4.x += shx;
+                        q4.y += shy;
+                        q4.z += shz;
+                        stage[ss + k] = q4;
                     }
                 }
             }
@@ -1490,8 +1553,14 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     const int mysel = floyd_slot(wa, nshell, p, lane, lt_mask);
                     if (lane < p) out[lane] = mysel;
                 };
-                if (sampA) draw(nsA, waA, selA);
-                if (sampB) draw(nsB, waB, selB);
+                if (sampA && sampB && c.shell_mode != 1) {
+                    int sa, sb;
+                    floyd_slot2(waA, nsA, waB, nsB, p, lane, lt_mask, sa, sb);
+                    if (lane < p) { selA[lane] = sa; selB[lane] = sb; }
+                } else {
+                    if (sampA) draw(nsA, waA, selA);
+                    if (sampB) draw(nsB, waB, selB);
+                }
                 __syncwarp();
                 // member of ordinal t of the shell: chunk c with pfx[c] <= t <
                 // pfx[c + 1] (binary search), the (t - pfx[c])-th set bit of
@@ -1533,60 +1602,50 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                 __syncwarp();
 
                 // ---- 4. pair terms of A and B on the lanes of the warp ---------
-                const int npA = ncAc + nbA, npB = hasB ? ncBc + nbB : 0, npt = npA + npB;
-                const float wshA = sampA ? (float)nsA / (float)p : 1.0f;
-                const float wshB = sampB ? (float)nsB / (float)p : 1.0f;
-                const int2 tiA = a.tm[iA], tiB = a.tm[iB];
-                const float qiA = __uint_as_float(sA.w), qiB = __uint_as_float(sB.w);
-                float ffA[3] = {0.f, 0.f, 0.f}, ffB[3] = {0.f, 0.f, 0.f};
-                auto pair_of = [&](int t, int& j, float& w) {
-                    const bool isA = t < npA;
-                    const int k = isA ? t : t - npA;
-                    const int ncx = isA ? ncAc : ncBc;
-                    if (k < ncx) { j = isA ? coreA[k] : coreB[k]; w = 1.0f; }
-                    else { j = isA ? jA[k - ncx] : jB[k - ncx]; w = isA ? wshA : wshB; }
+                // lanes 0-15 take A's pairs, lanes 16-31 B's: each lane keeps
+                // one atom, so the pair term needs no per-pair choice between
+                // A and B; two pairs per lane per iteration (k, k + 16), their
+                // loads issued together
+                const int npA = ncAc + nbA, npB = hasB ? ncBc + nbB : 0;
+                const bool hb = lane >= 16;
+                const int l16 = lane & 15;
+                const int npX = hb ? npB : npA, ncX = hb ? ncBc : ncAc;
+                const float wshX = hb ? (sampB ? (float)nsB / (float)p : 1.0f) : (sampA ? (float)nsA / (float)p : 1.0f);
+                const int* coreX = hb ? coreB : coreA;
+                const int* jX = hb ? jB : jA;
+                const uint4 sX = hb ? sB : sA;
+                const int2 tiX = a.tm[hb ? iB : iA];
+                const float kqX = kef * __uint_as_float(sX.w);
+                float ff[3] = {0.f, 0.f, 0.f};
+                auto pair_of = [&](int k, int& j, float& w) {
+                    if (k < ncX) { j = coreX[k]; w = 1.0f; }
+                    else { j = jX[k - ncX]; w = wshX; }
                 };
-                // one evaluation per lane whichever atom the pair belongs to
-                // (no divergence where a warp's pairs change from A to B)
-                auto term2 = [&](int t, const uint4 sj, const int2 tj, const float w) {
-                    const bool isA = t < npA;
-                    float g[3] = {0.f, 0.f, 0.f};
-                    mixed_term(isA ? sA : sB, isA ? qiA : qiB, isA ? tiA : tiB, sj, tj, w, g);
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        ffA[q] += isA ? g[q] : 0.f;
-                        ffB[q] += isA ? 0.f : g[q];
-                    }
-                };
-                // two pairs per lane per iteration (t, t + 32), loads issued together
-                for (int t = lane; t < npt; t += 64) {
-                    const bool v2 = t + 32 < npt;
+                for (int k = l16; k < npX; k += 32) {
+                    const bool v2 = k + 16 < npX;
                     int j1, j2;
                     float w1, w2;
-                    pair_of(t, j1, w1);
-                    if (v2) pair_of(t + 32, j2, w2);
+                    pair_of(k, j1, w1);
+                    if (v2) pair_of(k + 16, j2, w2);
                     else { j2 = j1; w2 = 0.f; }
                     const uint4 sj1 = a.s4[j1];
                     const int2 tj1 = a.tm[j1];
                     const uint4 sj2 = a.s4[j2];
                     const int2 tj2 = a.tm[j2];
-                    term2(t, sj1, tj1, w1);
-                    if (v2) term2(t + 32, sj2, tj2, w2);
+                    mixed_term(sX, kqX, tiX, sj1, tj1, w1, ff);
+                    if (v2) mixed_term(sX, kqX, tiX, sj2, tj2, w2, ff);
                 }
+                // sums over each half-warp
 #pragma unroll
-                for (int q = 0; q < 3; ++q) { ffA[q] = warp_sum(ffA[q]); ffB[q] = warp_sum(ffB[q]); }
-                if (lane == 0) {
-                    float* Fr = reinterpret_cast<float*>(a.F_real);
-                    Fr[3 * (size_t)iA + 0] = ffA[0];
-                    Fr[3 * (size_t)iA + 1] = ffA[1];
-                    Fr[3 * (size_t)iA + 2] = ffA[2];
-                    facc_f[0] += ffA[0]; facc_f[1] += ffA[1]; facc_f[2] += ffA[2];
-                    if (hasB) {
-                        Fr[3 * (size_t)iB + 0] = ffB[0];
-                        Fr[3 * (size_t)iB + 1] = ffB[1];
-                        Fr[3 * (size_t)iB + 2] = ffB[2];
-                        facc_f[0] += ffB[0]; facc_f[1] += ffB[1]; facc_f[2] += ffB[2];
-                    }
+                for (int q = 0; q < 3; ++q)
+#pragma unroll
+                    for (int o = 8; o >= 1; o >>= 1) ff[q] += __shfl_xor_sync(FULL, ff[q], o);
+                if (l16 == 0 && (!hb || hasB)) {
+                    float* Fr = reinterpret_cast<float*>(a.F_real) + 3 * (size_t)(hb ? iB : iA);
+                    Fr[0] = ff[0];
+                    Fr[1] = ff[1];
+                    Fr[2] = ff[2];
+                    facc_f[0] += ff[0]; facc_f[1] += ff[1]; facc_f[2] += ff[2];
                 }
                 flush_sums(hasB ? 2 : 1);
 
@@ -1631,6 +1690,12 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
             }
         }
     }
+
+    // every staging copy has completed (each unit waited for its phase): the
+    // barrier is invalidated before its memory is initialised again (the
+    // batched form runs this body once per task)
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_inval(&s_mbar);
 
     // ---- deterministic block partials ---------------------------------------
     if constexpr (LMODE == RBL_BUILD) return;        // no pair terms in the list build

@@ -546,6 +546,7 @@ int status_code(int bits)
     if (bits & RBE_ST_NONNEUTRAL) return RBE_ENONNEUTRAL;
     if (bits & RBE_ST_BADTYPE) return RBE_EINVAL;
     if (bits & RBE_ST_KSAMPLE) return RBE_ECUDA;
+    if (bits & RBE_ST_STAGE) return RBE_ECUDA;
     return RBE_OK;
 }
 

@@ -47,6 +47,7 @@
 #define RBE_ST_NONFINITE 8
 #define RBE_ST_KSAMPLE   16
 #define RBE_ST_BADTYPE   32
+#define RBE_ST_STAGE     64   // a shared-memory staging copy did not complete in time
 
 struct RbeConsts {
     double L, invL, alpha, sqrt_alpha, two_sqrt_alpha_over_sqrt_pi, k_e;
@@ -339,6 +340,56 @@ __device__ __forceinline__ T warp_sum(T v)
 }
 
 __device__ __forceinline__ void latch_status(int* status, int bit) { atomicOr(status, bit); }
+
+// Bulk asynchronous copies (TMA, non-tensor form) from global to shared
+// memory, completing on a shared-memory mbarrier: the barrier's arrival count
+// is 1 (the thread that posts the expected bytes), each copy decrements its
+// transaction count by the bytes it wrote, and the phase completes when both
+// reach zero.  Addresses 16-byte aligned, sizes multiples of 16.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* m)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* m, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+// Waits for the phase of the given parity to complete, giving up after
+// `limit` polls (each poll may suspend the thread for a short while).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, uint32_t parity, int limit)
+{
+    for (int it = 0; it < limit; ++it)
+        if (mbar_try_wait(m, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m)
+{
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(m))
+                 : "memory");
+}
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// its later async-proxy ones (a bulk copy into memory that was just written).
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // floor(u * n / 2^64) for n < 2^32: a uniform integer in [0, n) from a 64-bit word.
 __device__ __forceinline__ uint32_t uniform_below(uint64_t u, uint32_t n)
