@@ -50,6 +50,10 @@ L2_FLUSH_BYTES = 512 << 20
 # algorithmic work of the RBL kernel per atom: 420 pair classifications x 9
 # ops + 72.5 pair evaluations x 45 ops (core 52.5 + p = 20), in lane ops
 RBL_OPS_PER_ATOM = 420 * 9 + 72.5 * 45
+# Eq. (2.10) terms per atom (52.5 core + p = 20 batch members) and counted
+# operations per term: the part of RBL_OPS_PER_ATOM that the FP64 path
+# computes in FP64 (its classification is FP32 and integer, as on the mixed path)
+RBL_PAIRS_PER_ATOM, RBL_OPS_PER_PAIR = 72.5, 45
 SM_COUNT = 152
 LANES_PER_SM = 128
 SFU_LANES_PER_SM = 16
@@ -144,6 +148,22 @@ def _kernel_roofline(prof, n, P, ncells, peaks_meas):
         if cnt:
             out[k] = {"bound": "latency", "avg_launch_ms": ms / cnt}
     return out
+
+
+def _fp64_rbl_roofline(prof64, n, meas):
+    """The FP64 path's pair kernel against the measured FP64 FMA rate of this
+    GPU (bench_peak_probe 'dfma'): the counted FP64 operations of the pair
+    terms per launch over its CUDA-event time.  The library erfc, exp and
+    reciprocal square root take several FP64 instructions per counted
+    operation, so the FP64 pipe is far busier than this fraction says."""
+    ms, cnt = prof64.get("rbl", (0.0, 0)) if prof64 else (0.0, 0)
+    peak = meas.get("dfma")
+    if not cnt or not isinstance(peak, float):
+        return None
+    t = ms / cnt * 1e-3
+    a = RBL_PAIRS_PER_ATOM * RBL_OPS_PER_PAIR * n / t
+    return {"bound": "fp64", "achieved": a / 1e12, "peak": peak / 1e12, "unit": "Top/s", "frac": a / peak,
+            "peak_source": "measured: bench_peak_probe dfma in this run", "avg_launch_ms": t * 1e3}
 
 
 def _dist():
@@ -631,7 +651,7 @@ def run_ours(args):
             meas[kind] = f"unavailable: {e}"
     clocks_proc = _clock_sampler() if rank == 0 else None
     ms_mixed, prof, launches = timed(mixed, args.steps, args.warmup, profile=True)
-    ms_f64, _, _ = timed(f64, max(3, min(args.steps, 10)), max(3, min(args.warmup, 3)))
+    ms_f64, prof64, _ = timed(f64, max(3, min(args.steps, 10)), max(3, min(args.warmup, 3)), profile=True)
     batch = _batch_leg(flush) if ws == 1 else None
     next_rows = _next_rows_leg(flush, (s, pos, q, typ, mol)) if ws == 1 else None
     configs = _configs_leg(flush) if ws == 1 else None
@@ -693,7 +713,8 @@ def run_ours(args):
                      "traffic": traffic, "peak_source": "derived: 152 SMs x 128 lanes x 2070 MHz, 1 op/lane/clk",
                      "avg_launch_ms": rbl_avg_s * 1e3},
         "kernel_share": kshare,
-        "kernel_roofline": _kernel_roofline(prof, s.n, s.P, mixed.info()["n_cell"] ** 3, meas),
+        "kernel_roofline": dict(_kernel_roofline(prof, s.n, s.P, mixed.info()["n_cell"] ** 3, meas),
+                                rbl_fp64=_fp64_rbl_roofline(prof64, s.n, meas)),
         "measured_pipes": {
             "ffma_per_s": meas.get("ffma"), "dfma_per_s": meas.get("dfma"), "sfu_sin_per_s": meas.get("sfu"),
             "int_ops_per_s": meas.get("alu"), "copy_bytes_per_s": meas.get("copy"),

@@ -53,7 +53,8 @@ extern "C" {
 #define RBE_EOVERLAP     -3   /* two atoms at the same fixed-point position     */
 #define RBE_ENONFINITE   -4   /* non-finite position or result                  */
 #define RBE_ECAPACITY    -5   /* a per-atom list exceeded its capacity          */
-#define RBE_ECUDA        -6   /* a CUDA runtime call failed                     */
+#define RBE_ECUDA        -6   /* a CUDA runtime call failed, or a device-side
+                                  copy wait ran out (shared-memory staging)    */
 #define RBE_ENOMEM       -7   /* device allocation failed                       */
 
 /* precision modes (rbe_set_precision) */

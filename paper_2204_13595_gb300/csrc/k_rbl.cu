@@ -4,9 +4,13 @@
 // (cells of edge L/floor(L/r_c), the grid of Sec. 2.3).  A block takes units
 // round-robin; for each unit it stages, in shared memory, the FP32 positions
 // of every atom in the union of the unit's stencils: (2R+1)^2 rows of G+2R
-// cells, R = floor(r_s/w)+1 (Sec. 2.3's stencil reach), each piece of a row
-// moved to the periodic image adjacent to the unit.  Each warp then owns one
-// atom i of the unit at a time:
+// cells, R = floor(r_s/w)+1 (Sec. 2.3's stencil reach), by one bulk
+// asynchronous copy per contiguous piece of a row (completing on an
+// mbarrier), each piece that lies across the box boundary then moved to the
+// periodic image adjacent to the unit.  Each warp then owns one atom i of the
+// unit at a time (two atoms A, B of the same cell row on the mixed path,
+// which share the range lookups and staged loads of the classification and
+// split the warp's lanes between their pair terms):
 //   1. list construction: the lanes take i's stencil rows (32 per pass) in
 //      canonical order (ascending wrapped cell index, then fixed-point x, then
 //      atom index); each row is cut to the cells that can hold a point within
