@@ -120,15 +120,20 @@ static_assert(RBL_PAIR_CARVE == RBE_RBL_PAIR_CARVE, "carve of the two-atom path"
 // Shared-memory layout of k_rbl; every section starts on a 16-byte boundary.
 // Per warp: the range table of the current pass [RBL_MAX_RANGES] int2 and the
 // bitmap of range starts [RBL_MAX_PACKED / 32] words, the Philox words
-// [ga][p_pad], the core and shell lists and the batch ordinals.
+// [ga][p_pad], the core and shell lists and the batch ordinals, and (stored-
+// list kernel only) the double buffer of stored-list entries [2][RBL_LGROUP].
 struct SmemLayout {
-    size_t rows, cellpos, cellabs, lj, warps, wbytes, total;
+    size_t rows, cellpos, cellabs, lj, warps, wbytes, lbuf, total;
     int ga;                // atoms whose Philox words are made in one warp pass
 };
+// entries of a stored list V(i) classified per step of the stored-list
+// kernel (four chunks of 32), copied one step ahead
+constexpr int RBL_LGROUP = 128;
 
 __host__ __device__ inline size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline SmemLayout smem_layout(const RblGeom& g, int nt2, int p, int core_cap, int shell_cap)
+__host__ __device__ inline SmemLayout smem_layout(const RblGeom& g, int nt2, int p, int core_cap, int shell_cap,
+                                                  bool list_buffer = false)
 {
     SmemLayout L;
     const int p_pad = (p + 3) & ~3;
@@ -146,6 +151,8 @@ __host__ __device__ inline SmemLayout smem_layout(const RblGeom& g, int nt2, int
     L.warps = o;
     L.wbytes = sizeof(int2) * RBL_MAX_RANGES + sizeof(unsigned) * (RBL_MAX_PACKED / 32) +
                up16(sizeof(uint64_t) * (size_t)p_pad * L.ga + sizeof(int) * (size_t)(core_cap + shell_cap + p_pad));
+    L.lbuf = L.wbytes;     // offset inside a warp's region
+    if (list_buffer) L.wbytes += sizeof(int) * 2 * RBL_LGROUP;
     L.total = o + L.wbytes * WARPS;
     return L;
 }
@@ -614,43 +621,39 @@ __device__ __forceinline__ void classify_pair(const float4* __restrict__ stage, 
     }
 }
 
-// Classification of atom i's stored list V(i) (Verlet-skin variant) at the
-// current positions: the exact rule on the fixed-point codes (minimum image
-// by the 32-bit wrap), members appended in the order of V(i) to the core and
-// shell buffers.  Four chunks of 32 entries per iteration (their list and
-// position loads in flight together: the positions are gathered from L2);
-// V(i) never holds i.
-__device__ __forceinline__ void classify_stored(const RblArgs& a, int i, uint4 si, int lane, unsigned lt_mask,
-                                                int* core_buf, int* shell_buf, int& ncore, int& nshell, bool& overlap)
+// Classification of entries [t0, t0 + RBL_LGROUP) of atom i's stored list
+// V(i) (Verlet-skin variant; nv entries in all, those of this step in the
+// shared buffer vb) at the current positions: the exact rule on the
+// fixed-point codes (minimum image by the 32-bit wrap), members appended in
+// the order of V(i) to the core and shell buffers.  The four chunks' position
+// loads are in flight together; V(i) never holds i.
+__device__ __forceinline__ void classify_stored(const RblArgs& a, int i, uint4 si, const int* vb, int t0, int nv,
+                                                int lane, unsigned lt_mask, int* core_buf, int* shell_buf,
+                                                int& ncore, int& nshell, bool& overlap)
 {
     const unsigned FULL = 0xffffffffu;
-    const int nv = min(a.vcnt[i], a.vcap);
-    const int* __restrict__ V = a.vlist + (size_t)i * a.vcap;
-    for (int t0 = 0; t0 < nv; t0 += 128) {
-        int j[4];
-        bool ok[4];
+    int j[4];
+    bool ok[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int t = t0 + 32 * c + lane;
-            ok[c] = t < nv;
-            j[c] = ok[c] ? V[t] : i;
-        }
-        uint4 sj[4];
+    for (int c = 0; c < 4; ++c) {
+        ok[c] = t0 + 32 * c + lane < nv;
+        j[c] = ok[c] ? vb[32 * c + lane] : i;
+    }
+    uint4 sj[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) sj[c] = a.s4[j[c]];
+    for (int c = 0; c < 4; ++c) sj[c] = a.s4[j[c]];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const unsigned long long d2 = d2_exact(si, sj[c]);
-            const bool cc = ok[c] && d2 <= a.c.Rc2;
-            const bool ss = ok[c] && d2 > a.c.Rc2 && d2 <= a.c.Rs2;
-            overlap |= ok[c] && d2 == 0ull;
-            const unsigned cm = __ballot_sync(FULL, cc), sm = __ballot_sync(FULL, ss);
-            const int cp = ncore + __popc(cm & lt_mask), sp = nshell + __popc(sm & lt_mask);
-            if (cc && cp < a.core_cap) core_buf[cp] = j[c];
-            if (ss && sp < a.shell_cap) shell_buf[sp] = j[c];
-            ncore += __popc(cm);
-            nshell += __popc(sm);
-        }
+    for (int c = 0; c < 4; ++c) {
+        const unsigned long long d2 = d2_exact(si, sj[c]);
+        const bool cc = ok[c] && d2 <= a.c.Rc2;
+        const bool ss = ok[c] && d2 > a.c.Rc2 && d2 <= a.c.Rs2;
+        overlap |= ok[c] && d2 == 0ull;
+        const unsigned cm = __ballot_sync(FULL, cc), sm = __ballot_sync(FULL, ss);
+        const int cp = ncore + __popc(cm & lt_mask), sp = nshell + __popc(sm & lt_mask);
+        if (cc && cp < a.core_cap) core_buf[cp] = j[c];
+        if (ss && sp < a.shell_cap) shell_buf[sp] = j[c];
+        ncore += __popc(cm);
+        nshell += __popc(sm);
     }
 }
 
@@ -672,7 +675,8 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     // ---- shared layout ------------------------------------------------------
     const int nt2 = c.ntypes * c.ntypes;
     // (the list build keeps no core list here: the same layout as the host's)
-    const SmemLayout lay = smem_layout(g, nt2, p, LMODE == RBL_BUILD ? 0 : a.core_cap, a.shell_cap);
+    const SmemLayout lay = smem_layout(g, nt2, p, LMODE == RBL_BUILD ? 0 : a.core_cap, a.shell_cap,
+                                       LMODE == RBL_STORED);
     float4* stage = reinterpret_cast<float4*>(smem);                              // [cap_stage]
     RowInfo* rows = reinterpret_cast<RowInfo*>(smem + lay.rows);                   // [nrows]
     int* cellpos = reinterpret_cast<int*>(smem + lay.cellpos);                     // [nrows * cpr]
@@ -1048,10 +1052,31 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
     };
 
     if constexpr (LMODE == RBL_STORED) {
-        // atoms in sorted order, one per warp at a time, over the whole grid
+        // atoms in sorted order, one per warp at a time, over the whole grid.
+        // The entries of V(i) are classified RBL_LGROUP per step from a
+        // per-warp double buffer in shared memory: while one step's entries
+        // are classified, the next step's (the next group of V(i), or the
+        // first of the warp's next atom) are being copied in, so the list read
+        // from memory overlaps the position loads and the classification.
+        int* lbuf = reinterpret_cast<int*>(smem + lay.warps + lay.wbytes * wib + lay.lbuf);
         const int stride = nslots * WARPS;
+        // lane copies entries [t0 + 4 lane, t0 + 4 lane + 4) of V(ii) if the
+        // first is below nvv (rows hold vcap entries, a multiple of 4, so
+        // the copy stays in the row); one commit group per step
+        auto issue = [&](int ii, int t0, int nvv, int buf) {
+            const int e0 = t0 + 4 * lane;
+            if (4 * lane < RBL_LGROUP && e0 < nvv)
+                cp_async16(lbuf + buf * RBL_LGROUP + 4 * lane, a.vlist + (size_t)ii * a.vcap + e0);
+            cp_async_commit();
+        };
+        int i = slot * WARPS + wib;
+        int nv = i < a.n ? min(a.vcnt[i], a.vcap) : 0;
+        int buf = 0;
+        if (i < a.n) issue(i, 0, nv, buf);
         int kloc = 0;
-        for (int i = slot * WARPS + wib; i < a.n; i += stride, ++kloc) {
+        for (; i < a.n; i += stride, ++kloc) {
+            const int inext = i + stride;
+            const int nvn = inext < a.n ? min(a.vcnt[inext], a.vcap) : 0;
             const int aslot = kloc % lay.ga;
             if (aslot == 0) {
                 __syncwarp();
@@ -1070,10 +1095,22 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
             const uint4 si = a.s4[i];
             int ncore = 0, nshell = 0;
             bool overlap = false;
-            classify_stored(a, i, si, lane, lt_mask, core_buf, shell_buf, ncore, nshell, overlap);
-            __syncwarp();
+            const int ng = max(1, (nv + RBL_LGROUP - 1) / RBL_LGROUP);
+            for (int gi = 0; gi < ng; ++gi) {
+                if (gi + 1 < ng) issue(i, (gi + 1) * RBL_LGROUP, nv, buf ^ 1);
+                else if (inext < a.n) issue(inext, 0, nvn, buf ^ 1);
+                else cp_async_commit();                  // (an empty group)
+                cp_async_wait<1>();                      // this step's copies have landed
+                __syncwarp();
+                classify_stored(a, i, si, lbuf + buf * RBL_LGROUP, gi * RBL_LGROUP, nv, lane, lt_mask, core_buf,
+                                shell_buf, ncore, nshell, overlap);
+                __syncwarp();                            // the buffer is refilled two steps on
+                buf ^= 1;
+            }
             finish_atom(i, si, ncore, nshell, overlap, words + (size_t)aslot * p_pad);
+            nv = nvn;
         }
+        cp_async_wait<0>();
     }
     for (long unit = LMODE == RBL_STORED ? nunits : slot; unit < nunits; unit += nslots) {
         const int ux = (int)(unit % units_per_row);
@@ -1745,7 +1782,7 @@ __global__ void __launch_bounds__(WARPS * 32, RBE_BLOCKS_RBL) k_rbl_build(RblArg
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(WARPS * 32, RBE_BLOCKS_RBL) k_rbl_stored(RblArgs a)
+__global__ void __launch_bounds__(WARPS * 32, RBE_BLOCKS_STORED) k_rbl_stored(RblArgs a)
 {
     rbl_body<MIXED, false, false, RBL_STORED>(a, blockIdx.x, gridDim.x);
 }
@@ -1931,7 +1968,8 @@ void launch_rbl_stored(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st)
     g.G = 1; g.nrows = 0; g.cap_stage = 0; g.cells_per_row = 0; g.small = 0;
     a.g = g;
     a.vlist = ctx->vlist; a.vcnt = ctx->vcnt; a.vcap = ctx->skin_vcap;
-    const int smem = (int)smem_layout(g, ctx->c.ntypes * ctx->c.ntypes, ctx->c.p, ctx->core_cap, ctx->shell_cap).total;
+    const int smem =
+        (int)smem_layout(g, ctx->c.ntypes * ctx->c.ntypes, ctx->c.p, ctx->core_cap, ctx->shell_cap, true).total;
     if (a.debug) cudaMemsetAsync(ctx->dbg_unstaged, 0, 2 * sizeof(int), st);
     prof_begin(ctx, RBE_K_RBL, st);
     if (ctx->precision == RBE_MIXED) {

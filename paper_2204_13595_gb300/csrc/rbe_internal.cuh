@@ -24,6 +24,13 @@
 #ifndef RBE_BLOCKS_RBL
 #define RBE_BLOCKS_RBL 2         // resident blocks per SM the pair kernel is sized for
 #endif
+#ifndef RBE_BLOCKS_STORED
+// resident blocks per SM of the stored-list (Verlet skin) pair kernel: it
+// stages no stencil, so three blocks fit in shared memory; its register
+// budget then drops to 80 (a few spills), which the extra resident warps
+// repay (measured on the 1.2M-atom water box at a 1 A skin: 3.45 -> 3.13 ms)
+#define RBE_BLOCKS_STORED 3
+#endif
 #define RBE_NPART_RBL 12         // Ec, Elj, Ex, W[6], Fsum[3]
 #define RBE_NPART_Q 3            // sum q^2, sum q, sum |q|
 #define RBE_RBL_PAIR_CARVE 416   // words of the per-warp shell buffer the two-atom pair path uses beyond a core list
@@ -386,6 +393,20 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(m))
                  : "memory");
+}
+// Asynchronous 16-byte global -> shared copies (both addresses 16-byte
+// aligned); a thread sees its own copies after cp_async_wait, other threads'
+// after that and a barrier.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// waits until at most N of this thread's committed groups are still pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 // Orders this thread's earlier generic-proxy accesses to shared memory before
 // its later async-proxy ones (a bulk copy into memory that was just written).
