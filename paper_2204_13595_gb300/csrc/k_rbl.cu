@@ -471,6 +471,7 @@ __device__ __forceinline__ void classify_packed(const float4* __restrict__ stage
         for (int c = 0; c < 4; ++c) {
             const bool ok = c < 3 || (v0 + 96 + lane) < T;
             dist_class<false>(pp[c], ok, xi, yi, zi, g, 0.f, 0.f, cc[c], ss[c], mm[c]);
+            mm[c] = mm[c] && gg[c] != i;        // i's own entry (r = 0) is no member: no exact test
             any_m |= mm[c];
         }
         if (__any_sync(FULL, any_m)) {
@@ -502,6 +503,8 @@ __device__ __forceinline__ void classify_packed(const float4* __restrict__ stage
         dist_class<false>(pa, true, xi, yi, zi, g, 0.f, 0.f, ca, sha, ma);
         dist_class<false>(pb, vbok, xi, yi, zi, g, 0.f, 0.f, cb, shb, mb);
         const int ga = va + ra.y, gb = vb + rb.y;
+        ma = ma && ga != i;
+        mb = mb && gb != i;
         if (__any_sync(FULL, ma || mb)) {
             if (ma) exact_class(a, i, si, ga, ca, sha, overlap);
             if (mb) exact_class(a, i, si, gb, cb, shb, overlap);
@@ -527,6 +530,7 @@ __device__ __forceinline__ void classify_packed(const float4* __restrict__ stage
         bool ca, sha, ma;
         dist_class<false>(pa, vaok, xi, yi, zi, g, 0.f, 0.f, ca, sha, ma);
         const int ga = va + ra.y;
+        ma = ma && ga != i;
         if (__any_sync(FULL, ma)) {
             if (ma) exact_class(a, i, si, ga, ca, sha, overlap);
         }
@@ -575,6 +579,12 @@ __device__ __forceinline__ void classify_pair(const float4* __restrict__ stage, 
         dist_class<false>(qb, vbok, pA.x, pA.y, pA.z, g, 0.f, 0.f, cbA, sbA, mbA);
         dist_class<false>(qa, hasB, pB.x, pB.y, pB.z, g, 0.f, 0.f, caB, saB, maB);
         dist_class<false>(qb, hasB && vbok, pB.x, pB.y, pB.z, g, 0.f, 0.f, cbB, sbB, mbB);
+        // an atom's own entry (r = 0) is no member: excluded by index, which
+        // keeps it out of the exact test (one global load per atom saved)
+        maA = maA && ga != iA;
+        mbA = mbA && gb != iA;
+        maB = maB && ga != iB;
+        mbB = mbB && gb != iB;
         if (__any_sync(FULL, maA || mbA || maB || mbB)) {
             if (maA) exact_class(a, iA, sA, ga, caA, saA, overlap);
             if (mbA) exact_class(a, iA, sA, gb, cbA, sbA, overlap);
@@ -606,6 +616,8 @@ __device__ __forceinline__ void classify_pair(const float4* __restrict__ stage, 
         bool caA, saA, maA, caB, saB, maB;
         dist_class<false>(qa, vaok, pA.x, pA.y, pA.z, g, 0.f, 0.f, caA, saA, maA);
         dist_class<false>(qa, hasB && vaok, pB.x, pB.y, pB.z, g, 0.f, 0.f, caB, saB, maB);
+        maA = maA && ga != iA;
+        maB = maB && ga != iB;
         if (__any_sync(FULL, maA || maB)) {
             if (maA) exact_class(a, iA, sA, ga, caA, saA, overlap);
             if (maB) exact_class(a, iB, sB, ga, caB, saB, overlap);
@@ -1552,6 +1564,21 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     atomicMax(a.status + RBE_STW_NEED_CORE, max(ncA, ncB));
                 }
                 const int ncAc = min(ncA, a.core_cap), ncBc = min(ncB, a.core_cap);
+                // the first pair-term step of each half-warp (pairs l16 and
+                // l16 + 16 of its atom: core members when the core holds 32 or
+                // more) has its partner loads issued now, so that they land
+                // while the batches are drawn and located
+                const bool pre = (lane < 16 ? ncAc : ncBc) >= 32 && (lane < 16 || hasB);
+                uint4 ps1 = make_uint4(0u, 0u, 0u, 0u), ps2 = ps1;
+                int2 pt1 = make_int2(0, 0), pt2 = pt1;
+                if (pre) {
+                    const int* cX = lane < 16 ? coreA : coreB;
+                    const int j1 = cX[lane & 15], j2 = cX[(lane & 15) + 16];
+                    ps1 = a.s4[j1];
+                    pt1 = a.tm[j1];
+                    ps2 = a.s4[j2];
+                    pt2 = a.tm[j2];
+                }
 
                 // exclusive prefix counts over the chunks (two per lane): shell
                 // members of A and B, range starts
@@ -1662,7 +1689,13 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     if (k < ncX) { j = coreX[k]; w = 1.0f; }
                     else { j = jX[k - ncX]; w = wshX; }
                 };
-                for (int k = l16; k < npX; k += 32) {
+                int k0 = l16;
+                if (pre) {
+                    mixed_term(sX, kqX, tiX, ps1, pt1, 1.0f, ff);
+                    mixed_term(sX, kqX, tiX, ps2, pt2, 1.0f, ff);
+                    k0 += 32;
+                }
+                for (int k = k0; k < npX; k += 32) {
                     const bool v2 = k + 16 < npX;
                     int j1, j2;
                     float w1, w2;
