@@ -434,8 +434,7 @@ __device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, c
     __shared__ double4_32a sk_d[MIXED ? 1 : KT];      // kx, ky, kz, unused
     __shared__ double2 sab_d[MIXED ? 1 : KT];     // (c Im rho, c Re rho)
     __shared__ int4 sm[KT];
-    __shared__ float4 sk_f[MIXED ? KT : 1];       // kx, ky, kz, c Im rho
-    __shared__ float sb_f[MIXED ? KT : 1];        // c Re rho
+    __shared__ float4 sk_f[MIXED ? KT : 1];       // kx, ky, kz, c Im rho (mixed: sm[k].w holds c Re rho)
     const int i = bx * TPB + threadIdx.x;
     const bool act = i < n;
     uint4 si = make_uint4(0, 0, 0, 0);
@@ -459,9 +458,9 @@ __device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, c
             double4_32a k4 = kv[l0 + k];
             double2 r = rho[l0 + k];
             if (MIXED) {
-                sm[k] = km[l0 + k];
+                const int4 mk = km[l0 + k];
+                sm[k] = make_int4(mk.x, mk.y, mk.z, __float_as_int((float)(k4.w * r.x)));
                 sk_f[k] = make_float4((float)k4.x, (float)k4.y, (float)k4.z, (float)(k4.w * r.y));
-                sb_f[k] = (float)(k4.w * r.x);
             } else {
                 sm[k] = km[l0 + k];
                 sk_d[k] = k4;
@@ -480,7 +479,7 @@ __device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, c
                     __sincosf(ang, &sn, &cs);
                     float4 kk = sk_f[k];
                     // Im(e^{-i th} rho) c = cos(th) c Im rho - sin(th) c Re rho
-                    float h = cs * kk.w - sn * sb_f[k];
+                    float h = cs * kk.w - sn * __int_as_float(m.w);
                     g[0] += h * kk.x; g[1] += h * kk.y; g[2] += h * kk.z;
                 }
                 for (int a = 0; a < 3; ++a) f[a] += (double)g[a];
