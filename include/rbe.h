@@ -128,8 +128,11 @@ int rbe_set_capacity(rbe_ctx* ctx, int core_cap, int shell_cap);
  * membership and contribute -k_e q_i q_j erf(sqrt(alpha) r)/r instead of
  * erfc + LJ.  type may be NULL (all type 0).
  * pos, q, type, mol, F are either all device pointers or all host pointers.
- * With host pointers the library stages them through device memory and the
- * call returns after F is written.  energy (RBE_NE) and virial (RBE_NW) may each
+ * With host pointers the call returns after F is written: inputs in pinned
+ * (page-locked, device-mapped) host memory are read by the device in place,
+ * other host inputs are first copied to device memory (as are all host inputs
+ * of a context with a Verlet skin); F is computed in device memory and copied
+ * back.  energy (RBE_NE) and virial (RBE_NW) may each
  * be NULL, a host pointer (the call then waits for the stream) or a device
  * pointer.  Positions need not be wrapped into the box.
  * Errors found on the device (overlap, capacity, non-neutral charge,

@@ -30,12 +30,18 @@ __device__ __forceinline__ void nonfinite_stand_in(int i, int n, double L, doubl
     z = a * ((double)(i / ((long)m * m)) + 0.5);
 }
 
-// Wrap, quantise, bin; latch non-finite input; per-block sums of q^2, q, |q|.
+// Wrap, quantise, bin; latch non-finite input and bad types; per-block sums
+// of q^2, q, |q|; the atom's records in caller order (codes and FP32 charge,
+// wrapped FP64 position and charge, (type, molecule)) for the gather.  The
+// inputs are read once, in order: they may lie in pinned host memory.
 __device__ __forceinline__ void quantize_count_body(int bx, int nbx, int n, const double* __restrict__ pos,
-                                                    const double* __restrict__ q, const RbeConsts& c,
+                                                    const double* __restrict__ q, const int32_t* __restrict__ type,
+                                                    const int32_t* __restrict__ mol, const RbeConsts& c,
                                                     int* __restrict__ cell_count, int* __restrict__ cell_of,
                                                     int* __restrict__ slot, uint32_t* __restrict__ sx_of,
-                                                    double* __restrict__ part_q, int* __restrict__ status)
+                                                    uint4* __restrict__ rec_s4, double4_32a* __restrict__ rec_p4,
+                                                    int2* __restrict__ rec_tm, double* __restrict__ part_q,
+                                                    int* __restrict__ status)
 {
     double sq2 = 0.0, sq = 0.0, sabs = 0.0;
     const unsigned FULL = 0xffffffffu;
@@ -54,15 +60,23 @@ __device__ __forceinline__ void quantize_count_body(int bx, int nbx, int n, cons
             const bool bad_pos = !isfinite(x) || !isfinite(y) || !isfinite(z);
             if (bad_pos || !isfinite(qi)) latch_status(status, RBE_ST_NONFINITE);
             if (bad_pos) nonfinite_stand_in(i, n, c.L, x, y, z);     // the same rule as the gather
-            double xw;
+            double xw, yw, zw;
             uint32_t sx, sy, sz;
             wrap_fixed(x, c.invL, c.L, xw, sx);
-            wrap_fixed(y, c.invL, c.L, xw, sy);
-            wrap_fixed(z, c.invL, c.L, xw, sz);
+            wrap_fixed(y, c.invL, c.L, yw, sy);
+            wrap_fixed(z, c.invL, c.L, zw, sz);
             uint32_t cx = cell_of_fixed(sx, c.n_cell), cy = cell_of_fixed(sy, c.n_cell), cz = cell_of_fixed(sz, c.n_cell);
             cell = (int)(cx + (uint32_t)c.n_cell * (cy + (uint32_t)c.n_cell * cz));
             cell_of[i] = cell;
             sx_of[i] = sx;
+            rec_s4[i] = make_uint4(sx, sy, sz, __float_as_uint((float)qi));
+            rec_p4[i] = make_double4_32a(xw, yw, zw, qi);
+            int t = type ? type[i] : 0;
+            if (t < 0 || t >= c.ntypes) {
+                latch_status(status, RBE_ST_BADTYPE);
+                t = 0;
+            }
+            rec_tm[i] = make_int2(t, mol ? mol[i] : -(i + 1));
             sq2 += qi * qi;
             sq += qi;
             sabs += fabs(qi);
@@ -87,12 +101,16 @@ __device__ __forceinline__ void quantize_count_body(int bx, int nbx, int n, cons
 }
 
 __global__ void __launch_bounds__(TPB) k_quantize_count(int n, const double* __restrict__ pos,
-                                                        const double* __restrict__ q, RbeConsts c,
+                                                        const double* __restrict__ q, const int32_t* __restrict__ type,
+                                                        const int32_t* __restrict__ mol, RbeConsts c,
                                                         int* __restrict__ cell_count, int* __restrict__ cell_of,
                                                         int* __restrict__ slot, uint32_t* __restrict__ sx_of,
-                                                        double* __restrict__ part_q, int* __restrict__ status)
+                                                        uint4* __restrict__ rec_s4, double4_32a* __restrict__ rec_p4,
+                                                        int2* __restrict__ rec_tm, double* __restrict__ part_q,
+                                                        int* __restrict__ status)
 {
-    quantize_count_body(blockIdx.x, gridDim.x, n, pos, q, c, cell_count, cell_of, slot, sx_of, part_q, status);
+    quantize_count_body(blockIdx.x, gridDim.x, n, pos, q, type, mol, c, cell_count, cell_of, slot, sx_of, rec_s4,
+                        rec_p4, rec_tm, part_q, status);
 }
 
 // Exclusive scan of cell_count[0..m) into start[0..m] (single block).
@@ -282,43 +300,32 @@ __global__ void __launch_bounds__(TPB) k_sort_cells(long m, const int* __restric
     sort_cells_body(blockIdx.x, gridDim.x, m, start, skey, perm);
 }
 
-__device__ __forceinline__ void gather_body(int bx, int n, const int* __restrict__ perm, const double* __restrict__ pos,
-                                            const double* __restrict__ q, const int32_t* __restrict__ type,
-                                            const int32_t* __restrict__ mol, const RbeConsts& c,
-                                            uint4* __restrict__ s4, float4* __restrict__ f4,
-                                            double4_32a* __restrict__ p4, int2* __restrict__ tm,
-                                            int* __restrict__ status)
+// Sorted arrays from the quantisation's records: s4 (codes, FP32 charge), f4
+// (FP32 wrapped position, charge), p4 (FP64 wrapped position, charge) and tm
+// (type, molecule) of sorted atom k = caller atom perm[k].
+__device__ __forceinline__ void gather_body(int bx, int n, const int* __restrict__ perm,
+                                            const uint4* __restrict__ rec_s4, const double4_32a* __restrict__ rec_p4,
+                                            const int2* __restrict__ rec_tm, uint4* __restrict__ s4,
+                                            float4* __restrict__ f4, double4_32a* __restrict__ p4,
+                                            int2* __restrict__ tm)
 {
     int k = bx * TPB + threadIdx.x;
     if (k >= n) return;
-    int i = perm[k];
-    double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) nonfinite_stand_in(i, n, c.L, x, y, z);
-    double xw, yw, zw;
-    uint32_t sx, sy, sz;
-    wrap_fixed(x, c.invL, c.L, xw, sx);
-    wrap_fixed(y, c.invL, c.L, yw, sy);
-    wrap_fixed(z, c.invL, c.L, zw, sz);
-    double qi = q[i];
-    float qf = (float)qi;
-    s4[k] = make_uint4(sx, sy, sz, __float_as_uint(qf));
-    f4[k] = make_float4((float)xw, (float)yw, (float)zw, qf);
-    p4[k] = make_double4_32a(xw, yw, zw, qi);
-    int t = type ? type[i] : 0;
-    if (t < 0 || t >= c.ntypes) {
-        latch_status(status, RBE_ST_BADTYPE);
-        t = 0;
-    }
-    tm[k] = make_int2(t, mol ? mol[i] : -(i + 1));
+    const int i = perm[k];
+    const uint4 s = rec_s4[i];
+    const double4_32a p = rec_p4[i];
+    s4[k] = s;
+    f4[k] = make_float4((float)p.x, (float)p.y, (float)p.z, __uint_as_float(s.w));
+    p4[k] = p;
+    tm[k] = rec_tm[i];
 }
 
-__global__ void __launch_bounds__(TPB) k_gather(int n, const int* __restrict__ perm, const double* __restrict__ pos,
-                                                const double* __restrict__ q, const int32_t* __restrict__ type,
-                                                const int32_t* __restrict__ mol, RbeConsts c, uint4* __restrict__ s4,
-                                                float4* __restrict__ f4, double4_32a* __restrict__ p4, int2* __restrict__ tm,
-                                                int* __restrict__ status)
+__global__ void __launch_bounds__(TPB) k_gather(int n, const int* __restrict__ perm, const uint4* __restrict__ rec_s4,
+                                                const double4_32a* __restrict__ rec_p4, const int2* __restrict__ rec_tm,
+                                                uint4* __restrict__ s4, float4* __restrict__ f4,
+                                                double4_32a* __restrict__ p4, int2* __restrict__ tm)
 {
-    gather_body(blockIdx.x, n, perm, pos, q, type, mol, c, s4, f4, p4, tm, status);
+    gather_body(blockIdx.x, n, perm, rec_s4, rec_p4, rec_tm, s4, f4, p4, tm);
 }
 
 // ---- Verlet-skin variant: steps between rebuilds -------------------------
@@ -415,8 +422,8 @@ __global__ void __launch_bounds__(TPB) k_quantize_count_b(const RepDev* __restri
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    quantize_count_body(bx, nbx, d.n, d.pos, d.q, d.c, d.cell_count, d.cell_of, d.slot, d.sx_of, d.part_q,
-                        d.status);
+    quantize_count_body(bx, nbx, d.n, d.pos, d.q, d.type, d.mol, d.c, d.cell_count, d.cell_of, d.slot, d.sx_of,
+                        d.rec_s4, d.rec_p4, d.rec_tm, d.part_q, d.status);
 }
 
 __global__ void __launch_bounds__(1024) k_scan_b(const RepDev* __restrict__ R)
@@ -444,7 +451,7 @@ __global__ void __launch_bounds__(TPB) k_gather_b(const RepDev* __restrict__ R, 
 {
     int bx, nbx;
     const RepDev& d = R[rep_of_block(off, nrep, blockIdx.x, bx, nbx)];
-    gather_body(bx, d.n, d.perm, d.pos, d.q, d.type, d.mol, d.c, d.s4, d.f4, d.p4, d.tm, d.status);
+    gather_body(bx, d.n, d.perm, d.rec_s4, d.rec_p4, d.rec_tm, d.s4, d.f4, d.p4, d.tm);
 }
 
 }  // namespace
@@ -466,12 +473,14 @@ void launch_skin_mark(rbe_ctx* ctx, int n, cudaStream_t st)
     prof_end(ctx, RBE_K_SKIN, st);
 }
 
-void launch_quantize_count(rbe_ctx* ctx, int n, const double* pos, const double* q, cudaStream_t st)
+void launch_quantize_count(rbe_ctx* ctx, int n, const double* pos, const double* q, const int32_t* type,
+                           const int32_t* mol, cudaStream_t st)
 {
     cudaMemsetAsync(ctx->cell_count, 0, sizeof(int) * (size_t)(ctx->ncells + 1), st);
     prof_begin(ctx, RBE_K_QUANTIZE, st);
-    k_quantize_count<<<ctx->grid_q, TPB, 0, st>>>(n, pos, q, ctx->c, ctx->cell_count, ctx->cell_of, ctx->slot,
-                                                  ctx->sx_of, ctx->part_q, ctx->status);
+    k_quantize_count<<<ctx->grid_q, TPB, 0, st>>>(n, pos, q, type, mol, ctx->c, ctx->cell_count, ctx->cell_of,
+                                                  ctx->slot, ctx->sx_of, ctx->rec_s4, ctx->rec_p4, ctx->rec_tm,
+                                                  ctx->part_q, ctx->status);
     prof_end(ctx, RBE_K_QUANTIZE, st);
 }
 
@@ -492,8 +501,7 @@ void launch_scan(rbe_ctx* ctx, cudaStream_t st)
 
 long scan_tiles(long ncells) { return (ncells + SCAN_TILE - 1) / SCAN_TILE; }
 
-void launch_scatter_sort_gather(rbe_ctx* ctx, int n, const double* pos, const double* q, const int32_t* type,
-                                const int32_t* mol, cudaStream_t st)
+void launch_scatter_sort_gather(rbe_ctx* ctx, int n, cudaStream_t st)
 {
     int g = (n + TPB - 1) / TPB;
     prof_begin(ctx, RBE_K_SCATTER, st);
@@ -505,8 +513,8 @@ void launch_scatter_sort_gather(rbe_ctx* ctx, int n, const double* pos, const do
                                                                             ctx->perm);
     prof_end(ctx, RBE_K_SORT, st);
     prof_begin(ctx, RBE_K_GATHER, st);
-    k_gather<<<g, TPB, 0, st>>>(n, ctx->perm, pos, q, type, mol, ctx->c, ctx->s4, ctx->f4, ctx->p4, ctx->tm,
-                                 ctx->status);
+    k_gather<<<g, TPB, 0, st>>>(n, ctx->perm, ctx->rec_s4, ctx->rec_p4, ctx->rec_tm, ctx->s4, ctx->f4, ctx->p4,
+                                 ctx->tm);
     prof_end(ctx, RBE_K_GATHER, st);
 }
 

@@ -124,7 +124,7 @@ void refresh_consts(rbe_ctx* ctx)
 
 void free_dev(rbe_ctx* ctx)
 {
-    void* ptrs[] = {ctx->cis, ctx->skey, ctx->scan_tmp, ctx->sx_of, ctx->F_lang, ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
+    void* ptrs[] = {ctx->cis, ctx->skey, ctx->scan_tmp, ctx->sx_of, ctx->F_lang, ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->rec_s4, ctx->rec_p4, ctx->rec_tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
                     ctx->F_real, ctx->F_bond, ctx->part_rbl, ctx->part_q, ctx->part_bond, ctx->kT, ctx->km, ctx->kv,
                     ctx->rho_part, ctx->rho, ctx->totals, ctx->status, ctx->lj, ctx->dbg_ncore, ctx->dbg_nshell,
                     ctx->dbg_core, ctx->dbg_batch, ctx->dbg_unstaged, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
@@ -136,6 +136,7 @@ void free_dev(rbe_ctx* ctx)
     for (int k = 0; k < 5; ++k) ctx->skin_cap[k] = 0;
     ctx->skin_valid = 0;
     ctx->s4 = nullptr; ctx->f4 = nullptr; ctx->p4 = nullptr; ctx->tm = nullptr; ctx->perm = nullptr; ctx->cell_of = nullptr;
+    ctx->rec_s4 = nullptr; ctx->rec_p4 = nullptr; ctx->rec_tm = nullptr;
     ctx->slot = nullptr; ctx->cell_count = nullptr; ctx->cell_start = nullptr; ctx->F_real = nullptr;
     ctx->F_bond = nullptr; ctx->part_rbl = nullptr; ctx->part_q = nullptr; ctx->part_bond = nullptr;
     ctx->kT = nullptr; ctx->km = nullptr; ctx->kv = nullptr; ctx->rho_part = nullptr; ctx->rho = nullptr;
@@ -147,7 +148,7 @@ void free_dev(rbe_ctx* ctx)
     ctx->tau_part = nullptr; ctx->tau = nullptr; ctx->kpool_buf = nullptr; ctx->kpool_dirty = 1;
     ctx->F_lang = nullptr; ctx->F_lang_cap = 0; ctx->sx_of = nullptr; ctx->scan_tmp = nullptr; ctx->skey = nullptr; ctx->cis = nullptr;
     ctx->n_cap = 0; ctx->dbg_n_cap = 0; ctx->h_cap = 0;
-    for (int k = 0; k < 24; ++k) ctx->cap_atoms[k] = 0;
+    for (int k = 0; k < 28; ++k) ctx->cap_atoms[k] = 0;
     for (int k = 0; k < 8; ++k) ctx->cap_adj[k] = 0;
 }
 
@@ -417,6 +418,9 @@ int ensure(rbe_ctx* ctx, int n)
     if ((rc = grow(ctx, &ctx->f4, &ctx->cap_atoms[17], n))) return rc;
     if ((rc = grow(ctx, &ctx->p4, &ctx->cap_atoms[1], n))) return rc;
     if ((rc = grow(ctx, &ctx->tm, &ctx->cap_atoms[2], n))) return rc;
+    if ((rc = grow(ctx, &ctx->rec_s4, &ctx->cap_atoms[23], n))) return rc;
+    if ((rc = grow(ctx, &ctx->rec_p4, &ctx->cap_atoms[24], n))) return rc;
+    if ((rc = grow(ctx, &ctx->rec_tm, &ctx->cap_atoms[25], n))) return rc;
     if ((rc = grow(ctx, &ctx->perm, &ctx->cap_atoms[3], n))) return rc;
     if ((rc = grow(ctx, &ctx->cell_of, &ctx->cap_atoms[4], n))) return rc;
     if ((rc = grow(ctx, &ctx->slot, &ctx->cap_atoms[5], n))) return rc;
@@ -452,6 +456,19 @@ bool is_device_ptr(const void* p)
         return false;
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// The device address of pinned host memory that the device can read in
+// place (page-locked and mapped into the device's address space), else null.
+const void* pinned_device_view(const void* p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 }  // namespace
@@ -493,9 +510,9 @@ int skin_prepare(rbe_ctx* ctx, int n, const double* pos, const double* q, const 
         rebuild = moved != 0;
     }
     if (rebuild) {
-        launch_quantize_count(ctx, n, pos, q, st);
+        launch_quantize_count(ctx, n, pos, q, type, mol, st);
         launch_scan(ctx, st);
-        launch_scatter_sort_gather(ctx, n, pos, q, type, mol, st);
+        launch_scatter_sort_gather(ctx, n, st);
         launch_skin_mark(ctx, n, st);
         launch_rbl_build(ctx, n, st);
         ctx->skin_valid = 1;
@@ -514,9 +531,9 @@ int forces_device(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const d
         int rc = skin_prepare(ctx, n, pos, q, type, mol, st);
         if (rc) return rc;
     } else {
-        launch_quantize_count(ctx, n, pos, q, st);
+        launch_quantize_count(ctx, n, pos, q, type, mol, st);
         launch_scan(ctx, st);
-        launch_scatter_sort_gather(ctx, n, pos, q, type, mol, st);
+        launch_scatter_sort_gather(ctx, n, st);
     }
     launch_ksample(ctx, step, st);
     launch_rho(ctx, n, st);
@@ -836,12 +853,24 @@ int rbe_forces(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const doub
             if ((rc = dev_alloc(ctx, &ctx->h_F, 3 * (size_t)n))) return rc;
             ctx->h_cap = n;
         }
-        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
-        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_q, q, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-        if (type) CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_type, type, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
-        if (mol) CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_mol, mol, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
-        rc = forces_device(ctx, step, n, ctx->h_pos, ctx->h_q, type ? ctx->h_type : nullptr, mol ? ctx->h_mol : nullptr,
-                           ctx->h_F, st);
+        // inputs in pinned host memory that the device can address are read in
+        // place: the quantisation reads them once, in order, and everything
+        // after it reads its device copies (the Verlet-skin path reads the
+        // positions in sorted order and takes the copies)
+        const double* vpos = (const double*)pinned_device_view(pos);
+        const double* vq = (const double*)pinned_device_view(q);
+        const int32_t* vtype = type ? (const int32_t*)pinned_device_view(type) : nullptr;
+        const int32_t* vmol = mol ? (const int32_t*)pinned_device_view(mol) : nullptr;
+        if (ctx->skin == 0.0 && vpos && vq && (!type || vtype) && (!mol || vmol)) {
+            rc = forces_device(ctx, step, n, vpos, vq, vtype, vmol, ctx->h_F, st);
+        } else {
+            CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_q, q, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+            if (type) CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_type, type, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+            if (mol) CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_mol, mol, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+            rc = forces_device(ctx, step, n, ctx->h_pos, ctx->h_q, type ? ctx->h_type : nullptr,
+                               mol ? ctx->h_mol : nullptr, ctx->h_F, st);
+        }
         if (rc) return rc;
         CUDA_TRY(ctx, cudaMemcpyAsync(F, ctx->h_F, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
         need_sync = true;
@@ -969,9 +998,9 @@ int rbe_adjoint(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const dou
     if ((rc = grow(ctx, &ctx->tau, &ctx->cap_adj[4], (size_t)ctx->c.P))) return rc;
     ctx->last_launches = 0;
     // the forward set-up of the same step: identical lists, batches, k samples
-    launch_quantize_count(ctx, n, pos, q, st);
+    launch_quantize_count(ctx, n, pos, q, type, mol, st);
     launch_scan(ctx, st);
-    launch_scatter_sort_gather(ctx, n, pos, q, type, mol, st);
+    launch_scatter_sort_gather(ctx, n, st);
     launch_ksample(ctx, step, st);
     launch_rho(ctx, n, st);
     launch_adj_prep(ctx, n, gF, st);

@@ -181,6 +181,7 @@ int build_plan(rbe_batch* b)
         d.cell_count = ctx->cell_count; d.cell_start = ctx->cell_start; d.cell_of = ctx->cell_of;
         d.slot = ctx->slot; d.perm = ctx->perm; d.sx_of = ctx->sx_of; d.skey = ctx->skey;
         d.s4 = ctx->s4; d.f4 = ctx->f4; d.p4 = ctx->p4; d.tm = ctx->tm;
+        d.rec_s4 = ctx->rec_s4; d.rec_p4 = ctx->rec_p4; d.rec_tm = ctx->rec_tm;
         d.part_q = ctx->part_q; d.part_rbl = ctx->part_rbl; d.part_bond = ctx->part_bond; d.ke_part = ctx->ke_part;
         d.kT = ctx->kT; d.km = ctx->km; d.kv = ctx->kv; d.rho_part = ctx->rho_part; d.rho = ctx->rho;
         d.totals = ctx->totals; d.F_real = ctx->F_real; d.F_bond = ctx->F_bond; d.status = ctx->status;

@@ -130,6 +130,12 @@ struct rbe_ctx {
     float4* f4;
     double4_32a* p4;
     int2* tm;
+    // per-atom records in caller order, written by the quantisation and
+    // permuted into s4, f4, p4, tm by the gather: the codes and FP32 charge,
+    // the wrapped FP64 position and charge, (type, molecule)
+    uint4* rec_s4;
+    double4_32a* rec_p4;
+    int2* rec_tm;
     int* perm;
     int* cell_of;
     int* slot;
@@ -200,7 +206,7 @@ struct rbe_ctx {
     int* inv_perm;        // [n] caller index -> sorted index of the rebuild
     int* skin_moved;      // [1] set when an atom moved more than skin/2 since the rebuild
     size_t skin_cap[5];
-    size_t cap_atoms[24];
+    size_t cap_atoms[28];
     size_t cap_adj[8];
 };
 
@@ -237,6 +243,9 @@ struct RepDev {
     float4* f4;
     double4_32a* p4;
     int2* tm;
+    uint4* rec_s4;
+    double4_32a* rec_p4;
+    int2* rec_tm;
     double* part_q;
     double* part_rbl;
     double* part_bond;
@@ -428,11 +437,11 @@ void prof_begin(rbe_ctx* ctx, int kid, cudaStream_t st);
 void prof_end(rbe_ctx* ctx, int kid, cudaStream_t st);
 
 // cells / sort (k_cells.cu)
-void launch_quantize_count(rbe_ctx* ctx, int n, const double* pos, const double* q, cudaStream_t st);
+void launch_quantize_count(rbe_ctx* ctx, int n, const double* pos, const double* q, const int32_t* type,
+                           const int32_t* mol, cudaStream_t st);
 void launch_scan(rbe_ctx* ctx, cudaStream_t st);
 long scan_tiles(long ncells);
-void launch_scatter_sort_gather(rbe_ctx* ctx, int n, const double* pos, const double* q,
-                                const int32_t* type, const int32_t* mol, cudaStream_t st);
+void launch_scatter_sort_gather(rbe_ctx* ctx, int n, cudaStream_t st);
 // pair kernel (k_rbl.cu)
 void launch_rbl(rbe_ctx* ctx, int n, uint64_t step, cudaStream_t st, bool adjoint = false);
 // adjoint (k_kspace.cu)
