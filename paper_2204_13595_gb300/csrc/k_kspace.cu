@@ -27,7 +27,7 @@ namespace {
 
 constexpr int TILE = 256;
 constexpr int TPB = 256;
-constexpr int FIN_TPB = 256;   // threads of the finalisation block (both paths: same reduction order)
+constexpr int FIN_TPB = 256;   // threads of the batched finalisation block (one replica each)
 
 __device__ __forceinline__ int inv_cdf(uint64_t u, const uint64_t* __restrict__ T, int M)
 {
@@ -350,53 +350,65 @@ __device__ double block_sum_col(const double* __restrict__ src, int nrow, int st
 }
 
 // totals: E[0..5], W[6..11], corr[12..14]
-// Each of the 23 sums (the rows of the pair kernel's [grid][12] partials,
-// the columns of the charge and k-term partials, the bond partials) is taken
-// in one fixed order: thread t sums rows t, t + blockDim, ..., then a warp
-// butterfly, then the warp results in warp order (the order of block_sum_col);
-// the sums share one block barrier.
+// The pair kernel's [grid][12] block partials are summed in RBE_FIN_CHUNKS
+// fixed chunks of consecutive rows (one warp per chunk: lane l takes rows
+// start + l, start + l + 32, ..., then a warp butterfly), so that the FP64
+// additions spread over many SMs (GB300's FP64 pipe is narrow); one warp then
+// sums the chunk results, the charge and k-term partials and the bond
+// partials the same way (lane-strided rows, butterfly).  The batched form
+// computes the same chunks with its block's warps and the same last warp sum,
+// so both paths add in one fixed order.
 constexpr int FIN_NV = RBE_NPART_RBL + RBE_NPART_Q + 7 + 1;
-__device__ __forceinline__ void finalize_body(int n, const RbeConsts& c, const double* __restrict__ part_rbl,
-                                              int grid_rbl, const double* __restrict__ part_q, int grid_q,
-                                              const double* __restrict__ kterms, const double* __restrict__ part_bond,
-                                              int grid_bond, double* __restrict__ totals, int* __restrict__ status)
+__device__ __forceinline__ void rbl_chunk_sum(int g, int R, const double* __restrict__ part_rbl,
+                                              double* __restrict__ out)
 {
-    __shared__ double sh[FIN_TPB / 32][FIN_NV];
-    double v[FIN_NV];
+    const int lane = threadIdx.x & 31;
+    const int cs = (R + RBE_FIN_CHUNKS - 1) / RBE_FIN_CHUNKS;
+    const int r0 = g * cs, r1 = min(R, r0 + cs);
+    double v[RBE_NPART_RBL];
 #pragma unroll
-    for (int q = 0; q < FIN_NV; ++q) v[q] = 0.0;
-#pragma unroll 4
-    for (int r = threadIdx.x; r < grid_rbl; r += blockDim.x) {
+    for (int q = 0; q < RBE_NPART_RBL; ++q) v[q] = 0.0;
+    for (int r = r0 + lane; r < r1; r += 32) {
         const double* row = part_rbl + (size_t)r * RBE_NPART_RBL;
 #pragma unroll
         for (int q = 0; q < RBE_NPART_RBL; ++q) v[q] += row[q];
     }
-#pragma unroll 4
-    for (int r = threadIdx.x; r < grid_q; r += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < RBE_NPART_RBL; ++q) v[q] = warp_sum(v[q]);
+    if (lane == 0)
+        for (int q = 0; q < RBE_NPART_RBL; ++q) out[g * RBE_NPART_RBL + q] = v[q];
+}
+
+// one warp: the totals from the chunk sums and the other partials
+__device__ __forceinline__ void finalize_warp(int n, const RbeConsts& c, const double* __restrict__ chunks,
+                                              const double* __restrict__ part_q, int grid_q,
+                                              const double* __restrict__ kterms, const double* __restrict__ part_bond,
+                                              int grid_bond, double* __restrict__ totals, int* __restrict__ status)
+{
+    const int lane = threadIdx.x & 31;
+    double v[FIN_NV];
+#pragma unroll
+    for (int q = 0; q < FIN_NV; ++q) v[q] = 0.0;
+    for (int g = lane; g < RBE_FIN_CHUNKS; g += 32) {
+#pragma unroll
+        for (int q = 0; q < RBE_NPART_RBL; ++q) v[q] += chunks[g * RBE_NPART_RBL + q];
+    }
+    for (int r = lane; r < grid_q; r += 32) {
 #pragma unroll
         for (int q = 0; q < RBE_NPART_Q; ++q) v[RBE_NPART_RBL + q] += part_q[(size_t)r * RBE_NPART_Q + q];
     }
-    for (int r = threadIdx.x; r < c.P; r += blockDim.x) {
+    for (int r = lane; r < c.P; r += 32) {
 #pragma unroll
         for (int q = 0; q < 7; ++q) v[RBE_NPART_RBL + RBE_NPART_Q + q] += kterms[(size_t)r * 7 + q];
     }
-    for (int r = threadIdx.x; r < grid_bond; r += blockDim.x) v[FIN_NV - 1] += part_bond[r];
+    for (int r = lane; r < grid_bond; r += 32) v[FIN_NV - 1] += part_bond[r];
 #pragma unroll
     for (int q = 0; q < FIN_NV; ++q) v[q] = warp_sum(v[q]);
-    if ((threadIdx.x & 31) == 0)
-        for (int q = 0; q < FIN_NV; ++q) sh[threadIdx.x >> 5][q] = v[q];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t[FIN_NV];
-        for (int q = 0; q < FIN_NV; ++q) {
-            double a = 0.0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a += sh[k][q];
-            t[q] = a;
-        }
-        const double* r = t;
-        const double* qs = t + RBE_NPART_RBL;
+    if (lane == 0) {
+        const double* r = v;
+        const double* qs = v + RBE_NPART_RBL;
         const double* kt = qs + RBE_NPART_Q;
-        const double eb = t[FIN_NV - 1];
+        const double eb = v[FIN_NV - 1];
         totals[0] = 0.5 * r[0];
         totals[1] = kt[0];
         totals[2] = -c.k_e * sqrt(c.alpha / 3.14159265358979323846) * qs[0];
@@ -412,13 +424,21 @@ __device__ __forceinline__ void finalize_body(int n, const RbeConsts& c, const d
     }
 }
 
-__global__ void __launch_bounds__(FIN_TPB) k_finalize(int n, RbeConsts c, const double* __restrict__ part_rbl, int grid_rbl,
-                                                  const double* __restrict__ part_q, int grid_q,
-                                                  const double* __restrict__ kterms,
-                                                  const double* __restrict__ part_bond, int grid_bond,
-                                                  double* __restrict__ totals, int* __restrict__ status)
+// RBE_FIN_CHUNKS blocks of one warp
+__global__ void __launch_bounds__(32) k_fin_chunks(int grid_rbl, const double* __restrict__ part_rbl,
+                                                   double* __restrict__ chunks)
 {
-    finalize_body(n, c, part_rbl, grid_rbl, part_q, grid_q, kterms, part_bond, grid_bond, totals, status);
+    rbl_chunk_sum(blockIdx.x, grid_rbl, part_rbl, chunks);
+}
+
+// one warp
+__global__ void __launch_bounds__(32) k_finalize(int n, RbeConsts c, const double* __restrict__ chunks,
+                                                 const double* __restrict__ part_q, int grid_q,
+                                                 const double* __restrict__ kterms,
+                                                 const double* __restrict__ part_bond, int grid_bond,
+                                                 double* __restrict__ totals, int* __restrict__ status)
+{
+    finalize_warp(n, c, chunks, part_q, grid_q, kterms, part_bond, grid_bond, totals, status);
 }
 
 template <bool MIXED>
@@ -673,9 +693,13 @@ __global__ void __launch_bounds__(TPB) k_bonded_b(const RepDev* __restrict__ R, 
 
 __global__ void __launch_bounds__(FIN_TPB) k_finalize_b(const RepDev* __restrict__ R)
 {
+    __shared__ double chunks[RBE_FIN_CHUNKS * RBE_NPART_RBL];
     const RepDev& d = R[blockIdx.x];
-    finalize_body(d.n, d.c, d.part_rbl, d.grid_rbl, d.part_q, d.grid_q, d.totals + 32, d.part_bond, d.grid_bond,
-                  d.totals, d.status);
+    for (int g = threadIdx.x >> 5; g < RBE_FIN_CHUNKS; g += FIN_TPB / 32) rbl_chunk_sum(g, d.grid_rbl, d.part_rbl, chunks);
+    __syncthreads();
+    if (threadIdx.x < 32)
+        finalize_warp(d.n, d.c, chunks, d.part_q, d.grid_q, d.totals + 32, d.part_bond, d.grid_bond, d.totals,
+                      d.status);
 }
 
 template <bool MIXED>
@@ -777,7 +801,8 @@ void launch_bonded(rbe_ctx* ctx, int n, const double* pos, cudaStream_t st)
 void launch_finalize(rbe_ctx* ctx, int n, cudaStream_t st)
 {
     prof_begin(ctx, RBE_K_FINAL, st);
-    k_finalize<<<1, FIN_TPB, 0, st>>>(n, ctx->c, ctx->part_rbl, ctx->grid_rbl, ctx->part_q, ctx->grid_q, ctx->totals + 32,
+    k_fin_chunks<<<RBE_FIN_CHUNKS, 32, 0, st>>>(ctx->grid_rbl, ctx->part_rbl, ctx->fin_part);
+    k_finalize<<<1, 32, 0, st>>>(n, ctx->c, ctx->fin_part, ctx->part_q, ctx->grid_q, ctx->totals + 32,
                                   ctx->part_bond, ctx->n_wmol > 0 ? ctx->grid_bond : 0, ctx->totals, ctx->status);
     prof_end(ctx, RBE_K_FINAL, st);
 }

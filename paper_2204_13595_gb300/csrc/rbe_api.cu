@@ -124,7 +124,7 @@ void refresh_consts(rbe_ctx* ctx)
 
 void free_dev(rbe_ctx* ctx)
 {
-    void* ptrs[] = {ctx->cis, ctx->skey, ctx->scan_tmp, ctx->sx_of, ctx->F_lang, ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->rec_s4, ctx->rec_p4, ctx->rec_tm, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
+    void* ptrs[] = {ctx->cis, ctx->skey, ctx->scan_tmp, ctx->sx_of, ctx->F_lang, ctx->kpool_buf, ctx->s4, ctx->f4, ctx->p4, ctx->tm, ctx->rec_s4, ctx->rec_p4, ctx->rec_tm, ctx->fin_part, ctx->perm, ctx->cell_of, ctx->slot, ctx->cell_count, ctx->cell_start,
                     ctx->F_real, ctx->F_bond, ctx->part_rbl, ctx->part_q, ctx->part_bond, ctx->kT, ctx->km, ctx->kv,
                     ctx->rho_part, ctx->rho, ctx->totals, ctx->status, ctx->lj, ctx->dbg_ncore, ctx->dbg_nshell,
                     ctx->dbg_core, ctx->dbg_batch, ctx->dbg_unstaged, ctx->h_pos, ctx->h_q, ctx->h_type, ctx->h_mol, ctx->h_F,
@@ -136,7 +136,7 @@ void free_dev(rbe_ctx* ctx)
     for (int k = 0; k < 5; ++k) ctx->skin_cap[k] = 0;
     ctx->skin_valid = 0;
     ctx->s4 = nullptr; ctx->f4 = nullptr; ctx->p4 = nullptr; ctx->tm = nullptr; ctx->perm = nullptr; ctx->cell_of = nullptr;
-    ctx->rec_s4 = nullptr; ctx->rec_p4 = nullptr; ctx->rec_tm = nullptr;
+    ctx->rec_s4 = nullptr; ctx->rec_p4 = nullptr; ctx->rec_tm = nullptr; ctx->fin_part = nullptr;
     ctx->slot = nullptr; ctx->cell_count = nullptr; ctx->cell_start = nullptr; ctx->F_real = nullptr;
     ctx->F_bond = nullptr; ctx->part_rbl = nullptr; ctx->part_q = nullptr; ctx->part_bond = nullptr;
     ctx->kT = nullptr; ctx->km = nullptr; ctx->kv = nullptr; ctx->rho_part = nullptr; ctx->rho = nullptr;
@@ -421,6 +421,7 @@ int ensure(rbe_ctx* ctx, int n)
     if ((rc = grow(ctx, &ctx->rec_s4, &ctx->cap_atoms[23], n))) return rc;
     if ((rc = grow(ctx, &ctx->rec_p4, &ctx->cap_atoms[24], n))) return rc;
     if ((rc = grow(ctx, &ctx->rec_tm, &ctx->cap_atoms[25], n))) return rc;
+    if ((rc = grow(ctx, &ctx->fin_part, &ctx->cap_atoms[26], (size_t)RBE_FIN_CHUNKS * RBE_NPART_RBL))) return rc;
     if ((rc = grow(ctx, &ctx->perm, &ctx->cap_atoms[3], n))) return rc;
     if ((rc = grow(ctx, &ctx->cell_of, &ctx->cap_atoms[4], n))) return rc;
     if ((rc = grow(ctx, &ctx->slot, &ctx->cap_atoms[5], n))) return rc;

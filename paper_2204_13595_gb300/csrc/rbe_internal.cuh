@@ -32,6 +32,7 @@
 #define RBE_BLOCKS_STORED 3
 #endif
 #define RBE_NPART_RBL 12         // Ec, Elj, Ex, W[6], Fsum[3]
+#define RBE_FIN_CHUNKS 64        // chunks of the pair kernel's block partials in the finalisation
 #define RBE_NPART_Q 3            // sum q^2, sum q, sum |q|
 #define RBE_RBL_PAIR_CARVE 416   // words of the per-warp shell buffer the two-atom pair path uses beyond a core list
 
@@ -147,6 +148,7 @@ struct rbe_ctx {
     double* F_real;      // [3n] sorted (FP32 [3n] on the mixed path)
     double* F_bond;      // [3n] caller order
     double* part_rbl;    // [grid_rbl * 12]
+    double* fin_part;    // [RBE_FIN_CHUNKS * 12] chunk sums of part_rbl
     double* part_q;      // [grid_q * 3]
     double* part_bond;   // [grid_bond]
     int grid_rbl, grid_q, grid_rho, grid_bond;
