@@ -240,7 +240,8 @@ __device__ __forceinline__ void rho_sum_body(int bx, int nblk, const RbeConsts& 
     const int l = bx * (TPB / 32) + (threadIdx.x >> 5);
     if (l >= c.P) return;
     double re = 0.0, im = 0.0;
-    for (int b = lane; b < nblk; b += 32) {
+#pragma unroll 8
+    for (int b = lane; b < nblk; b += 32) {     // (unrolled: several partials' loads in flight)
         double2 v = part[(size_t)b * c.P + l];
         re += v.x;
         im += v.y;
@@ -389,14 +390,18 @@ __device__ __forceinline__ void finalize_warp(int n, const RbeConsts& c, const d
     double v[FIN_NV];
 #pragma unroll
     for (int q = 0; q < FIN_NV; ++q) v[q] = 0.0;
+    // (the loops are unrolled so that several rows' loads are in flight)
+#pragma unroll
     for (int g = lane; g < RBE_FIN_CHUNKS; g += 32) {
 #pragma unroll
         for (int q = 0; q < RBE_NPART_RBL; ++q) v[q] += chunks[g * RBE_NPART_RBL + q];
     }
+#pragma unroll 8
     for (int r = lane; r < grid_q; r += 32) {
 #pragma unroll
         for (int q = 0; q < RBE_NPART_Q; ++q) v[RBE_NPART_RBL + q] += part_q[(size_t)r * RBE_NPART_Q + q];
     }
+#pragma unroll 4
     for (int r = lane; r < c.P; r += 32) {
 #pragma unroll
         for (int q = 0; q < 7; ++q) v[RBE_NPART_RBL + RBE_NPART_Q + q] += kterms[(size_t)r * 7 + q];

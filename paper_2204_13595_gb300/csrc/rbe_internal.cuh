@@ -340,7 +340,15 @@ __device__ __forceinline__ void wrap_fixed(double x, double invL, double L, doub
     double t = __dmul_rn(x, invL);
     double f = __dsub_rn(t, floor(t));
     if (f >= 1.0) f = 0.0;
-    s = (uint32_t)(unsigned long long)__dmul_rn(f, 4294967296.0);
+    // s = floor(f 2^32) for 0 <= f < 1, from the bits of f: f 2^32 is exact,
+    // so its integer part is the 53-bit significand shifted right by 20 - e
+    // (e = f's exponent <= -1; 0 once the shift reaches 64, which covers f = 0
+    // and subnormal f).  Integer instructions instead of an FP64 multiply and
+    // conversion: GB300's FP64 pipe is the bound of this arithmetic.
+    const unsigned long long u = (unsigned long long)__double_as_longlong(f);
+    const int sh = 20 - ((int)((u >> 52) & 0x7FFull) - 1023);
+    const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    s = sh < 64 ? (uint32_t)(m >> sh) : 0u;
     xw = __dmul_rn(f, L);
 }
 
