@@ -250,3 +250,42 @@ def test_mixed_pair_energy_within_erfc_error_bound():
         worst = max(worst, err / bound)
         assert err <= bound, (r, err, bound)
     print(f"mixed pair energy: worst error / bound {worst:.3f}")
+
+
+def test_fp64_pair_energy_matches_erfc():
+    """The FP64 pair kernel evaluates erfc and erf by W. J. Cody's rational
+    Chebyshev approximations (Math. Comp. 23, 1969) from the e^{-x^2} of the
+    force term.  One +1/-1 pair per system at 64 distances from 0.3 to r_s,
+    once as an ordinary pair and once as a same-molecule (excluded) pair:
+    the FP64 real-space energy must equal k_e q_i q_j erfc(sqrt(alpha) r)/r
+    (math.erfc), and the exclusion energy -k_e q_i q_j erf(sqrt(alpha) r)/r
+    (math.erf), within 5e-15 relative plus the condition number of the
+    function (1 + 2 x^2 for erfc, at most 1 for erf) times the relative
+    error of the distance itself (the wrapped FP64 positions carry a few ulp
+    of coordinates up to 12 A); the arguments cover all three of Cody's
+    intervals (x = sqrt(alpha) r up to 6.1 with alpha = 1.5)."""
+    import math
+    worst = 0.0
+    for alpha in (None, 1.5):
+        for r in np.linspace(0.3, systems.electrolyte(n=2, L=20.0, seed=1).r_s * 0.999, 64):
+            for excl in (False, True):
+                s = systems.electrolyte(n=2, L=20.0, seed=1)
+                if alpha is not None:
+                    s.alpha = alpha
+                s.pos = np.array([[3.0, 4.0, 5.0], [3.0 + r * 0.6, 4.0 + r * 0.8, 5.0]])
+                s.q = np.array([1.0, -1.0])
+                s.type = np.zeros(2, np.int32)
+                s.mol = np.array([0, 0], np.int32) if excl else None
+                out = gpu_forces(s, 1, precision=rbe.FP64)
+                assert out["status"] == 0
+                x = math.sqrt(s.alpha) * r
+                if excl:
+                    exact, got = -s.k_e * s.q[0] * s.q[1] * math.erf(x) / r, out["E"][rbe.E_EXCL]
+                else:
+                    exact, got = s.k_e * s.q[0] * s.q[1] * math.erfc(x) / r, out["E"][rbe.E_REAL]
+                rel = abs(got - exact) / abs(exact)
+                cond = 1.0 if excl else 1.0 + 2.0 * x * x
+                bound = 5e-15 + cond * (4e-16 + 6e-15 / r)
+                worst = max(worst, rel / bound)
+                assert rel < bound, (alpha, r, excl, rel, bound)
+    print(f"FP64 pair energy: worst relative error / bound {worst:.3f}")
