@@ -536,10 +536,29 @@ int forces_device(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const d
         launch_scan(ctx, st);
         launch_scatter_sort_gather(ctx, n, st);
     }
-    launch_ksample(ctx, step, st);
-    launch_rho(ctx, n, st);
+    // the k samples and structure factors need only the sorted arrays: on an
+    // auxiliary stream they run beside the pair kernel, whose last wave
+    // leaves SMs idle that they can fill; joined before the finalisation
+    bool aux = RBE_OVERLAP_KSPACE != 0;
+    if (aux && !ctx->st_aux) {
+        if (cudaStreamCreateWithFlags(&ctx->st_aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(ctx, RBE_ECUDA, "cannot create the auxiliary stream");
+        }
+    }
+    cudaStream_t sk = aux ? ctx->st_aux : st;
+    if (aux) {
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, st));
+        CUDA_TRY(ctx, cudaStreamWaitEvent(sk, ctx->ev_fork, 0));
+    }
+    launch_ksample(ctx, step, sk);
+    launch_rho(ctx, n, sk);
+    if (aux) CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, sk));
     if (skin) launch_rbl_stored(ctx, n, step, st);
     else launch_rbl(ctx, n, step, st);
+    if (aux) CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0));
     if (ctx->n_wmol > 0) launch_bonded(ctx, n, pos, st);
     launch_finalize(ctx, n, st);
     launch_kforce(ctx, n, F, st);
@@ -1135,6 +1154,11 @@ void rbe_destroy(rbe_ctx* ctx)
         for (auto& r : ps->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (auto e : ps->pool) cudaEventDestroy(e);
         free_dev(ctx);
+        if (ctx->st_aux) {
+            cudaEventDestroy(ctx->ev_fork);
+            cudaEventDestroy(ctx->ev_join);
+            cudaStreamDestroy(ctx->st_aux);
+        }
     }
     delete (ProfState*)ctx->prof;
     free(ctx);

@@ -24,6 +24,12 @@
 #ifndef RBE_BLOCKS_RBL
 #define RBE_BLOCKS_RBL 2         // resident blocks per SM the pair kernel is sized for
 #endif
+#ifndef RBE_OVERLAP_KSPACE
+// 1: a force evaluation runs the k sampling and the structure factors on an
+// auxiliary stream beside the pair kernel (they are independent until the
+// finalisation); 0: everything on the caller's stream
+#define RBE_OVERLAP_KSPACE 1
+#endif
 #ifndef RBE_BLOCKS_STORED
 // resident blocks per SM of the stored-list (Verlet skin) pair kernel: it
 // stages no stencil, so three blocks fit in shared memory; its register
@@ -137,6 +143,10 @@ struct rbe_ctx {
     uint4* rec_s4;
     double4_32a* rec_p4;
     int2* rec_tm;
+    // auxiliary stream of the Fourier-space kernels and its fork/join events
+    // (created on first use)
+    cudaStream_t st_aux;
+    cudaEvent_t ev_fork, ev_join;
     int* perm;
     int* cell_of;
     int* slot;
