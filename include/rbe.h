@@ -221,7 +221,10 @@ int rbe_get_kspace(rbe_ctx* ctx, int32_t* m, double* rho, void* cuda_stream);
 int rbe_get_info(rbe_ctx* ctx, double* out, int nout);
 
 /* Kernel timing: when on, every launch is bracketed by CUDA events on its
- * stream.  rbe_get_profile waits for cuda_stream and returns, per kernel id
+ * stream, and a force evaluation runs all its kernels on the caller's stream
+ * (otherwise the k sampling and structure factors run on an auxiliary stream
+ * beside the pair kernel, where their event intervals would include waits
+ * for SMs).  rbe_get_profile waits for cuda_stream and returns, per kernel id
  * (RBE_K_*), the summed milliseconds and the number of launches since the
  * last reset (reset = 1 clears them afterwards). */
 #define RBE_K_QUANTIZE 0

@@ -538,8 +538,11 @@ int forces_device(rbe_ctx* ctx, uint64_t step, int n, const double* pos, const d
     }
     // the k samples and structure factors need only the sorted arrays: on an
     // auxiliary stream they run beside the pair kernel, whose last wave
-    // leaves SMs idle that they can fill; joined before the finalisation
-    bool aux = RBE_OVERLAP_KSPACE != 0;
+    // leaves SMs idle that they can fill; joined before the finalisation.
+    // With per-kernel profiling on they stay on the caller's stream: the
+    // event interval of a kernel on a concurrent stream includes its wait for
+    // SMs held by the pair kernel
+    bool aux = RBE_OVERLAP_KSPACE != 0 && !ctx->profiling;
     if (aux && !ctx->st_aux) {
         if (cudaStreamCreateWithFlags(&ctx->st_aux, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
