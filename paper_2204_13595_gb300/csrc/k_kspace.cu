@@ -476,6 +476,7 @@ __device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, c
         }
     }
     double f[3] = {0.0, 0.0, 0.0};
+    float fm[3] = {0.f, 0.f, 0.f};        // mixed: the Fourier sums in FP32
     for (int l0 = 0; l0 < c.P; l0 += KT) {
         const int cnt = min(KT, c.P - l0);
         __syncthreads();
@@ -507,7 +508,7 @@ __device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, c
                     float h = cs * kk.w - sn * __int_as_float(m.w);
                     g[0] += h * kk.x; g[1] += h * kk.y; g[2] += h * kk.z;
                 }
-                for (int a = 0; a < 3; ++a) f[a] += (double)g[a];
+                for (int a = 0; a < 3; ++a) fm[a] += g[a];
             } else {
                 for (int k = 0; k < cnt; ++k) {
                     const int4 m = sm[k];
@@ -523,7 +524,21 @@ __device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, c
         }
     }
     if (!act) return;
-    const double qi = MIXED ? (double)p4[i].w : pi.w;
+    if (MIXED) {
+        // the mixed forces are combined in FP32 (F_real, the Fourier sums and
+        // the charge are FP32 already) and widened once: the FP64 pipe of
+        // this part is narrow, and the result keeps the mixed path's bar
+        const float qf = __uint_as_float(si.w);
+        const int gi = perm[i];
+        const float* Fr = reinterpret_cast<const float*>(F_real) + 3 * (size_t)i;
+        for (int a = 0; a < 3; ++a) {
+            double v = (double)(Fr[a] - (float)totals[12 + a] - qf * fm[a]);
+            if (gi < n_bonded_atoms) v += F_bond[3 * (size_t)gi + a];
+            F[3 * (size_t)gi + a] = v;
+        }
+        return;
+    }
+    const double qi = pi.w;
     const int gi = perm[i];
     for (int a = 0; a < 3; ++a) {
         double fr = MIXED ? (double)reinterpret_cast<const float*>(F_real)[3 * (size_t)i + a] : F_real[3 * (size_t)i + a];
