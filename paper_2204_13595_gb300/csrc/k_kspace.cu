@@ -139,6 +139,44 @@ __device__ __forceinline__ void cis_fp64(uint32_t ph, double dk, const double2* 
     sn = e.y * c + e.x * sx;
 }
 
+// 64-bit fixed-point code floor(f 2^64) of a fraction 0 <= f < 1, from its
+// bits: f 2^64 = significand 2^(e + 12) for the exponent e <= -1 (exact; a
+// fraction below 2^-12 loses only bits below 2^-64, and 0 or a subnormal
+// gives 0).
+__device__ __forceinline__ uint64_t code64(double f)
+{
+    const uint64_t u = (uint64_t)__double_as_longlong(f);
+    const int e = (int)((u >> 52) & 0x7FFull) - 1023;
+    const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = e + 12;
+    return sh >= 0 ? (m << sh) : (-sh < 64 ? (m >> -sh) : 0ull);
+}
+
+// The 64-bit code of a wrapped FP64 coordinate 0 <= xw < L (the fraction
+// xw / L, taken as xw * (1/L) and folded to [0, 1))
+__device__ __forceinline__ uint64_t code64_of(double xw, double invL)
+{
+    double f = xw * invL;
+    if (f >= 1.0) f -= 1.0;
+    return code64(f);
+}
+
+// FP64 e^{i theta} for theta = 2 pi ph / 2^64 (ph = m . S mod 2^64 of the
+// 64-bit codes, exact in integer arithmetic): the table entry of the top 12
+// bits times a Taylor polynomial of the remaining 52 bits' angle, |x| <
+// 2 pi / 4096 (cos to x^4, sin to x^5: the first omitted terms are below
+// 2e-20).  No residual correction: the phase is exact to 2^-64 of a turn.
+__device__ __forceinline__ void cis_fp64_64(uint64_t ph, const double2* __restrict__ tab, double& cs, double& sn)
+{
+    const double2 e = __ldg(tab + (ph >> 52));
+    const double x = (double)(ph & 0xFFFFFFFFFFFFFull) * 3.4061215800865545e-19;     // 2 pi / 2^64
+    const double x2 = x * x;
+    const double c = fma(x2, fma(x2, 1.0 / 24.0, -0.5), 1.0);
+    const double sx = fma(x * x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
+    cs = e.x * c - e.y * sx;
+    sn = e.y * c + e.x * sx;
+}
+
 // Residual delta = x - s L 2^-32 of a wrapped FP64 coordinate and its code.
 __device__ __forceinline__ double fixed_residual(double xw, uint32_t s, double Lq)
 {
@@ -152,8 +190,8 @@ __device__ __forceinline__ void rho_body(int bx, int n, int chunk, const RbeCons
                                          const double4_32a* __restrict__ kv, const double2* __restrict__ cis,
                                          double2* __restrict__ part)
 {
-    __shared__ double4_32a tile_d[MIXED ? 1 : TILE];     // FP64: residuals (dx, dy, dz) and q
-    __shared__ uint4 tile_u[TILE];
+    __shared__ double4_32a tile_d[MIXED ? 1 : TILE];     // FP64: 64-bit codes (bit patterns) and q
+    __shared__ uint4 tile_u[MIXED ? TILE : 1];           // mixed: 32-bit codes and FP32 q
     const int b0 = bx * chunk;
     const int b1 = min(n, b0 + chunk);
     for (int l0 = 0; l0 < c.P; l0 += blockDim.x) {
@@ -165,13 +203,14 @@ __device__ __forceinline__ void rho_body(int bx, int n, int chunk, const RbeCons
             const int cnt = min(TILE, b1 - t0);
             __syncthreads();
             for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-                const uint4 su = s4[t0 + k];
-                tile_u[k] = su;
-                if (!MIXED) {
+                if (MIXED) {
+                    tile_u[k] = s4[t0 + k];
+                } else {
+                    // the 64-bit codes (as bit patterns) and the charge
                     const double4_32a p = p4[t0 + k];
-                    const double Lq = c.L * 2.3283064365386963e-10;
-                    tile_d[k] = make_double4_32a(fixed_residual(p.x, su.x, Lq), fixed_residual(p.y, su.y, Lq),
-                                                 fixed_residual(p.z, su.z, Lq), p.w);
+                    tile_d[k] = make_double4_32a(__longlong_as_double((long long)code64_of(p.x, c.invL)),
+                                                 __longlong_as_double((long long)code64_of(p.y, c.invL)),
+                                                 __longlong_as_double((long long)code64_of(p.z, c.invL)), p.w);
                 }
             }
             __syncthreads();
@@ -192,14 +231,15 @@ __device__ __forceinline__ void rho_body(int bx, int n, int chunk, const RbeCons
                     re += (double)fre;
                     im += (double)fim;
                 } else {
-                    const double4_32a kk = act ? kv[l] : make_double4_32a(0, 0, 0, 0);
-                    const uint32_t mx = (uint32_t)m.x, my = (uint32_t)m.y, mz = (uint32_t)m.z;
+                    const uint64_t mx = (uint64_t)(long long)m.x, my = (uint64_t)(long long)m.y,
+                                   mz = (uint64_t)(long long)m.z;
                     for (int k = 0; k < cnt; ++k) {
-                        const uint4 su = tile_u[k];
                         const double4_32a d = tile_d[k];
-                        const uint32_t ph = mx * su.x + my * su.y + mz * su.z;
+                        const uint64_t ph = mx * (uint64_t)__double_as_longlong(d.x) +
+                                            my * (uint64_t)__double_as_longlong(d.y) +
+                                            mz * (uint64_t)__double_as_longlong(d.z);
                         double sn, cs;
-                        cis_fp64(ph, fma(kk.x, d.x, fma(kk.y, d.y, kk.z * d.z)), cis, cs, sn);
+                        cis_fp64_64(ph, cis, cs, sn);
                         re += d.w * cs;
                         im += d.w * sn;
                     }
@@ -464,15 +504,14 @@ __device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, c
     const bool act = i < n;
     uint4 si = make_uint4(0, 0, 0, 0);
     double4_32a pi = make_double4_32a(0, 0, 0, 0);
-    double dxi = 0.0, dyi = 0.0, dzi = 0.0;     // FP64: residuals of the fixed-point code
+    uint64_t sxi = 0, syi = 0, szi = 0;         // FP64: 64-bit codes of the position
     if (act) {
         si = s4[i];
         if (!MIXED) {
             pi = p4[i];
-            const double Lq = c.L * 2.3283064365386963e-10;
-            dxi = fixed_residual(pi.x, si.x, Lq);
-            dyi = fixed_residual(pi.y, si.y, Lq);
-            dzi = fixed_residual(pi.z, si.z, Lq);
+            sxi = code64_of(pi.x, c.invL);
+            syi = code64_of(pi.y, c.invL);
+            szi = code64_of(pi.z, c.invL);
         }
     }
     double f[3] = {0.0, 0.0, 0.0};
@@ -513,9 +552,10 @@ __device__ __forceinline__ void kforce_body(int bx, int n, const RbeConsts& c, c
                 for (int k = 0; k < cnt; ++k) {
                     const int4 m = sm[k];
                     const double4_32a kk = sk_d[k];
-                    const uint32_t ph = (uint32_t)m.x * si.x + (uint32_t)m.y * si.y + (uint32_t)m.z * si.z;
+                    const uint64_t ph = (uint64_t)(long long)m.x * sxi + (uint64_t)(long long)m.y * syi +
+                                        (uint64_t)(long long)m.z * szi;
                     double sn, cs;
-                    cis_fp64(ph, fma(kk.x, dxi, fma(kk.y, dyi, kk.z * dzi)), cis, cs, sn);
+                    cis_fp64_64(ph, cis, cs, sn);
                     const double2 ab = sab_d[k];
                     const double h = cs * ab.x - sn * ab.y;
                     f[0] += h * kk.x; f[1] += h * kk.y; f[2] += h * kk.z;
