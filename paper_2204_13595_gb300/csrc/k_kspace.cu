@@ -123,18 +123,18 @@ __global__ void k_kpool_build(uint64_t seed, int M, int K, int burn, const doubl
 // FP64 phase factor e^{i theta}, theta = k . x, from the exact 32-bit phase
 // ph = m . s mod 2^32 of the fixed-point coordinates (theta = 2 pi ph / 2^32
 // + k . delta, delta = x - s L / 2^32 the sub-quantum residual of the
-// position, |delta| < L 2^-32): a table of e^{2 pi i j / 4096} for the top 12
-// bits of ph times a Taylor polynomial of the rest, |x| < 2 pi / 4096 + |k|
-// |delta| < 1.6e-3 (cos to x^4, sin to x^5: the first omitted terms are below
-// 2e-20).  About half the FP64 work of a general sincos.
+// position, |delta| < L 2^-32): a table of e^{2 pi i j / 65536} for the top
+// 16 bits of ph times a Taylor polynomial of the rest, |x| < 2 pi / 65536 +
+// |k| |delta| < 1e-4 (cos to x^2, sin to x^3: the first omitted terms are
+// below 5e-18).  A fraction of the FP64 work of a general sincos.
 __device__ __forceinline__ void cis_fp64(uint32_t ph, double dk, const double2* __restrict__ tab, double& cs,
                                          double& sn)
 {
-    const double2 e = __ldg(tab + (ph >> 20));
-    const double x = fma((double)(ph & 0xFFFFFu), 6.283185307179586 * 2.3283064365386963e-10, dk);
+    const double2 e = __ldg(tab + (ph >> 16));
+    const double x = fma((double)(ph & 0xFFFFu), 6.283185307179586 * 2.3283064365386963e-10, dk);
     const double x2 = x * x;
-    const double c = fma(x2, fma(x2, 1.0 / 24.0, -0.5), 1.0);
-    const double sx = fma(x * x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
+    const double c = fma(x2, -0.5, 1.0);
+    const double sx = fma(x * x2, -1.0 / 6.0, x);
     cs = e.x * c - e.y * sx;
     sn = e.y * c + e.x * sx;
 }
@@ -162,17 +162,19 @@ __device__ __forceinline__ uint64_t code64_of(double xw, double invL)
 }
 
 // FP64 e^{i theta} for theta = 2 pi ph / 2^64 (ph = m . S mod 2^64 of the
-// 64-bit codes, exact in integer arithmetic): the table entry of the top 12
-// bits times a Taylor polynomial of the remaining 52 bits' angle, |x| <
-// 2 pi / 4096 (cos to x^4, sin to x^5: the first omitted terms are below
-// 2e-20).  No residual correction: the phase is exact to 2^-64 of a turn.
+// 64-bit codes, exact in integer arithmetic): the table entry of the top 16
+// bits times a Taylor polynomial of the remaining 48 bits' angle, |x| <
+// 2 pi / 65536 (cos to x^2, sin to x^3: the first omitted terms are below
+// 4e-18).  No residual correction: the phase is exact to 2^-64 of a turn.
+// (The 1 MB table is read from L2: it costs less than the two FP64
+// operations per phase that a 4,096-entry table's longer series took.)
 __device__ __forceinline__ void cis_fp64_64(uint64_t ph, const double2* __restrict__ tab, double& cs, double& sn)
 {
-    const double2 e = __ldg(tab + (ph >> 52));
-    const double x = (double)(ph & 0xFFFFFFFFFFFFFull) * 3.4061215800865545e-19;     // 2 pi / 2^64
+    const double2 e = __ldg(tab + (ph >> 48));
+    const double x = (double)(ph & 0xFFFFFFFFFFFFull) * 3.4061215800865545e-19;     // 2 pi / 2^64
     const double x2 = x * x;
-    const double c = fma(x2, fma(x2, 1.0 / 24.0, -0.5), 1.0);
-    const double sx = fma(x * x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
+    const double c = fma(x2, -0.5, 1.0);
+    const double sx = fma(x * x2, -1.0 / 6.0, x);
     cs = e.x * c - e.y * sx;
     sn = e.y * c + e.x * sx;
 }
@@ -258,13 +260,13 @@ __global__ void k_rho(int n, int chunk, RbeConsts c, const uint4* __restrict__ s
     rho_body<MIXED>(blockIdx.x, n, chunk, c, s4, p4, km, kv, cis, part);
 }
 
-// Table of e^{2 pi i j / 4096}, j = 0..4095 (cos, sin), for cis_fp64.
+// Table of e^{2 pi i j / 65536}, j = 0..65535 (cos, sin), for cis_fp64 and cis_fp64_64.
 __global__ void k_cis_table(double2* __restrict__ tab)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= 4096) return;
+    if (j >= 65536) return;
     double sn, cs;
-    sincospi((double)j / 2048.0, &sn, &cs);
+    sincospi((double)j / 32768.0, &sn, &cs);
     tab[j] = make_double2(cs, sn);
 }
 
@@ -826,7 +828,7 @@ void launch_kpool_build(rbe_ctx* ctx, const double* w, const double* q, const ui
 
 void launch_cis_table(double2* tab, cudaStream_t st)
 {
-    k_cis_table<<<16, 256, 0, st>>>(tab);
+    k_cis_table<<<256, 256, 0, st>>>(tab);
 }
 
 void launch_rho(rbe_ctx* ctx, int n, cudaStream_t st)

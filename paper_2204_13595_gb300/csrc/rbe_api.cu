@@ -299,7 +299,7 @@ int ensure(rbe_ctx* ctx, int n)
         if ((rc = dev_alloc(ctx, &ctx->km, ctx->c.P))) return rc;
         if ((rc = dev_alloc(ctx, &ctx->kv, ctx->c.P))) return rc;
         if ((rc = dev_alloc(ctx, &ctx->rho, ctx->c.P))) return rc;
-        if ((rc = dev_alloc(ctx, &ctx->cis, 4096))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->cis, 65536))) return rc;
         launch_cis_table(ctx->cis, 0);
         CUDA_TRY(ctx, cudaDeviceSynchronize());
         if ((rc = dev_alloc(ctx, &ctx->totals, 32 + 7 * (size_t)ctx->c.P))) return rc;

@@ -166,7 +166,7 @@ struct rbe_ctx {
     int4* km;            // [P] m
     double4_32a* kv;         // [P] kx, ky, kz, c_l
     double2* rho_part;   // [grid_rho * P]
-    double2* cis;        // [4096] e^{2 pi i j / 4096}: FP64 phase table
+    double2* cis;        // [65536] e^{2 pi i j / 65536}: FP64 phase table
     double2* rho;        // [P]
     double* totals;      // [32]: E[6], W[6], corr[3], spare
     int* status;         // [RBE_STW_WORDS] status bits, needed capacities, halt code
