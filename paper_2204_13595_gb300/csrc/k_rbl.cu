@@ -243,29 +243,18 @@ __device__ __forceinline__ float erfc_hastings(float x, float ex2)
 // taken (its rounding, x^2 <= 16 here, stays below 2e-15 relative).
 // Relative error below 4e-15 against the C library on [0, 6]
 // (test_fp64_pair_energy_matches_erfc).
+//
+// The first two intervals share one Horner chain of eight steps whose
+// coefficients each lane selects by its interval: R1's shorter numerator and
+// denominator are padded with leading zero coefficients (the chain stays at
+// exactly 0 until R1's first coefficient enters, so R1 is evaluated in its own
+// order), and the final factor is x on the first interval, e^{-x^2} on the
+// second.  A warp whose pairs straddle x = 0.46875 (a water molecule's own
+// O-H and H-H pairs beside the others) then evaluates one rational function
+// instead of both; selecting a coefficient is integer work, off the FP64 pipe.
 __device__ __forceinline__ double erf_cody(double x, double ex2, bool want_erf)
 {
-    if (x <= 0.46875) {
-        const double y = x * x;
-        double num = 1.85777706184603153e-1 * y, den = y;
-        num = (num + 3.16112374387056560e00) * y; den = (den + 2.36012909523441209e01) * y;
-        num = (num + 1.13864154151050156e02) * y; den = (den + 2.44024637934444173e02) * y;
-        num = (num + 3.77485237685302021e02) * y; den = (den + 1.28261652607737228e03) * y;
-        const double e = x * (num + 3.20937758913846947e03) / (den + 2.84423683343917062e03);
-        return want_erf ? e : 1.0 - e;
-    }
-    double r;
-    if (x <= 4.0) {
-        double num = 2.15311535474403846e-8 * x, den = x;
-        num = (num + 5.64188496988670089e-1) * x; den = (den + 1.57449261107098347e01) * x;
-        num = (num + 8.88314979438837594e00) * x; den = (den + 1.17693950891312499e02) * x;
-        num = (num + 6.61191906371416295e01) * x; den = (den + 5.37181101862009858e02) * x;
-        num = (num + 2.98635138197400131e02) * x; den = (den + 1.62138957456669019e03) * x;
-        num = (num + 8.81952221241769090e02) * x; den = (den + 3.29079923573345963e03) * x;
-        num = (num + 1.71204761263407058e03) * x; den = (den + 4.36261909014324716e03) * x;
-        num = (num + 2.05107837782607147e03) * x; den = (den + 3.43936767414372164e03) * x;
-        r = ex2 * (num + 1.23033935479799725e03) / (den + 1.23033935480374942e03);
-    } else {
+    if (x > 4.0) {
         const double y = 1.0 / (x * x);
         double num = 1.63153871373020978e-2 * y, den = y;
         num = (num + 3.05326634961232344e-1) * y; den = (den + 2.56852019228982242e00) * y;
@@ -273,9 +262,47 @@ __device__ __forceinline__ double erf_cody(double x, double ex2, bool want_erf)
         num = (num + 1.25781726111229246e-1) * y; den = (den + 5.27905102951428412e-1) * y;
         num = (num + 1.60837851487422766e-2) * y; den = (den + 6.05183413124413191e-2) * y;
         const double t = y * (num + 6.58749161529837803e-4) / (den + 2.33520497626869185e-3);
-        r = ex2 * (0.56418958354775628695 - t) / x;
+        const double r = ex2 * (0.56418958354775628695 - t) / x;
+        return want_erf ? 1.0 - r : r;
     }
-    return want_erf ? 1.0 - r : r;
+    const bool lo = x <= 0.46875;
+    const double v = lo ? x * x : x;
+    // numerator: R2's nine coefficients; R1's five after four zeros
+    double num = (lo ? 0.0 : 2.15311535474403846e-8) * v;
+    num = (num + (lo ? 0.0 : 5.64188496988670089e-1)) * v;
+    num = (num + (lo ? 0.0 : 8.88314979438837594e00)) * v;
+    num = (num + (lo ? 0.0 : 6.61191906371416295e01)) * v;
+    num = (num + (lo ? 1.85777706184603153e-1 : 2.98635138197400131e02)) * v;
+    num = (num + (lo ? 3.16112374387056560e00 : 8.81952221241769090e02)) * v;
+    num = (num + (lo ? 1.13864154151050156e02 : 1.71204761263407058e03)) * v;
+    num = (num + (lo ? 3.77485237685302021e02 : 2.05107837782607147e03)) * v;
+    num += lo ? 3.20937758913846947e03 : 1.23033935479799725e03;
+    // denominator: monic, R2's eight further coefficients; R1's four after zeros
+    double den = (lo ? 0.0 : 1.0) * v;
+    den = (den + (lo ? 0.0 : 1.57449261107098347e01)) * v;
+    den = (den + (lo ? 0.0 : 1.17693950891312499e02)) * v;
+    den = (den + (lo ? 0.0 : 5.37181101862009858e02)) * v;
+    den = (den + (lo ? 1.0 : 1.62138957456669019e03)) * v;
+    den = (den + (lo ? 2.36012909523441209e01 : 3.29079923573345963e03)) * v;
+    den = (den + (lo ? 2.44024637934444173e02 : 4.36261909014324716e03)) * v;
+    den = (den + (lo ? 1.28261652607737228e03 : 3.43936767414372164e03)) * v;
+    den += lo ? 2.84423683343917062e03 : 1.23033935480374942e03;
+    // erf = x R1 on the first interval, erfc = e^{-x^2} R2 on the second
+    const double q = (lo ? x : ex2) * num / den;
+    return lo == want_erf ? q : 1.0 - q;
+}
+
+// Minimum-image shift (-L, 0 or +L) of the FP64 coordinate difference
+// x_j - x_i of two wrapped positions less than L/2 apart along that axis
+// (every list member: r <= r_s <= L/2), from their 32-bit fixed-point codes:
+// the plain difference crosses half the box exactly when the code difference
+// wrapped to 32 bits has the opposite sign.  Adding the shift rounds once, as
+// x - L rint(x / L) does, so the difference is the same double; the decision
+// takes integer compares and selects instead of an FP64 multiply and round.
+__device__ __forceinline__ double image_shift(uint32_t cj, uint32_t ci, double L)
+{
+    const int w = (int)(cj - ci);
+    return (cj > ci && w < 0) ? -L : ((cj < ci && w > 0) ? L : 0.0);
 }
 
 // Position of the r-th set bit (r counted from 0) of m, r < popc(m): a
@@ -949,10 +976,10 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     qj = (double)__uint_as_float(sj.w);
                 } else {
                     const double4_32a pj = a.p4[j];
-                    dx = pj.x - pi.x; dy = pj.y - pi.y; dz = pj.z - pi.z;
-                    dx -= c.L * rint(dx * c.invL);
-                    dy -= c.L * rint(dy * c.invL);
-                    dz -= c.L * rint(dz * c.invL);
+                    const uint4 sj = a.s4[j];
+                    dx = pj.x - pi.x + image_shift(sj.x, si.x, c.L);
+                    dy = pj.y - pi.y + image_shift(sj.y, si.y, c.L);
+                    dz = pj.z - pi.z + image_shift(sj.z, si.z, c.L);
                     r2 = dx * dx + dy * dy + dz * dz;
                     const double rinv = rsqrt(r2);     // one reciprocal square root, no division
                     const double rr = r2 * rinv;
@@ -1049,11 +1076,11 @@ __device__ __forceinline__ void rbl_body(const RblArgs& a, int slot, int nslots)
                     w = wsh;
                 }
                 const double4_32a pj = a.p4[j];
+                const uint4 sj = a.s4[j];
                 const int2 tj = a.tm[j];
-                double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                dx -= c.L * rint(dx * c.invL);
-                dy -= c.L * rint(dy * c.invL);
-                dz -= c.L * rint(dz * c.invL);
+                const double dx = pj.x - pi.x + image_shift(sj.x, si.x, c.L);
+                const double dy = pj.y - pi.y + image_shift(sj.y, si.y, c.L);
+                const double dz = pj.z - pi.z + image_shift(sj.z, si.z, c.L);
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 const double rinv = rsqrt(r2);         // one reciprocal square root, no division
                 const double r = r2 * rinv;
